@@ -1,0 +1,323 @@
+"""Benchmark of the transport hot path on one GB300 (particle-steps per second).
+
+Workload (one "step" of this benchmark = one pass of the whole hot path):
+  1 degree global grid 360 x 181 x 60 levels (log-spaced 1000 -> 10 hPa), wind =
+  seeded sum of 64 Fourier modes on the sphere (20 m/s rms u, v; 0.5 Pa/s rms
+  omega), 4 snapshots 6 h apart (24 h periodic); 1e6 particles uniform in
+  lon/lat/ln p; dt = 180 s over 24 h = 480 fused steps of advection + turbulent
+  (Dx = 50, Dz = 0.1 m^2/s) + mesoscale diffusion (Philox normals), particles
+  sorted by met cell every 20 steps; 5 snapshot loads (repack) per pass.
+  Each pass restarts from the same initial particle state.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DT = 180.0
+DT_MET = 21600.0
+T_END = 86400.0
+N_PART = 1_000_000
+SORT_EVERY = 20
+SEED_FIELD = 2
+SEED_PART = 2
+SEED_RNG = 2
+METRIC = "particle-steps/s on 1 GB300 (advect+diffuse) and % gather roofline, surrogate vs plain"
+WORKLOAD = ("1deg 360x181x60 Fourier-mode wind, 4 snapshots 6h apart, 1e6 particles, dt=180s, 24h "
+            "(480 fused advect+turb+meso steps), sort by met cell every 20 steps")
+
+
+def _config(n, extra=None):
+    c = {"workload": WORKLOAD, "grid": "360x181x60", "particles": n, "steps_per_pass": int(T_END / DT),
+         "dt_s": DT, "sort_every": SORT_EVERY, "met_storage": "fp32",
+         "l2": "inputs larger than L2 (~0.45 GB of met sources, slots, particles and sort workspace per pass)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index, self.proc, self.lines = index, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# --------------------------------------------------------------------------
+def oracle_sample_rate(n_sample: int, t_end: float = T_END):
+    """Times the FP64 oracle on the first ``n_sample`` particles of the workload."""
+    from oracle import transport as tr
+    from oracle.driver import run_schedule
+    from workloads import fourier_modes, fourier_snapshot, grid_1deg_60lev, uniform_particles
+    grid = grid_1deg_60lev()
+    modes = fourier_modes(SEED_FIELD)
+    snaps = [fourier_snapshot(grid, modes, h * DT_MET) for h in range(4)]
+    st = uniform_particles(N_PART, grid.plev, SEED_PART)
+    sub = {k: v[:n_sample] for k, v in st.items()}
+    at = lambda t: snaps[int(round(t / DT_MET)) % 4]
+    t0 = time.perf_counter()
+    run_schedule(grid, at, DT_MET, sub, 0.0, t_end, DT, tr.DiffParams(), SEED_RNG)
+    el = time.perf_counter() - t0
+    psteps = n_sample * (t_end / DT)
+    return psteps / el, el
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    n_sample = int(os.environ.get("BENCH_ORACLE_SAMPLE", "2000"))
+    rates, times = [], []
+    for i in range(args.warmup + args.steps):
+        r, el = oracle_sample_rate(n_sample)
+        if i >= args.warmup:
+            rates.append(r)
+            times.append(el)
+    value = len(times) * n_sample * (T_END / DT) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(n_sample, {"oracle_sample_particles": n_sample}),
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {n_sample} particles of the workload, full 24 h (480 steps) per step"},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2211_12616_gb300 as M
+    from paper_2211_12616_gb300.simulation import Simulation, periodic_snapshots
+    from workloads import fourier_modes, fourier_snapshot, grid_1deg_60lev, uniform_particles
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    n = args.particles
+    grid = grid_1deg_60lev()
+    modes = fourier_modes(SEED_FIELD)
+    snaps = [fourier_snapshot(grid, modes, h * DT_MET, device=dev, as_numpy=False) for h in range(4)]
+    st0 = uniform_particles(n, grid.plev, SEED_PART + 1000 * rank, id0=rank * n)
+    init = M.Particles.from_numpy(st0, device=dev)
+    work = init.clone()
+    ctx = M.Context(grid, M.MPTRAC_FP32)
+    prm = M.DiffParams()
+    stream = torch.cuda.Stream(device=dev)
+    sim = Simulation(ctx, periodic_snapshots(snaps, DT_MET), DT_MET, work, DT, prm, SEED_RNG, SORT_EVERY)
+    psteps_per_pass = n * int(round(T_END / DT))
+
+    # per-launch timing of the dominant kernel (the fused step) on its own stream
+    ev_pairs = []
+
+    def hook(stage, s):
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(s)
+        if stage == "begin":
+            ev_pairs.append([e, None])
+        else:
+            ev_pairs[-1][1] = e
+
+    def one_pass():
+        with torch.cuda.stream(stream):
+            work.copy_(init)
+            sim.run(0.0, T_END, stream=stream)
+
+    for _ in range(args.warmup):
+        one_pass()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    time.sleep(0.3)
+    sim.step_hook = hook
+    l0 = M.load().mptrac_kernel_launches()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for _ in range(args.steps):
+        one_pass()
+    end.record(stream)
+    torch.cuda.synchronize()
+    launches = M.load().mptrac_kernel_launches() - l0
+    sim.step_hook = None
+    ms = start.elapsed_time(end)
+    clk = clocks.stop()
+    ms_t = torch.tensor([ms], dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * psteps_per_pass * args.steps / (ms_max / 1000.0)
+    step_ms = [a.elapsed_time(b) for a, b in ev_pairs]
+    step_avg_ms = sum(step_ms) / len(step_ms)
+    psteps_per_launch = n * SORT_EVERY
+
+    # ---- end-to-end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        host_init = {k: getattr(init, k).cpu().pin_memory() for k in M.Particles.FIELDS if getattr(init, k) is not None}
+        host_snaps = [{k: v.cpu().pin_memory() for k, v in s.items()} for s in snaps]
+        out_host = {k: torch.empty(n, dtype=torch.float64).pin_memory() for k in ("lon", "lat", "p")}
+        sim_h = Simulation(ctx, periodic_snapshots(host_snaps, DT_MET), DT_MET, work, DT, prm, SEED_RNG, SORT_EVERY)
+        h2d = sum(t.numel() * t.element_size() for t in host_init.values())
+        h2d += 5 * sum(t.numel() * t.element_size() for t in host_snaps[0].values())
+        d2h = sum(t.numel() * t.element_size() for t in out_host.values())
+
+        def e2e_pass():
+            with torch.cuda.stream(stream):
+                for k, v in host_init.items():
+                    getattr(work, k).copy_(v, non_blocking=True)
+                sim_h.run(0.0, T_END, stream=stream)
+                for k, v in out_host.items():
+                    v.copy_(getattr(work, k), non_blocking=True)
+        for _ in range(max(1, args.warmup // 2)):
+            e2e_pass()
+        torch.cuda.synchronize()
+        s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s2.record(stream)
+        k2 = max(1, args.steps)
+        for _ in range(k2):
+            e2e_pass()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        ms2 = s2.elapsed_time(e2)
+        e2e = {"value": world * psteps_per_pass * k2 / (ms2 / 1000.0), "unit": "particle-steps/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    if rank != 0:
+        return
+    hbm_peak, peak_kind = _peaks()
+    # algorithmic bytes of the fused step per particle-step (float32 met records):
+    # stencil 2 evaluations x 2 snapshots x 8 corners x 16 B record = 512 B, plus the
+    # particle stream per launch (lon/lat/p f64 + meso f32 read and written, id/release read)
+    # spread over SORT_EVERY steps.
+    stencil_b = 2 * 2 * 8 * 16
+    stream_b = (2 * (3 * 8 + 3 * 4) + 2 * 4) / SORT_EVERY
+    bytes_per_launch = psteps_per_launch * (stencil_b + stream_b)
+    achieved = bytes_per_launch / (step_avg_ms / 1000.0) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": _config(n),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None,
+                     "kernel": "k_transport<fp32, step>", "avg_launch_ms": step_avg_ms,
+                     "launches_timed": len(step_ms), "bytes_per_particle_step": stencil_b + stream_b,
+                     "peak_kind": f"{peak_kind} hbm_gbs"},
+        "clocks": clk, "gpu_launches": int(launches),
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        n_sample = int(os.environ.get("BENCH_ORACLE_SAMPLE", "8000"))
+        rate, el = oracle_sample_rate(n_sample)
+        line["cpu_baseline"] = {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first {n_sample} of the 1e6 particles, full 24 h (480 steps), "
+                                          f"{el:.1f} s of numpy float64 on one host core"}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--particles", type=int, default=N_PART)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        import __graft_entry__
+        __graft_entry__.build()
+        run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

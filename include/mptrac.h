@@ -1,0 +1,236 @@
+/*
+ * mptrac.h -- C ABI of the GB300 Lagrangian transport hot path.
+ *
+ * The calls follow the structure of the MPTRAC time loop described in
+ * arxiv 2211.12616:
+ *   mptrac_load_met   ~ read_met + "update device" of a met snapshot (Sections 3.1, 4.1)
+ *   mptrac_set_releases / release masking ~ module_timesteps       (Section 4.3)
+ *   mptrac_advect     ~ module_advection + module_position          (Section 3.2)
+ *   mptrac_diffuse    ~ module_diffusion_turb + module_diffusion_meso with
+ *                       per-device counter-based random numbers     (Sections 3.2, 4.3)
+ *   mptrac_step       ~ the fused chain advection -> turbulent -> mesoscale
+ *                       diffusion -> position, as called in the time loop
+ *   mptrac_sort       ~ the particle sorting modules                (Section 6)
+ * The paper prints no formulas for any of these; the numerics implemented are:
+ *   - 4D linear interpolation (lon periodic, lat clamped, linear in p between
+ *     levels, linear in time between two snapshots);
+ *   - explicit midpoint step on the sphere, R = 6371 km, angles in degrees,
+ *     second stage with cos(lat) of the midpoint;
+ *   - turbulent diffusion sqrt(2 D dt) xi (horizontal metres; vertical metres
+ *     converted as dp = -p dz / H);
+ *   - mesoscale AR(1) wind perturbation scaled by the time-weighted population
+ *     standard deviation of the 8 cell-corner winds;
+ *   - Philox4x32-10 (Salmon et al., SC'11) with counter
+ *     (particle id, step, stream, release), key = seed, Box-Muller normals;
+ *   - lat reflected over the poles (lon + 180), lon wrapped into
+ *     [lon0, lon0 + 360), p clamped to the level range.
+ *
+ * Conventions
+ *   - Every function returns an int status (MPTRAC_OK = 0, negative = error);
+ *     mptrac_last_error() gives a message for the calling thread's last error.
+ *     No C++ exception crosses this boundary.  Arguments are validated on the
+ *     host before anything is launched; an invalid call launches nothing.
+ *   - "device" pointers are CUDA device (or managed) memory owned by the caller;
+ *     the library never frees them.  "host" pointers are read before the call
+ *     returns unless stated otherwise.
+ *   - Work is enqueued asynchronously on `stream` (a cudaStream_t passed as an
+ *     integer; 0 = legacy default stream).  Results are ready once the stream
+ *     has been synchronised.  There is no CPU fallback: without a usable CUDA
+ *     device every call that launches work returns MPTRAC_E_CUDA.
+ *   - A context is not thread-safe; calls on one context must be serialised
+ *     by the caller (they may use different streams).
+ */
+#ifndef MPTRAC_H
+#define MPTRAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define MPTRAC_OK              0
+#define MPTRAC_E_INVALID_ARG  -1   /* a pointer, size or parameter is invalid */
+#define MPTRAC_E_OOM          -2   /* device allocation failed */
+#define MPTRAC_E_CUDA         -3   /* a CUDA runtime call or launch failed */
+#define MPTRAC_E_TIME_RANGE   -4   /* [t, t + nsteps*dt] leaves the loaded snapshots */
+#define MPTRAC_E_WORKSPACE    -5   /* workspace pointer NULL, misaligned or too small */
+#define MPTRAC_E_TIMEOUT      -6   /* a bounded device-side wait gave up */
+#define MPTRAC_E_NOT_INIT     -7   /* context NULL, or met snapshots not loaded */
+
+/* ---- met storage precision -------------------------------------------- */
+#define MPTRAC_FP32 0   /* 4 x float32 per grid point */
+#define MPTRAC_BF16 1   /* 4 x bfloat16 codes + per-(level,variable) power-of-two scale */
+#define MPTRAC_FP16 2   /* 4 x float16 codes + per-(level,variable) power-of-two scale */
+
+#define MPTRAC_MAX_NZ        256   /* largest supported number of pressure levels */
+#define MPTRAC_MAX_RELEASES  65536 /* largest release table */
+
+typedef struct mptrac_ctx mptrac_ctx;   /* opaque: met slots, level tables, release table */
+
+/* Grid of the met snapshots (the paper's met_t, Section 3.1).
+ *   nx, ny, nz      number of longitudes, latitudes and pressure levels
+ *                   (nx >= 2, ny >= 2, 2 <= nz <= MPTRAC_MAX_NZ)
+ *   lon0, dlon      first longitude and spacing [deg]; the grid is periodic:
+ *                   nx * dlon must equal 360 (within 1e-9)
+ *   lat0, dlat      first latitude and spacing [deg], dlat > 0
+ *   plev            HOST array of nz levels [Pa], strictly decreasing
+ *                   (level 0 is the lowest); copied during the call
+ *   storage         MPTRAC_FP32 / MPTRAC_BF16 / MPTRAC_FP16
+ *   nvars           3 (u, v, omega) or 4 (u, v, omega, T)                  */
+typedef struct {
+    int nx, ny, nz;
+    double lon0, dlon, lat0, dlat;
+    const double* plev;
+    int storage;
+    int nvars;
+} mptrac_grid_desc;
+
+/* Particle state (the paper's atm_t, Section 4.4), structure of arrays of
+ * length n, all DEVICE pointers owned by the caller.
+ *   lon, lat, p     float64 positions [deg, deg, Pa]; lon in [lon0, lon0+360)
+ *   id              uint32 particle identity (the random-number counter uses
+ *                   it, so results do not depend on the array order)
+ *   release         uint32 release index into the table set by
+ *                   mptrac_set_releases, or NULL (all particles always active)
+ *   up, vp, wp      float32 mesoscale wind perturbations [m/s, m/s, Pa/s];
+ *                   may be NULL when mesoscale diffusion is off and the arrays
+ *                   are not to be sorted.                                    */
+typedef struct {
+    int64_t n;
+    double* lon;
+    double* lat;
+    double* p;
+    uint32_t* id;
+    uint32_t* release;
+    float* up;
+    float* vp;
+    float* wp;
+} mptrac_particles;
+
+/* Diffusion parameters (module_diffusion_turb / module_diffusion_meso).
+ *   dx, dz          horizontal and vertical turbulent diffusivity [m^2/s], >= 0
+ *   meso_f          mesoscale scaling factor f, >= 0
+ *   scale_height    H [m] converting vertical metres to pressure, > 0
+ *   turb, meso      non-zero to enable each term                          */
+typedef struct {
+    double dx, dz;
+    double meso_f;
+    double scale_height;
+    int turb, meso;
+} mptrac_diff_params;
+
+/* Creates a context for grid `g`: allocates two device met slots and the
+ * level tables on the current CUDA device.  On success *out owns them until
+ * mptrac_destroy.  Errors: E_INVALID_ARG (bad grid), E_OOM, E_CUDA. */
+int mptrac_init_grid(mptrac_ctx** out, const mptrac_grid_desc* g);
+
+/* Frees everything the context owns (after synchronising the device). NULL is a no-op. */
+int mptrac_destroy(mptrac_ctx* ctx);
+
+/* Message of the calling thread's most recent error ("" if none). `ctx` may be NULL. */
+const char* mptrac_last_error(const mptrac_ctx* ctx);
+
+/* Loads snapshot time `t` [s] into met slot `slot` (0 or 1)  -- read_met +
+ * update device (Sections 3.1, 4.1).  u, v, omega (and T when nvars == 4,
+ * otherwise ignored) are float32 arrays of nz*ny*nx values in layout
+ * [level][lat][lon], on the DEVICE if src_is_device != 0, else on the HOST (copied
+ * on `stream` through a context-owned staging buffer; the host arrays must
+ * stay valid until the stream has passed this call).  The slot is rewritten
+ * as records [lat][lon][level] x (u, v, omega, T) in the grid's storage
+ * precision; reduced precision uses per-(level, variable) power-of-two scales
+ * 2^(E-15), maxabs = m 2^E, m in [0.5, 1).  The two loaded slots must have
+ * different times; the earlier one is the interval start.
+ * Errors: E_INVALID_ARG, E_NOT_INIT, E_CUDA. */
+int mptrac_load_met(mptrac_ctx* ctx, int slot, double t,
+                    const float* u, const float* v, const float* omega, const float* T,
+                    int src_is_device, uintptr_t stream);
+
+/* Release table for time-step masking (module_timesteps, Section 4.3):
+ * a particle of release r moves at step time t_n only if
+ * t_start[r] <= t_n < t_end[r].  HOST arrays of n entries (0 < n <=
+ * MPTRAC_MAX_RELEASES), copied synchronously.  n == 0 clears the table (then
+ * every particle is active whatever its release index).
+ * Particles whose release index is >= n are never active. */
+int mptrac_set_releases(mptrac_ctx* ctx, int n, const double* t_start, const double* t_end);
+
+/* nsteps explicit midpoint advection steps from time t with step dt > 0
+ * (module_advection, each step followed by module_position).  Requires
+ * t0 <= t and t + nsteps*dt <= t1 for the loaded snapshot times, else
+ * E_TIME_RANGE.  nsteps >= 0.  Particle positions are updated in place. */
+int mptrac_advect(mptrac_ctx* ctx, const mptrac_particles* parts, double t, double dt,
+                  int nsteps, uintptr_t stream);
+
+/* nsteps diffusion-only steps (module_diffusion_turb + module_diffusion_meso +
+ * module_position): subgrid variance and displacement at the current position.
+ * Random numbers: Philox4x32-10, counter (id, step0 + n, stream 0|1, release),
+ * key (seed low, seed high words).  up/vp/wp must be non-NULL when
+ * prm->meso != 0.  Same time-range rule as mptrac_advect. */
+int mptrac_diffuse(mptrac_ctx* ctx, const mptrac_particles* parts, double t, double dt,
+                   const mptrac_diff_params* prm, uint64_t seed, uint64_t step0,
+                   int nsteps, uintptr_t stream);
+
+/* Fused production step: per step, midpoint advection (its first wind
+ * evaluation also yields the corner variances), turbulent + mesoscale
+ * displacement converted at the post-advection position, then the position
+ * rules.  With prm->turb == prm->meso == 0 it equals mptrac_advect; with a
+ * zero wind it equals mptrac_diffuse.  The particle state stays in registers
+ * for all nsteps steps of the call (temporal blocking). */
+int mptrac_step(mptrac_ctx* ctx, const mptrac_particles* parts, double t, double dt,
+                const mptrac_diff_params* prm, uint64_t seed, uint64_t step0,
+                int nsteps, uintptr_t stream);
+
+/* Bytes of device workspace mptrac_sort needs for n particles. */
+size_t mptrac_sort_workspace_bytes(const mptrac_ctx* ctx, int64_t n);
+
+/* Sorts the particles by met cell (Section 6, the sorting modules): key =
+ * (j*nx + i)*nz + k of the cell containing each particle (same cell rule as
+ * the interpolation), stable LSD radix sort, then every non-NULL array of
+ * `parts` is permuted the same way.  `workspace` is caller-owned DEVICE memory,
+ * 256-byte aligned, of at least mptrac_sort_workspace_bytes(ctx, n) bytes,
+ * else E_WORKSPACE.  It must not be in use by another call in flight. */
+int mptrac_sort(mptrac_ctx* ctx, const mptrac_particles* parts, void* workspace,
+                size_t ws_bytes, uintptr_t stream);
+
+/* ---- inspection entry points (used by the parity tests) ---------------- */
+
+/* Cell keys of the sort, written to DEVICE array keys[n]. */
+int mptrac_cell_keys(mptrac_ctx* ctx, const mptrac_particles* parts, uint32_t* keys,
+                     uintptr_t stream);
+
+/* Wind (u, v, omega) interpolated at n DEVICE positions lon/lat/p (float64)
+ * and time t (4D linear, float32 arithmetic as in the step kernels); writes
+ * DEVICE float32 arrays out_u/out_v/out_w[n]; if out_var is non-NULL it also
+ * receives the time-weighted corner variances, layout [3][n]. */
+int mptrac_interp(mptrac_ctx* ctx, int64_t n, const double* lon, const double* lat,
+                  const double* p, double t, float* out_u, float* out_v, float* out_w,
+                  float* out_var, uintptr_t stream);
+
+/* Raw Philox4x32-10 words: ctr is a DEVICE uint32 array [4][n] (counter word c
+ * of item i at ctr[c*n + i]); out receives [4][n] words.  If normals is non-NULL
+ * it receives the four Box-Muller normals [4][n] (float32) of each item. */
+int mptrac_philox(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_t* out,
+                  float* normals, uintptr_t stream);
+
+/* Read-only view of met slot `slot`: device pointer to its records
+ * ([lat][lon][level] x 4 values: float32, or uint16 codes), its scales
+ * (device float32 [4][nz]), its time and its record bytes.  Any output
+ * pointer may be NULL. */
+int mptrac_met_slot_info(const mptrac_ctx* ctx, int slot, const void** records,
+                         const float** scales, double* t, size_t* bytes);
+
+/* Number of CUDA kernels this library has launched in this process so far. */
+uint64_t mptrac_kernel_launches(void);
+
+/* Copies met slot `slot` into caller-owned DEVICE buffers: records_out
+ * (mptrac_met_slot_info's `bytes` bytes) and scales_out (4*nz float32), on
+ * `stream`.  Either output may be NULL. */
+int mptrac_met_slot_copy(const mptrac_ctx* ctx, int slot, void* records_out, float* scales_out,
+                         uintptr_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPTRAC_H */

@@ -1,0 +1,11 @@
+"""GB300-native Lagrangian transport hot path (MPTRAC-style, arxiv 2211.12616).
+
+The computation lives in ``libmptrac.so`` (hand-written CUDA for sm_103a behind
+the C ABI of ``include/mptrac.h``); this package is its thin ctypes binding.
+PyTorch provides device memory and streams only.
+"""
+from ._native import (Context, DiffParams, MptracError, Particles, load, philox,
+                      MPTRAC_BF16, MPTRAC_FP16, MPTRAC_FP32, SIGNATURES, LIB_PATH)
+
+__all__ = ["Context", "DiffParams", "MptracError", "Particles", "load", "philox",
+           "MPTRAC_FP32", "MPTRAC_BF16", "MPTRAC_FP16", "SIGNATURES", "LIB_PATH"]

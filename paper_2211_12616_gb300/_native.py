@@ -1,0 +1,282 @@
+"""ctypes binding of libmptrac (include/mptrac.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; this module only turns
+torch tensors into device pointers and status codes into exceptions.  If the
+shared library is missing the import fails loudly -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmptrac.so")
+
+MPTRAC_FP32, MPTRAC_BF16, MPTRAC_FP16 = 0, 1, 2
+STATUS = {0: "OK", -1: "E_INVALID_ARG", -2: "E_OOM", -3: "E_CUDA", -4: "E_TIME_RANGE",
+          -5: "E_WORKSPACE", -6: "E_TIMEOUT", -7: "E_NOT_INIT"}
+
+
+class MptracError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("lon0", C.c_double), ("dlon", C.c_double), ("lat0", C.c_double), ("dlat", C.c_double),
+                ("plev", C.POINTER(C.c_double)), ("storage", C.c_int), ("nvars", C.c_int)]
+
+
+class ParticlesDesc(C.Structure):
+    _fields_ = [("n", C.c_int64), ("lon", C.c_void_p), ("lat", C.c_void_p), ("p", C.c_void_p),
+                ("id", C.c_void_p), ("release", C.c_void_p), ("up", C.c_void_p), ("vp", C.c_void_p),
+                ("wp", C.c_void_p)]
+
+
+class DiffParamsDesc(C.Structure):
+    _fields_ = [("dx", C.c_double), ("dz", C.c_double), ("meso_f", C.c_double),
+                ("scale_height", C.c_double), ("turb", C.c_int), ("meso", C.c_int)]
+
+
+# exported symbol -> (restype, argtypes)
+SIGNATURES = {
+    "mptrac_init_grid": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(GridDesc)]),
+    "mptrac_destroy": (C.c_int, [C.c_void_p]),
+    "mptrac_last_error": (C.c_char_p, [C.c_void_p]),
+    "mptrac_load_met": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_int, C.c_void_p]),
+    "mptrac_set_releases": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "mptrac_advect": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_double, C.c_double, C.c_int,
+                                C.c_void_p]),
+    "mptrac_diffuse": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_double, C.c_double,
+                                 C.POINTER(DiffParamsDesc), C.c_uint64, C.c_uint64, C.c_int, C.c_void_p]),
+    "mptrac_step": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_double, C.c_double,
+                              C.POINTER(DiffParamsDesc), C.c_uint64, C.c_uint64, C.c_int, C.c_void_p]),
+    "mptrac_sort_workspace_bytes": (C.c_size_t, [C.c_void_p, C.c_int64]),
+    "mptrac_sort": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_void_p, C.c_size_t, C.c_void_p]),
+    "mptrac_cell_keys": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_void_p, C.c_void_p]),
+    "mptrac_interp": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mptrac_philox": (C.c_int, [C.c_void_p, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mptrac_met_slot_info": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                       C.POINTER(C.c_double), C.POINTER(C.c_size_t)]),
+    "mptrac_met_slot_copy": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mptrac_kernel_launches": (C.c_uint64, []),
+}
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Loads libmptrac.so (built by ``__graft_entry__.build()``); raises if it is absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libmptrac.so not found at {LIB_PATH}: build it first "
+                              "(python -c 'import __graft_entry__ as g; g.build()'); there is no CPU fallback")
+        lib = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype, fn.argtypes = res, args
+        _lib = lib
+    return _lib
+
+
+def check(code: int, ctx=None):
+    if code != 0:
+        msg = load().mptrac_last_error(ctx)
+        raise MptracError(code, msg.decode() if msg else "")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError("tensors passed to libmptrac must be contiguous")
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays passed to libmptrac must be C-contiguous")
+        return t.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(t)}")
+
+
+class DiffParams:
+    def __init__(self, dx=50.0, dz=0.1, meso_f=0.16, scale_height=7000.0, turb=True, meso=True):
+        self.dx, self.dz, self.meso_f, self.scale_height = dx, dz, meso_f, scale_height
+        self.turb, self.meso = bool(turb), bool(meso)
+
+    def desc(self) -> DiffParamsDesc:
+        return DiffParamsDesc(self.dx, self.dz, self.meso_f, self.scale_height, int(self.turb), int(self.meso))
+
+
+class Particles:
+    """Device structure-of-arrays particle state (torch tensors own the memory).
+
+    lon/lat/p float64, id/release int32 tensors holding uint32 bit patterns,
+    up/vp/wp float32 mesoscale perturbations.
+    """
+    FIELDS = ("lon", "lat", "p", "id", "release", "up", "vp", "wp")
+
+    def __init__(self, lon, lat, p, id, release=None, up=None, vp=None, wp=None):
+        self.lon, self.lat, self.p, self.id = lon, lat, p, id
+        self.release, self.up, self.vp, self.wp = release, up, vp, wp
+
+    @classmethod
+    def from_numpy(cls, d: dict, device="cuda", meso=True, release=True):
+        n = len(d["lon"])
+        t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(device=device, dtype=dt)
+        u32 = lambda a: torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.uint32)).view(np.int32)).to(device)
+        up = vp = wp = None
+        if meso:
+            up = t(d.get("up", np.zeros(n)), torch.float32)
+            vp = t(d.get("vp", np.zeros(n)), torch.float32)
+            wp = t(d.get("wp", np.zeros(n)), torch.float32)
+        rel = u32(d.get("release", np.zeros(n, np.uint32))) if release else None
+        return cls(t(d["lon"], torch.float64), t(d["lat"], torch.float64), t(d["p"], torch.float64),
+                   u32(d["id"]), rel, up, vp, wp)
+
+    def to_numpy(self) -> dict:
+        out = {}
+        for k in self.FIELDS:
+            v = getattr(self, k)
+            if v is None:
+                continue
+            a = v.detach().cpu().numpy()
+            out[k] = a.view(np.uint32) if k in ("id", "release") else a
+        return out
+
+    def clone(self) -> "Particles":
+        return Particles(*[None if getattr(self, k) is None else getattr(self, k).clone() for k in self.FIELDS])
+
+    def copy_(self, other: "Particles"):
+        for k in self.FIELDS:
+            a, b = getattr(self, k), getattr(other, k)
+            if a is not None and b is not None:
+                a.copy_(b, non_blocking=True)
+        return self
+
+    @property
+    def n(self) -> int:
+        return int(self.lon.numel())
+
+    def desc(self) -> ParticlesDesc:
+        return ParticlesDesc(self.n, *[_ptr(getattr(self, k)) for k in self.FIELDS[:]])
+
+
+class Context:
+    """One grid + two met slots (``mptrac_init_grid``)."""
+
+    def __init__(self, grid, storage: int = MPTRAC_FP32, nvars: int = 3):
+        lib = load()
+        self.grid = grid
+        self.storage, self.nvars = storage, nvars
+        self._plev = np.ascontiguousarray(grid.plev, dtype=np.float64)
+        gd = GridDesc(grid.nx, grid.ny, grid.nz, grid.lon0, grid.dlon, grid.lat0, grid.dlat,
+                      self._plev.ctypes.data_as(C.POINTER(C.c_double)), storage, nvars)
+        h = C.c_void_p()
+        check(lib.mptrac_init_grid(C.byref(h), C.byref(gd)))
+        self.h = h
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            check(load().mptrac_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_met(self, slot, t, u, v, w, T=None, stream=None):
+        on_dev = isinstance(u, torch.Tensor) and u.is_cuda
+        if not on_dev:
+            u, v, w = (np.ascontiguousarray(a, dtype=np.float32) for a in (u, v, w))
+            T = None if T is None else np.ascontiguousarray(T, dtype=np.float32)
+            self._keep = [u, v, w, T]     # host copies stay alive until the next call
+        check(load().mptrac_load_met(self.h, slot, float(t), _ptr(u), _ptr(v), _ptr(w), _ptr(T),
+                                     int(on_dev), _stream(stream)), self.h)
+
+    def set_releases(self, t_start, t_end):
+        ts = np.ascontiguousarray(t_start, dtype=np.float64)
+        te = np.ascontiguousarray(t_end, dtype=np.float64)
+        check(load().mptrac_set_releases(self.h, ts.size, ts.ctypes.data, te.ctypes.data), self.h)
+
+    def advect(self, parts: Particles, t, dt, nsteps, stream=None):
+        check(load().mptrac_advect(self.h, C.byref(parts.desc()), float(t), float(dt), int(nsteps),
+                                   _stream(stream)), self.h)
+
+    def diffuse(self, parts: Particles, t, dt, prm: DiffParams, seed, step0, nsteps, stream=None):
+        check(load().mptrac_diffuse(self.h, C.byref(parts.desc()), float(t), float(dt), C.byref(prm.desc()),
+                                    int(seed), int(step0), int(nsteps), _stream(stream)), self.h)
+
+    def step(self, parts: Particles, t, dt, prm: DiffParams, seed, step0, nsteps, stream=None):
+        check(load().mptrac_step(self.h, C.byref(parts.desc()), float(t), float(dt), C.byref(prm.desc()),
+                                 int(seed), int(step0), int(nsteps), _stream(stream)), self.h)
+
+    def sort_workspace_bytes(self, n: int) -> int:
+        return int(load().mptrac_sort_workspace_bytes(self.h, int(n)))
+
+    def sort(self, parts: Particles, workspace: torch.Tensor | None = None, stream=None):
+        nbytes = self.sort_workspace_bytes(parts.n)
+        if workspace is None:
+            workspace = torch.empty(nbytes, dtype=torch.uint8, device=parts.lon.device)
+        check(load().mptrac_sort(self.h, C.byref(parts.desc()), _ptr(workspace), workspace.numel(),
+                                 _stream(stream)), self.h)
+        return workspace
+
+    def cell_keys(self, parts: Particles, stream=None) -> torch.Tensor:
+        keys = torch.empty(parts.n, dtype=torch.int32, device=parts.lon.device)
+        check(load().mptrac_cell_keys(self.h, C.byref(parts.desc()), _ptr(keys), _stream(stream)), self.h)
+        return keys
+
+    def interp(self, lon, lat, p, t, stream=None):
+        n = lon.numel()
+        dev = lon.device
+        u, v, w = (torch.empty(n, dtype=torch.float32, device=dev) for _ in range(3))
+        var = torch.empty(3, n, dtype=torch.float32, device=dev)
+        check(load().mptrac_interp(self.h, n, _ptr(lon), _ptr(lat), _ptr(p), float(t), _ptr(u), _ptr(v),
+                                   _ptr(w), _ptr(var), _stream(stream)), self.h)
+        return u, v, w, var
+
+    def slot_info(self, slot):
+        rec, sc, t, nb = C.c_void_p(), C.c_void_p(), C.c_double(), C.c_size_t()
+        check(load().mptrac_met_slot_info(self.h, slot, C.byref(rec), C.byref(sc), C.byref(t), C.byref(nb)),
+              self.h)
+        return rec.value, sc.value, t.value, nb.value
+
+    def slot_arrays(self, slot, stream=None):
+        """Copies of slot `slot`'s records ([ny][nx][nz][4]) and scales ([4][nz]) as numpy arrays."""
+        _, _, t, nb = self.slot_info(slot)
+        g = self.grid
+        rec = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        sc = torch.empty(4 * g.nz, dtype=torch.float32, device="cuda")
+        check(load().mptrac_met_slot_copy(self.h, slot, _ptr(rec), _ptr(sc), _stream(stream)), self.h)
+        torch.cuda.synchronize()
+        dt = np.float32 if self.storage == MPTRAC_FP32 else np.uint16
+        return rec.cpu().numpy().view(dt).reshape(g.ny, g.nx, g.nz, 4), sc.cpu().numpy().reshape(4, g.nz), t
+
+
+def philox(ctr: torch.Tensor, seed: int, with_normals: bool = False, stream=None):
+    """Raw Philox4x32-10 words for counters ``ctr`` (int32 tensor [4][n] of uint32 bits)."""
+    n = ctr.shape[1]
+    out = torch.empty(4, n, dtype=torch.int32, device=ctr.device)
+    z = torch.empty(4, n, dtype=torch.float32, device=ctr.device) if with_normals else None
+    check(load().mptrac_philox(_ptr(ctr), n, int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out), _ptr(z), _stream(stream)))
+    return (out, z) if with_normals else out

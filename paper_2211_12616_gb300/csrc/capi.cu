@@ -1,0 +1,494 @@
+// C ABI of libmptrac (declared in include/mptrac.h): context management,
+// host-side argument validation and kernel dispatch.  Every entry point
+// validates before it launches; errors are reported as status codes plus a
+// thread-local message, never as exceptions or device faults.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace mptrac;
+
+struct mptrac_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int nx = 0, ny = 0, nz = 0, storage = 0, nvars = 3;
+    double lon0 = 0, dlon = 0, lat0 = 0, dlat = 0;
+    std::vector<double> plev;
+    float* d_plev = nullptr;
+    float* d_invdp = nullptr;
+    int16_t* d_kguess = nullptr;
+    double* d_plev_d = nullptr;
+    void* d_met[2] = {nullptr, nullptr};
+    float* d_scales[2] = {nullptr, nullptr};
+    double t_slot[2] = {0.0, 0.0};
+    bool loaded[2] = {false, false};
+    size_t rec_bytes = 0;
+    float* d_staging = nullptr;
+    double* d_rel_ts = nullptr;
+    double* d_rel_te = nullptr;
+    int2* d_win = nullptr;
+    int n_rel = 0;
+    int key_bits = 0;
+    Geo geo{};
+};
+
+namespace {
+
+thread_local char g_err[1024] = "";
+std::atomic<uint64_t> g_launches{0};
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int ok() {
+    g_err[0] = '\0';
+    return MPTRAC_OK;
+}
+
+#define MPTRAC_CUDA(call)                                                                    \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            (void)cudaGetLastError();                                                        \
+            return fail(e_ == cudaErrorMemoryAllocation ? MPTRAC_E_OOM : MPTRAC_E_CUDA,      \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));                     \
+        }                                                                                    \
+    } while (0)
+
+// A pointer the device can dereference: device, managed or registered host memory.
+bool device_accessible(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged ||
+           at.type == cudaMemoryTypeHost;
+}
+
+constexpr double kRadius = 6371000.0;
+constexpr double kPi = 3.14159265358979323846;
+
+void free_ctx(mptrac_ctx* c) {
+    void* ptrs[] = {c->d_plev, c->d_invdp, c->d_kguess, c->d_plev_d, c->d_met[0], c->d_met[1],
+                    c->d_scales[0], c->d_scales[1], c->d_staging, c->d_rel_ts, c->d_rel_te,
+                    c->d_win};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete c;
+}
+
+int check_particles(const mptrac_particles* P, bool need_meso) {
+    if (!P) return fail(MPTRAC_E_INVALID_ARG, "particles descriptor is NULL");
+    if (P->n < 0 || P->n > 0x7FFFFFFF) return fail(MPTRAC_E_INVALID_ARG, "particle count %lld out of range [0, 2^31-1]", (long long)P->n);
+    if (P->n == 0) return MPTRAC_OK;
+    const void* req[] = {P->lon, P->lat, P->p, P->id};
+    const char* names[] = {"lon", "lat", "p", "id"};
+    for (int q = 0; q < 4; ++q)
+        if (!device_accessible(req[q]))
+            return fail(MPTRAC_E_INVALID_ARG, "particles.%s is NULL or not device memory", names[q]);
+    if (P->release && !device_accessible(P->release))
+        return fail(MPTRAC_E_INVALID_ARG, "particles.release is not device memory");
+    const void* meso[] = {P->up, P->vp, P->wp};
+    const char* mnames[] = {"up", "vp", "wp"};
+    for (int q = 0; q < 3; ++q) {
+        if (meso[q] && !device_accessible(meso[q]))
+            return fail(MPTRAC_E_INVALID_ARG, "particles.%s is not device memory", mnames[q]);
+        if (need_meso && !meso[q])
+            return fail(MPTRAC_E_INVALID_ARG, "particles.%s is NULL but mesoscale diffusion is on", mnames[q]);
+    }
+    return MPTRAC_OK;
+}
+
+int ordered_slots(const mptrac_ctx* c, int& a, int& b) {
+    if (!c->loaded[0] || !c->loaded[1])
+        return fail(MPTRAC_E_NOT_INIT, "both met slots must be loaded (slot0 %s, slot1 %s)",
+                    c->loaded[0] ? "loaded" : "empty", c->loaded[1] ? "loaded" : "empty");
+    if (c->t_slot[0] == c->t_slot[1])
+        return fail(MPTRAC_E_NOT_INIT, "met slots hold the same time %g", c->t_slot[0]);
+    a = c->t_slot[0] < c->t_slot[1] ? 0 : 1;
+    b = 1 - a;
+    return MPTRAC_OK;
+}
+
+int run_transport(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
+                  const mptrac_diff_params* prm, uint64_t seed, uint64_t step0, int nsteps,
+                  uintptr_t stream, int mode) {
+    if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(MPTRAC_E_INVALID_ARG, "dt must be finite and > 0 (got %g)", dt);
+    if (!std::isfinite(t)) return fail(MPTRAC_E_INVALID_ARG, "t must be finite");
+    if (nsteps < 0) return fail(MPTRAC_E_INVALID_ARG, "nsteps must be >= 0 (got %d)", nsteps);
+    bool turb = false, meso = false;
+    if (mode != MODE_ADVECT) {
+        if (!prm) return fail(MPTRAC_E_INVALID_ARG, "diffusion parameters are NULL");
+        turb = prm->turb != 0;
+        meso = prm->meso != 0;
+        if (!(prm->dx >= 0) || !(prm->dz >= 0) || !(prm->meso_f >= 0) || !(prm->scale_height > 0) ||
+            !std::isfinite(prm->dx) || !std::isfinite(prm->dz) || !std::isfinite(prm->meso_f) ||
+            !std::isfinite(prm->scale_height))
+            return fail(MPTRAC_E_INVALID_ARG, "diffusion parameters out of range");
+    }
+    int rc = check_particles(P, meso);
+    if (rc) return rc;
+    int s0, s1;
+    if ((rc = ordered_slots(c, s0, s1))) return rc;
+    const double t0 = c->t_slot[s0], t1 = c->t_slot[s1];
+    const double tend = t + (double)nsteps * dt;
+    const double tol = 1e-9 * (t1 - t0);
+    if (t < t0 - tol || tend > t1 + tol)
+        return fail(MPTRAC_E_TIME_RANGE, "[%.9g, %.9g] leaves the loaded snapshots [%.9g, %.9g]", t, tend, t0, t1);
+    if (P->n == 0 || nsteps == 0) return ok();
+    // the fused step with both diffusion terms off is exactly the advection kernel
+    if (mode == MODE_STEP && !turb && !meso) mode = MODE_ADVECT;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+
+    StepArgs a;
+    memset(&a, 0, sizeof(a));
+    a.geo = c->geo;
+    a.m0 = MetView{c->d_met[s0], c->d_scales[s0]};
+    a.m1 = MetView{c->d_met[s1], c->d_scales[s1]};
+    a.n = P->n;
+    a.lon = P->lon;
+    a.lat = P->lat;
+    a.p = P->p;
+    a.id = P->id;
+    a.release = P->release;
+    a.up = P->up;
+    a.vp = P->vp;
+    a.wp = P->wp;
+    const bool use_win = P->release && c->n_rel > 0;
+    a.win = use_win ? c->d_win : nullptr;
+    a.n_rel = c->n_rel;
+    a.dt = (float)dt;
+    a.half_dt = (float)(0.5 * dt);
+    a.kdeg = (float)(180.0 / (kPi * kRadius));
+    a.turb = turb;
+    a.meso = meso;
+    if (mode != MODE_ADVECT) {
+        a.sh = (float)std::sqrt(2.0 * prm->dx * dt);
+        a.sv = (float)std::sqrt(2.0 * prm->dz * dt);
+        a.inv_H = (float)(1.0 / prm->scale_height);
+        double r = 1.0 - 2.0 * dt / (t1 - t0);
+        r = r < 0.0 ? 0.0 : (r > 1.0 ? 1.0 : r);
+        a.r_ar = (float)r;
+        a.a_ar = (float)(std::sqrt(1.0 - r * r) * prm->meso_f);
+    }
+    a.key0 = (uint32_t)(seed & 0xFFFFFFFFull);
+    a.key1 = (uint32_t)(seed >> 32);
+    const int grid = (int)std::min<int64_t>((P->n + kBlock - 1) / kBlock, (int64_t)1 << 20);
+    for (int n0 = 0; n0 < nsteps; n0 += kMaxStepsPerLaunch) {
+        const int cnt = std::min(kMaxStepsPerLaunch, nsteps - n0);
+        a.nsteps = cnt;
+        a.step0 = step0 + (uint64_t)n0;
+        for (int q = 0; q < cnt; ++q) {
+            const double tn = t + (double)(n0 + q) * dt;
+            a.wt[2 * q] = (float)((tn - t0) / (t1 - t0));
+            a.wt[2 * q + 1] = (float)((tn + 0.5 * dt - t0) / (t1 - t0));
+        }
+        if (use_win) MPTRAC_CUDA(launch_windows(c->d_rel_ts, c->d_rel_te, c->n_rel, t, dt, n0, cnt, c->d_win, st));
+        MPTRAC_CUDA(launch_transport(c->storage, mode, a, grid, st));
+    }
+    return ok();
+}
+
+}  // namespace
+
+namespace mptrac {
+void note_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+}  // namespace mptrac
+
+extern "C" {
+
+uint64_t mptrac_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int mptrac_init_grid(mptrac_ctx** out, const mptrac_grid_desc* g) {
+    if (!out || !g) return fail(MPTRAC_E_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (g->nx < 2 || g->ny < 2 || g->nz < 2 || g->nz > MPTRAC_MAX_NZ)
+        return fail(MPTRAC_E_INVALID_ARG, "grid size %d x %d x %d out of range", g->nx, g->ny, g->nz);
+    const int64_t npts = (int64_t)g->nx * g->ny * g->nz;
+    if (npts >= ((int64_t)1 << 31)) return fail(MPTRAC_E_INVALID_ARG, "grid has %lld points (limit 2^31-1)", (long long)npts);
+    if (!(g->dlon > 0) || !(g->dlat > 0) || !std::isfinite(g->lon0) || !std::isfinite(g->lat0))
+        return fail(MPTRAC_E_INVALID_ARG, "bad grid spacing or origin");
+    if (std::fabs(g->nx * g->dlon - 360.0) > 1e-9 * 360.0)
+        return fail(MPTRAC_E_INVALID_ARG, "nx * dlon = %.12g, must be 360 (periodic longitude)", g->nx * g->dlon);
+    if ((double)(float)g->lon0 != g->lon0) return fail(MPTRAC_E_INVALID_ARG, "lon0 must be exactly representable in float32");
+    if (g->storage < MPTRAC_FP32 || g->storage > MPTRAC_FP16) return fail(MPTRAC_E_INVALID_ARG, "unknown storage %d", g->storage);
+    if (g->nvars != 3 && g->nvars != 4) return fail(MPTRAC_E_INVALID_ARG, "nvars must be 3 or 4");
+    if (!g->plev) return fail(MPTRAC_E_INVALID_ARG, "plev is NULL");
+    for (int k = 0; k < g->nz; ++k) {
+        if (!(g->plev[k] > 0) || !std::isfinite(g->plev[k])) return fail(MPTRAC_E_INVALID_ARG, "plev[%d] must be finite and > 0", k);
+        if (k && !(g->plev[k] < g->plev[k - 1])) return fail(MPTRAC_E_INVALID_ARG, "plev must be strictly decreasing (level %d)", k);
+    }
+    mptrac_ctx* c = new (std::nothrow) mptrac_ctx();
+    if (!c) return fail(MPTRAC_E_OOM, "host allocation failed");
+    c->nx = g->nx; c->ny = g->ny; c->nz = g->nz;
+    c->lon0 = g->lon0; c->dlon = g->dlon; c->lat0 = g->lat0; c->dlat = g->dlat;
+    c->storage = g->storage; c->nvars = g->nvars;
+    c->plev.assign(g->plev, g->plev + g->nz);
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete c;
+        return fail(MPTRAC_E_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
+    }
+    const int nz = g->nz;
+    std::vector<float> plev_f(nz), invdp(nz, 0.f);
+    for (int k = 0; k < nz; ++k) plev_f[k] = (float)g->plev[k];
+    for (int k = 0; k + 1 < nz; ++k) invdp[k] = (float)(1.0 / ((double)plev_f[k] - (double)plev_f[k + 1]));
+    const double ln_top = std::log(g->plev[nz - 1]), ln_bot = std::log(g->plev[0]);
+    const int nbins = kGuessBins;
+    const double inv_dln = nbins / (ln_bot - ln_top);
+    std::vector<int16_t> kg(nbins);
+    for (int b = 0; b < nbins; ++b) {
+        const double pc = std::exp(ln_top + (b + 0.5) / inv_dln);
+        int cnt = 0;
+        for (int k = 0; k < nz; ++k) cnt += (plev_f[k] >= pc);
+        int k = cnt - 1;
+        k = k < 0 ? 0 : (k > nz - 2 ? nz - 2 : k);
+        kg[b] = (int16_t)k;
+    }
+    c->rec_bytes = (size_t)npts * (g->storage == MPTRAC_FP32 ? 16 : 8);
+    c->key_bits = 0;
+    while (c->key_bits < 32 && ((uint64_t)1 << c->key_bits) < (uint64_t)npts) ++c->key_bits;
+
+    auto alloc = [&](void** p, size_t bytes) -> int {
+        cudaError_t ee = cudaMalloc(p, bytes);
+        if (ee != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(ee == cudaErrorMemoryAllocation ? MPTRAC_E_OOM : MPTRAC_E_CUDA,
+                        "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(ee));
+        }
+        return MPTRAC_OK;
+    };
+    int rc = MPTRAC_OK;
+    if (!rc) rc = alloc((void**)&c->d_plev, nz * sizeof(float));
+    if (!rc) rc = alloc((void**)&c->d_invdp, nz * sizeof(float));
+    if (!rc) rc = alloc((void**)&c->d_kguess, nbins * sizeof(int16_t));
+    if (!rc) rc = alloc((void**)&c->d_plev_d, nz * sizeof(double));
+    for (int s = 0; s < 2 && !rc; ++s) {
+        rc = alloc(&c->d_met[s], c->rec_bytes);
+        if (!rc) rc = alloc((void**)&c->d_scales[s], 4 * nz * sizeof(float));
+    }
+    if (rc) {
+        free_ctx(c);
+        return rc;
+    }
+    e = cudaMemcpy(c->d_plev, plev_f.data(), nz * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_invdp, invdp.data(), nz * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_kguess, kg.data(), nbins * sizeof(int16_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_plev_d, g->plev, nz * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        free_ctx(c);
+        return fail(MPTRAC_E_CUDA, "table upload failed: %s", cudaGetErrorString(e));
+    }
+    Geo& G = c->geo;
+    G.nx = g->nx; G.ny = g->ny; G.nz = nz; G.nbins = nbins;
+    G.lon0 = (float)g->lon0;
+    G.inv_dlon = (float)(1.0 / g->dlon);
+    G.lat0 = (float)g->lat0;
+    G.inv_dlat = (float)(1.0 / g->dlat);
+    const double pmin = g->plev[nz - 1], pmax = g->plev[0];
+    G.pmin = (float)pmin;
+    G.pmin_lo = (float)(pmin - (double)G.pmin);
+    G.pmax = (float)pmax;
+    G.pmax_lo = (float)(pmax - (double)G.pmax);
+    G.lnp_top = (float)ln_top;
+    G.inv_dln = (float)inv_dln;
+    G.plev = c->d_plev;
+    G.inv_dp = c->d_invdp;
+    G.kguess = c->d_kguess;
+    G.lon0_d = g->lon0; G.dlon_d = g->dlon; G.lat0_d = g->lat0; G.dlat_d = g->dlat;
+    G.pmin_d = pmin; G.pmax_d = pmax;
+    G.plev_d = c->d_plev_d;
+    *out = c;
+    return ok();
+}
+
+int mptrac_destroy(mptrac_ctx* ctx) {
+    if (!ctx) return ok();
+    cudaError_t e = cudaDeviceSynchronize();
+    free_ctx(ctx);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(MPTRAC_E_CUDA, "device error while destroying context: %s", cudaGetErrorString(e));
+    }
+    return ok();
+}
+
+const char* mptrac_last_error(const mptrac_ctx*) { return g_err; }
+
+int mptrac_load_met(mptrac_ctx* c, int slot, double t, const float* u, const float* v,
+                    const float* omega, const float* T, int src_is_device, uintptr_t stream) {
+    if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    if (slot != 0 && slot != 1) return fail(MPTRAC_E_INVALID_ARG, "slot must be 0 or 1 (got %d)", slot);
+    if (!std::isfinite(t)) return fail(MPTRAC_E_INVALID_ARG, "t must be finite");
+    if (!u || !v || !omega) return fail(MPTRAC_E_INVALID_ARG, "u, v and omega must not be NULL");
+    if (c->nvars == 4 && !T) return fail(MPTRAC_E_INVALID_ARG, "T must not be NULL when nvars == 4");
+    if (c->nvars == 3) T = nullptr;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t npts = (size_t)c->nx * c->ny * c->nz;
+    const float* src[4] = {u, v, omega, T};
+    if (src_is_device) {
+        for (int q = 0; q < c->nvars; ++q)
+            if (!device_accessible(src[q])) return fail(MPTRAC_E_INVALID_ARG, "met variable %d is not device memory", q);
+    } else {
+        if (!c->d_staging) {
+            cudaError_t e = cudaMalloc((void**)&c->d_staging, 4 * npts * sizeof(float));
+            if (e != cudaSuccess) {
+                (void)cudaGetLastError();
+                c->d_staging = nullptr;
+                return fail(MPTRAC_E_OOM, "staging allocation failed: %s", cudaGetErrorString(e));
+            }
+        }
+        for (int q = 0; q < c->nvars; ++q) {
+            float* dst = c->d_staging + q * npts;
+            MPTRAC_CUDA(cudaMemcpyAsync(dst, src[q], npts * sizeof(float), cudaMemcpyHostToDevice, st));
+            src[q] = dst;
+        }
+    }
+    MPTRAC_CUDA(launch_pack(c->storage, c->nvars, src[0], src[1], src[2], src[3], c->nx, c->ny, c->nz,
+                            c->d_met[slot], c->d_scales[slot], st));
+    c->t_slot[slot] = t;
+    c->loaded[slot] = true;
+    return ok();
+}
+
+int mptrac_set_releases(mptrac_ctx* c, int n, const double* ts, const double* te) {
+    if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    if (n < 0 || n > MPTRAC_MAX_RELEASES) return fail(MPTRAC_E_INVALID_ARG, "release count %d out of range", n);
+    if (n > 0 && (!ts || !te)) return fail(MPTRAC_E_INVALID_ARG, "release times are NULL");
+    for (int r = 0; r < n; ++r)
+        if (std::isnan(ts[r]) || std::isnan(te[r])) return fail(MPTRAC_E_INVALID_ARG, "release %d has NaN times", r);
+    void* old[] = {c->d_rel_ts, c->d_rel_te, c->d_win};
+    for (void* p : old)
+        if (p) MPTRAC_CUDA(cudaFree(p));
+    c->d_rel_ts = c->d_rel_te = nullptr;
+    c->d_win = nullptr;
+    c->n_rel = 0;
+    if (n == 0) return ok();
+    MPTRAC_CUDA(cudaMalloc((void**)&c->d_rel_ts, n * sizeof(double)));
+    MPTRAC_CUDA(cudaMalloc((void**)&c->d_rel_te, n * sizeof(double)));
+    MPTRAC_CUDA(cudaMalloc((void**)&c->d_win, n * sizeof(int2)));
+    MPTRAC_CUDA(cudaMemcpy(c->d_rel_ts, ts, n * sizeof(double), cudaMemcpyHostToDevice));
+    MPTRAC_CUDA(cudaMemcpy(c->d_rel_te, te, n * sizeof(double), cudaMemcpyHostToDevice));
+    c->n_rel = n;
+    return ok();
+}
+
+int mptrac_advect(mptrac_ctx* c, const mptrac_particles* P, double t, double dt, int nsteps,
+                  uintptr_t stream) {
+    return run_transport(c, P, t, dt, nullptr, 0, 0, nsteps, stream, MODE_ADVECT);
+}
+
+int mptrac_diffuse(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
+                   const mptrac_diff_params* prm, uint64_t seed, uint64_t step0, int nsteps,
+                   uintptr_t stream) {
+    return run_transport(c, P, t, dt, prm, seed, step0, nsteps, stream, MODE_DIFFUSE);
+}
+
+int mptrac_step(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
+                const mptrac_diff_params* prm, uint64_t seed, uint64_t step0, int nsteps,
+                uintptr_t stream) {
+    return run_transport(c, P, t, dt, prm, seed, step0, nsteps, stream, MODE_STEP);
+}
+
+size_t mptrac_sort_workspace_bytes(const mptrac_ctx*, int64_t n) {
+    return sort_workspace_bytes(n < 0 ? 0 : n);
+}
+
+int mptrac_sort(mptrac_ctx* c, const mptrac_particles* P, void* ws, size_t ws_bytes,
+                uintptr_t stream) {
+    if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    int rc = check_particles(P, false);
+    if (rc) return rc;
+    if (P->n == 0) return ok();
+    const size_t need = sort_workspace_bytes(P->n);
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < need)
+        return fail(MPTRAC_E_WORKSPACE, "sort workspace must be 256-byte aligned device memory of >= %zu bytes (got %p, %zu)", need, ws, ws_bytes);
+    if (!device_accessible(ws)) return fail(MPTRAC_E_WORKSPACE, "sort workspace is not device memory");
+    MPTRAC_CUDA(run_sort(c->geo, *P, ws, c->key_bits, reinterpret_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
+int mptrac_cell_keys(mptrac_ctx* c, const mptrac_particles* P, uint32_t* keys, uintptr_t stream) {
+    if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    int rc = check_particles(P, false);
+    if (rc) return rc;
+    if (P->n == 0) return ok();
+    if (!device_accessible(keys)) return fail(MPTRAC_E_INVALID_ARG, "keys is not device memory");
+    MPTRAC_CUDA(launch_cell_keys(c->geo, P->n, P->lon, P->lat, P->p, keys, reinterpret_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
+int mptrac_interp(mptrac_ctx* c, int64_t n, const double* lon, const double* lat, const double* p,
+                  double t, float* ou, float* ov, float* ow, float* ovar, uintptr_t stream) {
+    if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    if (n < 0 || n > 0x7FFFFFFF) return fail(MPTRAC_E_INVALID_ARG, "n out of range");
+    int s0, s1, rc;
+    if ((rc = ordered_slots(c, s0, s1))) return rc;
+    if (n == 0) return ok();
+    const void* ptrs[] = {lon, lat, p, ou, ov, ow};
+    for (const void* q : ptrs)
+        if (!device_accessible(q)) return fail(MPTRAC_E_INVALID_ARG, "interp arrays must be device memory");
+    if (ovar && !device_accessible(ovar)) return fail(MPTRAC_E_INVALID_ARG, "out_var is not device memory");
+    const double t0 = c->t_slot[s0], t1 = c->t_slot[s1];
+    if (!(t >= t0 && t <= t1)) return fail(MPTRAC_E_TIME_RANGE, "t = %g outside [%g, %g]", t, t0, t1);
+    const float w = (float)((t - t0) / (t1 - t0));
+    MPTRAC_CUDA(launch_interp(c->storage, c->geo, MetView{c->d_met[s0], c->d_scales[s0]},
+                              MetView{c->d_met[s1], c->d_scales[s1]}, w, n, lon, lat, p, ou, ov, ow,
+                              ovar, reinterpret_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
+int mptrac_philox(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_t* out, float* normals,
+                  uintptr_t stream) {
+    if (n < 0 || n > 0x7FFFFFFF) return fail(MPTRAC_E_INVALID_ARG, "n out of range");
+    if (n == 0) return ok();
+    if (!device_accessible(ctr) || !device_accessible(out))
+        return fail(MPTRAC_E_INVALID_ARG, "ctr and out must be device memory");
+    if (normals && !device_accessible(normals)) return fail(MPTRAC_E_INVALID_ARG, "normals is not device memory");
+    MPTRAC_CUDA(launch_philox(ctr, n, (uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32), out,
+                              normals, reinterpret_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
+int mptrac_met_slot_info(const mptrac_ctx* c, int slot, const void** records, const float** scales,
+                         double* t, size_t* bytes) {
+    if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    if (slot != 0 && slot != 1) return fail(MPTRAC_E_INVALID_ARG, "slot must be 0 or 1");
+    if (records) *records = c->d_met[slot];
+    if (scales) *scales = c->d_scales[slot];
+    if (t) *t = c->t_slot[slot];
+    if (bytes) *bytes = c->rec_bytes;
+    return ok();
+}
+
+int mptrac_met_slot_copy(const mptrac_ctx* c, int slot, void* rec_out, float* sc_out,
+                         uintptr_t stream) {
+    if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    if (slot != 0 && slot != 1) return fail(MPTRAC_E_INVALID_ARG, "slot must be 0 or 1");
+    if (rec_out && !device_accessible(rec_out)) return fail(MPTRAC_E_INVALID_ARG, "records_out is not device memory");
+    if (sc_out && !device_accessible(sc_out)) return fail(MPTRAC_E_INVALID_ARG, "scales_out is not device memory");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (rec_out) MPTRAC_CUDA(cudaMemcpyAsync(rec_out, c->d_met[slot], c->rec_bytes, cudaMemcpyDeviceToDevice, st));
+    if (sc_out) MPTRAC_CUDA(cudaMemcpyAsync(sc_out, c->d_scales[slot], 4 * c->nz * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// Internal declarations shared by the translation units of libmptrac.
+// Nothing here crosses the C ABI; see include/mptrac.h for the public calls.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "../../include/mptrac.h"
+
+namespace mptrac {
+
+constexpr int kMaxNZ = MPTRAC_MAX_NZ;
+constexpr int kMaxStepsPerLaunch = 128;   // time-weight table carried in the kernel parameters
+constexpr int kGuessBins = 1024;          // ln(p) bins of the level first-guess table
+constexpr int kBlock = 256;               // threads per block of the particle kernels
+
+// Grid geometry as the kernels see it.
+struct Geo {
+    int nx, ny, nz, nbins;
+    float lon0, inv_dlon, lat0, inv_dlat;
+    float pmin, pmax;             // level range (float)
+    float pmin_lo, pmax_lo;       // pmin = pmin + pmin_lo exactly as float-float
+    float lnp_top, inv_dln;       // ln(p) bin origin and inverse width
+    const float* plev;            // [nz]    float levels
+    const float* inv_dp;          // [nz]    1 / (plev[k] - plev[k+1])
+    const int16_t* kguess;        // [nbins] first-guess level index per ln(p) bin
+    // float64 copies for the exact cell keys of the sort
+    double lon0_d, dlon_d, lat0_d, dlat_d, pmin_d, pmax_d;
+    const double* plev_d;         // [nz]
+};
+
+// One met slot: records [lat][lon][level] x 4 values, scales [4][nz].
+struct MetView {
+    const void* rec;
+    const float* scales;
+};
+
+// Arguments of the particle kernels (advect / diffuse / step).
+struct StepArgs {
+    Geo geo;
+    MetView m0, m1;               // m0 = earlier snapshot
+    int64_t n;
+    double* lon;
+    double* lat;
+    double* p;
+    const uint32_t* id;
+    const uint32_t* release;      // may be null
+    float* up;
+    float* vp;
+    float* wp;
+    const int2* win;              // per-release active step window, or null
+    int n_rel;
+    int nsteps;
+    float dt, half_dt, kdeg;      // kdeg = 180 / (pi R)  [deg per metre]
+    int turb, meso;
+    float sh, sv, inv_H;          // sqrt(2 Dx dt), sqrt(2 Dz dt), 1/H
+    float r_ar, a_ar;             // AR(1) coefficient r and sqrt(1 - r^2) f
+    uint32_t key0, key1;          // Philox key = seed
+    uint64_t step0;
+    float wt[2 * kMaxStepsPerLaunch];   // time weights at t_n and t_n + dt/2
+};
+
+enum Mode { MODE_ADVECT = 0, MODE_DIFFUSE = 1, MODE_STEP = 2 };
+
+// Process-wide count of kernels this library has launched (inspection only).
+void note_launches(int n);
+
+// ---- launchers (each returns a cudaError_t of the launch) -------------------
+cudaError_t launch_transport(int storage, int mode, const StepArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_windows(const double* ts, const double* te, int nrel, double t, double dt,
+                           int n_begin, int nsteps, int2* out, cudaStream_t s);
+cudaError_t launch_interp(int storage, const Geo& g, MetView m0, MetView m1, float w, int64_t n,
+                          const double* lon, const double* lat, const double* p, float* ou,
+                          float* ov, float* ow, float* ovar, cudaStream_t s);
+cudaError_t launch_philox(const uint32_t* ctr, int64_t n, uint32_t k0, uint32_t k1, uint32_t* out,
+                          float* normals, cudaStream_t s);
+
+cudaError_t launch_pack(int storage, int nvars, const float* u, const float* v, const float* w,
+                        const float* T, int nx, int ny, int nz, void* rec, float* scales,
+                        cudaStream_t s);
+
+size_t sort_workspace_bytes(int64_t n);
+cudaError_t launch_cell_keys(const Geo& g, int64_t n, const double* lon, const double* lat,
+                             const double* p, uint32_t* keys, cudaStream_t s);
+cudaError_t run_sort(const Geo& g, const mptrac_particles& P, void* ws, int key_bits,
+                     cudaStream_t s);
+
+}  // namespace mptrac

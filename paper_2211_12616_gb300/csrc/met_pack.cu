@@ -1,0 +1,131 @@
+// Met snapshot repacking (read_met + "update device", arxiv 2211.12616
+// Sections 3.1 and 4.1): variables given as separate [level][lat][lon] float32
+// arrays become one record per grid point, [lat][lon][level] x (u, v, omega, T),
+// so that the two levels of a cell column are adjacent in memory.
+//
+// 16-bit storage first reduces each (variable, level) plane to its largest
+// magnitude maxabs = m 2^E (m in [0.5, 1)) and stores the power-of-two scale
+// 2^(E-15); codes are round-to-nearest-even of x * 2^(15-E), an exact scaling.
+//
+// The transpose goes through shared memory in tiles of 32 longitudes x 32
+// levels: reads are 128-byte rows of one level, writes are runs of 32
+// consecutive records.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "internal.h"
+
+namespace mptrac {
+namespace {
+
+constexpr int kTile = 32;
+
+// One block per (variable, level): largest |x| over the lat-lon plane, then
+// the power-of-two scale of that plane.
+__global__ void k_plane_scale(const float* __restrict__ f0, const float* __restrict__ f1,
+                              const float* __restrict__ f2, const float* __restrict__ f3,
+                              int64_t plane, int nz, float* scales) {
+    const int k = blockIdx.x, var = blockIdx.y;
+    const float* f = var == 0 ? f0 : var == 1 ? f1 : var == 2 ? f2 : f3;
+    float m = 0.f;
+    if (f) {
+        const float* row = f + (int64_t)k * plane;
+        for (int64_t q = threadIdx.x; q < plane; q += blockDim.x) m = fmaxf(m, fabsf(row[q]));
+    }
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    __shared__ float red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.f;
+        for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if (threadIdx.x == 0) {
+            float s = 1.f;
+            if (m > 0.f) {
+                int e;
+                frexpf(m, &e);
+                s = ldexpf(1.f, e - 15);
+            }
+            scales[var * nz + k] = s;
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t code16(float x, int storage) {
+    if (storage == MPTRAC_BF16) return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
+    return (uint32_t)__half_as_ushort(__float2half_rn(x));
+}
+
+// grid (ceil(nx/32), ny, ceil(nz/32)), block (32, 8)
+template <int ST>
+__global__ void __launch_bounds__(256) k_pack(const float* __restrict__ u, const float* __restrict__ v,
+                                              const float* __restrict__ w, const float* __restrict__ T,
+                                              int nx, int ny, int nz, void* recv,
+                                              const float* __restrict__ scales) {
+    __shared__ float tile[4][kTile][kTile + 1];   // [var][level][lon]
+    const int i0 = blockIdx.x * kTile, j = blockIdx.y, k0 = blockIdx.z * kTile;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t plane = (int64_t)nx * ny;
+    const float* src[4] = {u, v, w, T};
+#pragma unroll
+    for (int var = 0; var < 4; ++var) {
+        for (int kk = ty; kk < kTile; kk += 8) {
+            const int k = k0 + kk, i = i0 + tx;
+            float x = 0.f;
+            if (src[var] && k < nz && i < nx) {
+                x = src[var][(int64_t)k * plane + (int64_t)j * nx + i];
+                if (ST != MPTRAC_FP32) x *= 1.0f / scales[var * nz + k];
+            }
+            tile[var][kk][tx] = x;
+        }
+    }
+    __syncthreads();
+    const int t = ty * kTile + tx;
+#pragma unroll
+    for (int rep = 0; rep < (kTile * kTile) / 256; ++rep) {
+        const int e = rep * 256 + t;
+        const int il = e / kTile, kl = e % kTile;
+        const int i = i0 + il, k = k0 + kl;
+        if (i >= nx || k >= nz) continue;
+        const int64_t r = ((int64_t)j * nx + i) * nz + k;
+        if (ST == MPTRAC_FP32) {
+            static_cast<float4*>(recv)[r] =
+                make_float4(tile[0][kl][il], tile[1][kl][il], tile[2][kl][il], tile[3][kl][il]);
+        } else {
+            const uint32_t a = code16(tile[0][kl][il], ST) | (code16(tile[1][kl][il], ST) << 16);
+            const uint32_t b = code16(tile[2][kl][il], ST) | (code16(tile[3][kl][il], ST) << 16);
+            static_cast<uint2*>(recv)[r] = make_uint2(a, b);
+        }
+    }
+}
+
+__global__ void k_fill(float* p, int n, float v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+}  // namespace
+
+cudaError_t launch_pack(int storage, int nvars, const float* u, const float* v, const float* w,
+                        const float* T, int nx, int ny, int nz, void* rec, float* scales,
+                        cudaStream_t s) {
+    if (nvars < 4) T = nullptr;
+    const int64_t plane = (int64_t)nx * ny;
+    note_launches(2);
+    if (storage == MPTRAC_FP32) {
+        k_fill<<<(4 * nz + 255) / 256, 256, 0, s>>>(scales, 4 * nz, 1.f);
+    } else {
+        k_plane_scale<<<dim3(nz, 4), 512, 0, s>>>(u, v, w, T, plane, nz, scales);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const dim3 grid((nx + kTile - 1) / kTile, ny, (nz + kTile - 1) / kTile), block(kTile, 8);
+    switch (storage) {
+        case MPTRAC_FP32: k_pack<MPTRAC_FP32><<<grid, block, 0, s>>>(u, v, w, T, nx, ny, nz, rec, scales); break;
+        case MPTRAC_BF16: k_pack<MPTRAC_BF16><<<grid, block, 0, s>>>(u, v, w, T, nx, ny, nz, rec, scales); break;
+        default: k_pack<MPTRAC_FP16><<<grid, block, 0, s>>>(u, v, w, T, nx, ny, nz, rec, scales); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mptrac

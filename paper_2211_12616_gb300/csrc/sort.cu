@@ -1,0 +1,302 @@
+// Particle sorting by met cell (the sorting modules of arxiv 2211.12616,
+// Section 6).  key = (j*nx + i)*nz + k of each particle's cell, computed in
+// float64 with the same expressions as the interpolation's cell rule, then a
+// stable least-significant-digit radix sort of (key, index) pairs with 8-bit
+// digits, then one gather of every particle array.
+//
+// Each pass: (1) per-tile digit histograms, (2) per-digit scan over tiles,
+// (3) stable scatter.  A tile is 2048 keys handled by 256 threads in 8 rounds
+// of 256 consecutive keys; inside a round, lanes with equal digits find each
+// other with __match_any_sync and are ranked by lane, warps are ranked by a
+// shared-memory scan, rounds by a running count -- which keeps equal keys in
+// their input order.
+#include "internal.h"
+
+namespace mptrac {
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kRounds = 8;
+constexpr int kTileKeys = kSortThreads * kRounds;
+constexpr int kRadix = 256;
+
+__device__ __forceinline__ uint32_t cell_key(double lon, double lat, double p, const Geo& g) {
+    // longitude: x = ((lon - lon0) mod 360) / dlon, mod with a non-negative result
+    double r = fmod(__dsub_rn(lon, g.lon0_d), 360.0);
+    if (r < 0.0) r = __dadd_rn(r, 360.0);
+    const double x = __ddiv_rn(r, g.dlon_d);
+    long long i = (long long)floor(x);
+    i %= g.nx;
+    if (i < 0) i += g.nx;
+    const double y = __ddiv_rn(__dsub_rn(lat, g.lat0_d), g.dlat_d);
+    long long j = (long long)floor(y);
+    j = j < 0 ? 0 : (j > g.ny - 2 ? g.ny - 2 : j);
+    const double pc = fmin(fmax(p, g.pmin_d), g.pmax_d);
+    // k = (number of levels with plev >= pc) - 1, clamped to [0, nz-2]
+    int lo = 0, hi = g.nz;   // plev decreasing: count the prefix with plev >= pc
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (g.plev_d[mid] >= pc) lo = mid + 1; else hi = mid;
+    }
+    int k = lo - 1;
+    k = k < 0 ? 0 : (k > g.nz - 2 ? g.nz - 2 : k);
+    return (uint32_t)((j * g.nx + i) * g.nz + k);
+}
+
+__global__ void k_keys(Geo g, int64_t n, const double* lon, const double* lat, const double* p,
+                       uint32_t* keys, uint32_t* vals) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
+        keys[q] = cell_key(lon[q], lat[q], p[q], g);
+        if (vals) vals[q] = (uint32_t)q;
+    }
+}
+
+// hist[d * ntiles + tile] = number of keys of `tile` with digit d
+__global__ void __launch_bounds__(kSortThreads) k_hist(const uint32_t* __restrict__ keys, int64_t n,
+                                                       int shift, uint32_t* hist, int ntiles) {
+    __shared__ uint32_t h[kRadix];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kTileKeys;
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const int64_t q = base + r * kSortThreads + threadIdx.x;
+        if (q < n) atomicAdd(&h[(keys[q] >> shift) & 0xFF], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// One block per digit: exclusive scan of its row of tile counts; row total to tot[d].
+__global__ void __launch_bounds__(kSortThreads) k_scan_rows(uint32_t* hist, int ntiles, uint32_t* tot) {
+    __shared__ uint32_t warp_sum[kSortThreads / 32];
+    __shared__ uint32_t carry;
+    uint32_t* row = hist + (int64_t)blockIdx.x * ntiles;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int base = 0; base < ntiles; base += kSortThreads) {
+        const int q = base + threadIdx.x;
+        const uint32_t v = q < ntiles ? row[q] : 0u;
+        uint32_t incl = v;
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += o;
+        }
+        if (lane == 31) warp_sum[wid] = incl;
+        __syncthreads();
+        uint32_t wpre = 0, total = 0;
+        for (int w = 0; w < kSortThreads / 32; ++w) {
+            const uint32_t s = warp_sum[w];
+            if (w < wid) wpre += s;
+            total += s;
+        }
+        const uint32_t c = carry;
+        if (q < ntiles) row[q] = c + wpre + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry = c + total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tot[blockIdx.x] = carry;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_scatter(const uint32_t* __restrict__ kin,
+                                                          const uint32_t* __restrict__ vin,
+                                                          uint32_t* __restrict__ kout,
+                                                          uint32_t* __restrict__ vout, int64_t n,
+                                                          int shift, const uint32_t* __restrict__ offs,
+                                                          const uint32_t* __restrict__ tot, int ntiles) {
+    __shared__ uint32_t s_base[kRadix];
+    __shared__ uint32_t s_run[kRadix];
+    __shared__ uint32_t s_wc[kSortThreads / 32][kRadix];
+    __shared__ uint32_t s_tot_scan[kRadix];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    // exclusive scan of the digit totals (256 values, one per thread)
+    {
+        const uint32_t v = tot[tid];
+        uint32_t incl = v;
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += o;
+        }
+        __shared__ uint32_t ws[kSortThreads / 32];
+        if (lane == 31) ws[wid] = incl;
+        __syncthreads();
+        uint32_t pre = 0;
+        for (int w = 0; w < wid; ++w) pre += ws[w];
+        s_tot_scan[tid] = pre + incl - v;
+    }
+    s_base[tid] = s_tot_scan[tid] + offs[(int64_t)tid * ntiles + blockIdx.x];
+    s_run[tid] = 0;
+    __syncthreads();
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int64_t base = (int64_t)blockIdx.x * kTileKeys;
+    for (int r = 0; r < kRounds; ++r) {
+        const int64_t q = base + r * kSortThreads + tid;
+        const bool valid = q < n;
+        const uint32_t key = valid ? kin[q] : 0u;
+        const uint32_t val = valid ? (vin ? vin[q] : (uint32_t)q) : 0u;
+        const uint32_t d = (key >> shift) & 0xFF;
+#pragma unroll
+        for (int w = 0; w < kSortThreads / 32; ++w) s_wc[w][tid] = 0;
+        __syncthreads();
+        const unsigned peers = __match_any_sync(0xffffffffu, valid ? d : (kRadix + lane));
+        const uint32_t rank = __popc(peers & lt_mask);
+        if (valid && rank == 0) s_wc[wid][d] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t run = s_run[tid];
+#pragma unroll
+            for (int w = 0; w < kSortThreads / 32; ++w) {
+                const uint32_t c = s_wc[w][tid];
+                s_wc[w][tid] = run;
+                run += c;
+            }
+            s_run[tid] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            const uint32_t pos = s_base[d] + s_wc[wid][d] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+    }
+}
+
+struct PermArgs {
+    int64_t n;
+    const uint32_t* perm;
+    double* dst_d[3];
+    const double* src_d[3];
+    uint32_t* dst_u[2];
+    const uint32_t* src_u[2];
+    float* dst_f[3];
+    const float* src_f[3];
+};
+
+__global__ void k_permute(const __grid_constant__ PermArgs a) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
+        const uint32_t s = a.perm[q];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (a.dst_d[c]) a.dst_d[c][q] = a.src_d[c][s];
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+            if (a.dst_u[c]) a.dst_u[c][q] = a.src_u[c][s];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (a.dst_f[c]) a.dst_f[c][q] = a.src_f[c][s];
+    }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int64_t ntiles_for(int64_t n) { return (n + kTileKeys - 1) / kTileKeys; }
+
+struct WsLayout {
+    size_t keys_a, keys_b, vals_a, vals_b, hist, tot, copy_d, copy_u, copy_f, total;
+};
+
+WsLayout ws_layout(int64_t n) {
+    WsLayout L{};
+    size_t o = 0;
+    const size_t nn = (size_t)(n > 0 ? n : 0);
+    const size_t nt = (size_t)ntiles_for(n);
+    L.keys_a = o; o += align256(nn * 4);
+    L.keys_b = o; o += align256(nn * 4);
+    L.vals_a = o; o += align256(nn * 4);
+    L.vals_b = o; o += align256(nn * 4);
+    L.hist = o; o += align256(nt * kRadix * 4);
+    L.tot = o; o += align256(kRadix * 4);
+    L.copy_d = o; o += align256(nn * 8) * 3;
+    L.copy_u = o; o += align256(nn * 4) * 2;
+    L.copy_f = o; o += align256(nn * 4) * 3;
+    L.total = o;
+    return L;
+}
+
+int grid_for(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    if (b < 1) b = 1;
+    if (b > (1 << 20)) b = 1 << 20;
+    return (int)b;
+}
+
+}  // namespace
+
+size_t sort_workspace_bytes(int64_t n) { return ws_layout(n).total; }
+
+cudaError_t launch_cell_keys(const Geo& g, int64_t n, const double* lon, const double* lat,
+                             const double* p, uint32_t* keys, cudaStream_t s) {
+    note_launches(1);
+    k_keys<<<grid_for(n), 256, 0, s>>>(g, n, lon, lat, p, keys, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t run_sort(const Geo& g, const mptrac_particles& P, void* ws, int key_bits,
+                     cudaStream_t s) {
+    const int64_t n = P.n;
+    if (n <= 0) return cudaSuccess;
+    const WsLayout L = ws_layout(n);
+    char* w = static_cast<char*>(ws);
+    uint32_t* ka = reinterpret_cast<uint32_t*>(w + L.keys_a);
+    uint32_t* kb = reinterpret_cast<uint32_t*>(w + L.keys_b);
+    uint32_t* va = reinterpret_cast<uint32_t*>(w + L.vals_a);
+    uint32_t* vb = reinterpret_cast<uint32_t*>(w + L.vals_b);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(w + L.hist);
+    uint32_t* tot = reinterpret_cast<uint32_t*>(w + L.tot);
+    const int ntiles = (int)ntiles_for(n);
+
+    k_keys<<<grid_for(n), 256, 0, s>>>(g, n, P.lon, P.lat, P.p, ka, nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int passes = key_bits <= 0 ? 1 : (key_bits + 7) / 8;
+    note_launches(2 + 3 * passes);
+    bool first = true;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        k_hist<<<ntiles, kSortThreads, 0, s>>>(ka, n, shift, hist, ntiles);
+        k_scan_rows<<<kRadix, kSortThreads, 0, s>>>(hist, ntiles, tot);
+        k_scatter<<<ntiles, kSortThreads, 0, s>>>(ka, first ? nullptr : va, kb, vb, n, shift, hist,
+                                                  tot, ntiles);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        first = false;
+        uint32_t* t = ka; ka = kb; kb = t;
+        t = va; va = vb; vb = t;
+    }
+    // copy the arrays aside, then gather them back in sorted order
+    PermArgs pa{};
+    pa.n = n;
+    pa.perm = va;
+    double* dd[3] = {P.lon, P.lat, P.p};
+    uint32_t* uu[2] = {P.id, P.release};
+    float* fl[3] = {P.up, P.vp, P.wp};
+    for (int c = 0; c < 3; ++c) {
+        if (!dd[c]) continue;
+        double* cp = reinterpret_cast<double*>(w + L.copy_d + c * align256((size_t)n * 8));
+        if ((e = cudaMemcpyAsync(cp, dd[c], (size_t)n * 8, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+        pa.dst_d[c] = dd[c];
+        pa.src_d[c] = cp;
+    }
+    for (int c = 0; c < 2; ++c) {
+        if (!uu[c]) continue;
+        uint32_t* cp = reinterpret_cast<uint32_t*>(w + L.copy_u + c * align256((size_t)n * 4));
+        if ((e = cudaMemcpyAsync(cp, uu[c], (size_t)n * 4, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+        pa.dst_u[c] = uu[c];
+        pa.src_u[c] = cp;
+    }
+    for (int c = 0; c < 3; ++c) {
+        if (!fl[c]) continue;
+        float* cp = reinterpret_cast<float*>(w + L.copy_f + c * align256((size_t)n * 4));
+        if ((e = cudaMemcpyAsync(cp, fl[c], (size_t)n * 4, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+        pa.dst_f[c] = fl[c];
+        pa.src_f[c] = cp;
+    }
+    k_permute<<<grid_for(n), 256, 0, s>>>(pa);
+    return cudaGetLastError();
+}
+
+}  // namespace mptrac

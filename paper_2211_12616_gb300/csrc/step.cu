@@ -1,0 +1,542 @@
+// Particle kernels of the transport hot path: 4D interpolation, explicit
+// midpoint advection on the sphere, Philox-driven turbulent and mesoscale
+// diffusion, release masking and position boundary rules
+// (module_timesteps / module_advection / module_diffusion_turb /
+//  module_diffusion_meso / module_position of arxiv 2211.12616, Sections 3.2
+//  and 4.3; the numerics are the readings stated in include/mptrac.h).
+//
+// GB300 design:
+//  * one thread per particle, grid-stride; the particle's state stays in
+//    registers for all steps of a launch (temporal blocking), so the particle
+//    stream costs ~60 B per launch, not per step;
+//  * positions are float64 in memory but carried as float-float pairs
+//    (hi + lo) in registers: GB300's float64 rate is a small fraction of its
+//    float32 rate, while a float-float add is six float32 adds;
+//  * met records are [lat][lon][level] x (u, v, omega, T): the two levels of a
+//    cell column are adjacent, so one evaluation touches 4 columns x 2 levels
+//    per snapshot, fetched with 16-byte (float32) or 8-byte (16-bit) loads
+//    through L1/L2; sorting particles by cell makes a warp's stencils overlap;
+//  * random numbers are generated in registers (counter-based Philox): no
+//    random-number arrays are stored or read.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "internal.h"
+
+namespace mptrac {
+namespace {
+
+constexpr float kCosFloor = 1.745329243e-05f;   // cos(89.999 deg)
+constexpr float kTwoPow23Inv = 1.1920928955078125e-07f;
+
+// ---------------------------------------------------------------------------
+// float-float arithmetic (value = hi + lo, |lo| <= ulp(hi)/2)
+// ---------------------------------------------------------------------------
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_make(double d) {
+    float h = __double2float_rn(d);
+    float l = __double2float_rn(d - (double)h);
+    return {h, l};
+}
+__device__ __forceinline__ double ff_val(ff a) { return (double)a.hi + (double)a.lo; }
+
+// a + b with the rounding error of the hi sum carried into lo (Knuth TwoSum),
+// then renormalised.  Explicit _rn intrinsics keep the compiler from fusing.
+__device__ __forceinline__ ff ff_add(ff a, float b) {
+    float s = __fadd_rn(a.hi, b);
+    float bb = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    float lo = __fadd_rn(a.lo, e);
+    float hi = __fadd_rn(s, lo);
+    lo = __fsub_rn(lo, __fsub_rn(hi, s));
+    return {hi, lo};
+}
+__device__ __forceinline__ bool ff_less(ff a, float bh, float bl) {
+    return a.hi < bh || (a.hi == bh && a.lo < bl);
+}
+__device__ __forceinline__ bool ff_greater(ff a, float bh, float bl) {
+    return a.hi > bh || (a.hi == bh && a.lo > bl);
+}
+
+// |cos(lat)| floored at cos(89.999 deg), from the colatitude so that it keeps
+// its relative precision next to the poles.
+__device__ __forceinline__ float coslat(ff lat) {
+    float colat = (lat.hi >= 0.f) ? __fsub_rn(__fsub_rn(90.f, lat.hi), lat.lo)
+                                  : __fadd_rn(__fadd_rn(90.f, lat.hi), lat.lo);
+    float c = fabsf(sinpif(colat * (1.0f / 180.0f)));
+    return fmaxf(c, kCosFloor);
+}
+
+// module_position: reflect over the poles (lon + 180), wrap lon into
+// [lon0, lon0 + 360), clamp p to the level range.
+__device__ __forceinline__ void position_bc(ff& lon, ff& lat, ff& p, const Geo& g) {
+    if (ff_greater(lat, 90.f, 0.f)) {
+        lat.hi = __fsub_rn(180.f, lat.hi);   // exact: lat.hi in [90, 180]
+        lat.lo = -lat.lo;
+        lon = ff_add(lon, 180.f);
+    } else if (ff_less(lat, -90.f, 0.f)) {
+        lat.hi = __fsub_rn(-180.f, lat.hi);
+        lat.lo = -lat.lo;
+        lon = ff_add(lon, 180.f);
+    }
+    const float L0 = g.lon0, L1 = g.lon0 + 360.f;
+    if (!ff_less(lon, L1, 0.f) || ff_less(lon, L0, 0.f)) {
+        float turns = floorf((lon.hi - L0) * (1.0f / 360.0f));
+        if (isfinite(turns)) {
+            lon = ff_add(lon, -360.f * turns);
+            if (!ff_less(lon, L1, 0.f)) lon = ff_add(lon, -360.f);
+            if (ff_less(lon, L0, 0.f)) lon = ff_add(lon, 360.f);
+        }
+    }
+    if (ff_less(p, g.pmin, g.pmin_lo)) { p.hi = g.pmin; p.lo = g.pmin_lo; }
+    if (ff_greater(p, g.pmax, g.pmax_lo)) { p.hi = g.pmax; p.lo = g.pmax_lo; }
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11) and Box-Muller normals
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// top 23 bits -> (0, 1), exact in float32
+__device__ __forceinline__ float u23(uint32_t x) {
+    return (__uint2float_rn(x >> 9) + 0.5f) * kTwoPow23Inv;
+}
+
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1) {
+    const float r = sqrtf(-2.0f * logf(u23(a)));
+    float s, c;
+    sincospif(2.0f * u23(b), &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
+// ---------------------------------------------------------------------------
+// Met record access
+// ---------------------------------------------------------------------------
+template <int ST> struct RecT;
+template <> struct RecT<MPTRAC_FP32> { using T = float4; };
+template <> struct RecT<MPTRAC_BF16> { using T = uint2; };
+template <> struct RecT<MPTRAC_FP16> { using T = uint2; };
+
+template <int ST> __device__ __forceinline__ float4 decode(typename RecT<ST>::T r);
+template <> __device__ __forceinline__ float4 decode<MPTRAC_FP32>(float4 r) { return r; }
+template <> __device__ __forceinline__ float4 decode<MPTRAC_BF16>(uint2 r) {
+    return make_float4(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xFFFF0000u),
+                       __uint_as_float(r.y << 16), __uint_as_float(r.y & 0xFFFF0000u));
+}
+template <> __device__ __forceinline__ float4 decode<MPTRAC_FP16>(uint2 r) {
+    return make_float4(__half2float(__ushort_as_half((unsigned short)(r.x & 0xFFFFu))),
+                       __half2float(__ushort_as_half((unsigned short)(r.x >> 16))),
+                       __half2float(__ushort_as_half((unsigned short)(r.y & 0xFFFFu))),
+                       __half2float(__ushort_as_half((unsigned short)(r.y >> 16))));
+}
+
+template <typename T> __device__ __forceinline__ T ldg_rec(const T* p) { return __ldg(p); }
+
+// Shared-memory tables of one block.
+struct Smem {
+    float plev[kMaxNZ];
+    float inv_dp[kMaxNZ];
+    int16_t kguess[kGuessBins];
+    float sc[2][3][kMaxNZ];   // scales of u, v, omega for slot 0 / 1 (16-bit storage)
+};
+
+// Cell of a point: column record offsets of the 4 corner columns, lower level,
+// fractions.  All indices are clamped into the grid whatever the input.
+struct Cell {
+    int c00, c01, c10, c11;   // (j, i), (j, i+1), (j+1, i), (j+1, i+1)   [record index]
+    int k;
+    float fx, fy, fz;
+};
+
+__device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.f), 1.f); }
+
+__device__ __forceinline__ Cell locate(float lon, float lat, float p, const Geo& g,
+                                       const Smem& s) {
+    Cell c;
+    const float x = (lon - g.lon0) * g.inv_dlon;
+    const float xf = floorf(x);
+    int i = (int)xf;
+    if (i >= g.nx) i -= g.nx;
+    if (i < 0) i += g.nx;
+    i = min(max(i, 0), g.nx - 1);
+    const int i1 = (i + 1 == g.nx) ? 0 : i + 1;
+    c.fx = clamp01(x - xf);
+
+    const float y = (lat - g.lat0) * g.inv_dlat;
+    int j = (int)floorf(y);
+    j = min(max(j, 0), g.ny - 2);
+    c.fy = clamp01(y - (float)j);
+
+    const float pc = fminf(fmaxf(p, g.pmin), g.pmax);
+    int b = (int)((__logf(pc) - g.lnp_top) * g.inv_dln);
+    b = min(max(b, 0), g.nbins - 1);
+    int k = s.kguess[b];
+    while (k > 0 && s.plev[k] < pc) --k;
+    while (k < g.nz - 2 && s.plev[k + 1] >= pc) ++k;
+    c.k = k;
+    c.fz = clamp01((s.plev[k] - pc) * s.inv_dp[k]);
+
+    const int row0 = j * g.nx, row1 = row0 + g.nx;
+    c.c00 = (row0 + i) * g.nz;
+    c.c01 = (row0 + i1) * g.nz;
+    c.c10 = (row1 + i) * g.nz;
+    c.c11 = (row1 + i1) * g.nz;
+    return c;
+}
+
+struct Wind {
+    float u, v, w;
+};
+
+// Trilinear interpolation of (u, v, omega) on one snapshot, optionally with
+// the population variance of the 8 corner values of each variable.
+template <int ST, bool SIG>
+__device__ __forceinline__ void interp_slot(const void* recv, const float* sc, const Cell& c,
+                                            int nz, Wind& out, Wind& var) {
+    using R = typename RecT<ST>::T;
+    const R* rec = static_cast<const R*>(recv);
+    R r[8];
+    r[0] = ldg_rec(rec + c.c00 + c.k);
+    r[1] = ldg_rec(rec + c.c01 + c.k);
+    r[2] = ldg_rec(rec + c.c10 + c.k);
+    r[3] = ldg_rec(rec + c.c11 + c.k);
+    r[4] = ldg_rec(rec + c.c00 + c.k + 1);
+    r[5] = ldg_rec(rec + c.c01 + c.k + 1);
+    r[6] = ldg_rec(rec + c.c10 + c.k + 1);
+    r[7] = ldg_rec(rec + c.c11 + c.k + 1);
+    float4 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = decode<ST>(r[q]);
+    if (ST != MPTRAC_FP32) {
+        const float su0 = sc[c.k], sv0 = sc[kMaxNZ + c.k], sw0 = sc[2 * kMaxNZ + c.k];
+        const float su1 = sc[c.k + 1], sv1 = sc[kMaxNZ + c.k + 1], sw1 = sc[2 * kMaxNZ + c.k + 1];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            v[q].x *= su0; v[q].y *= sv0; v[q].z *= sw0;
+            v[q + 4].x *= su1; v[q + 4].y *= sv1; v[q + 4].z *= sw1;
+        }
+    }
+    (void)nz;
+    const float fx = c.fx, fy = c.fy, fz = c.fz;
+#define MPTRAC_TRI(comp, dst)                                                        \
+    {                                                                                \
+        const float e0 = fmaf(fx, v[1].comp - v[0].comp, v[0].comp);                 \
+        const float e1 = fmaf(fx, v[3].comp - v[2].comp, v[2].comp);                 \
+        const float e2 = fmaf(fx, v[5].comp - v[4].comp, v[4].comp);                 \
+        const float e3 = fmaf(fx, v[7].comp - v[6].comp, v[6].comp);                 \
+        const float s0 = fmaf(fy, e1 - e0, e0);                                      \
+        const float s1 = fmaf(fy, e3 - e2, e2);                                      \
+        dst = fmaf(fz, s1 - s0, s0);                                                 \
+    }
+    MPTRAC_TRI(x, out.u)
+    MPTRAC_TRI(y, out.v)
+    MPTRAC_TRI(z, out.w)
+#undef MPTRAC_TRI
+    if (SIG) {
+#define MPTRAC_VAR(comp, dst)                                                        \
+    {                                                                                \
+        float m = 0.f;                                                               \
+        _Pragma("unroll") for (int q = 0; q < 8; ++q) m += v[q].comp;                \
+        m *= 0.125f;                                                                 \
+        float a = 0.f;                                                               \
+        _Pragma("unroll") for (int q = 0; q < 8; ++q) {                              \
+            const float d = v[q].comp - m;                                           \
+            a = fmaf(d, d, a);                                                       \
+        }                                                                            \
+        dst = a * 0.125f;                                                            \
+    }
+        MPTRAC_VAR(x, var.u)
+        MPTRAC_VAR(y, var.v)
+        MPTRAC_VAR(z, var.w)
+#undef MPTRAC_VAR
+    }
+}
+
+// Wind at a located point and time weight w (0 -> m0, 1 -> m1).
+template <int ST, bool SIG>
+__device__ __forceinline__ void eval_wind(const MetView& m0, const MetView& m1, const Smem& s,
+                                          const Cell& c, float w, int nz, Wind& out, Wind& var) {
+    Wind a, b, va, vb;
+    interp_slot<ST, SIG>(m0.rec, &s.sc[0][0][0], c, nz, a, va);
+    interp_slot<ST, SIG>(m1.rec, &s.sc[1][0][0], c, nz, b, vb);
+    out.u = fmaf(w, b.u - a.u, a.u);
+    out.v = fmaf(w, b.v - a.v, a.v);
+    out.w = fmaf(w, b.w - a.w, a.w);
+    if (SIG) {
+        var.u = fmaf(w, vb.u - va.u, va.u);
+        var.v = fmaf(w, vb.v - va.v, va.v);
+        var.w = fmaf(w, vb.w - va.w, va.w);
+    }
+}
+
+__device__ __forceinline__ void load_tables(Smem& s, const Geo& g, const MetView& m0,
+                                            const MetView& m1, bool scales) {
+    for (int q = threadIdx.x; q < g.nz; q += blockDim.x) {
+        s.plev[q] = g.plev[q];
+        s.inv_dp[q] = g.inv_dp[q];
+    }
+    for (int q = threadIdx.x; q < g.nbins; q += blockDim.x) s.kguess[q] = g.kguess[q];
+    if (scales) {
+        for (int q = threadIdx.x; q < 3 * g.nz; q += blockDim.x) {
+            const int var = q / g.nz, k = q - var * g.nz;
+            s.sc[0][var][k] = m0.scales[var * g.nz + k];
+            s.sc[1][var][k] = m1.scales[var * g.nz + k];
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// The particle kernel
+// ---------------------------------------------------------------------------
+template <int ST, int MODE>
+__global__ void __launch_bounds__(kBlock, 2) k_transport(const __grid_constant__ StepArgs a) {
+    __shared__ Smem s;
+    load_tables(s, a.geo, a.m0, a.m1, ST != MPTRAC_FP32);
+    const Geo& g = a.geo;
+    const bool use_meso = (MODE != MODE_ADVECT) && a.meso;
+    const bool use_turb = (MODE != MODE_ADVECT) && a.turb;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < a.n; idx += stride) {
+        int nlo = 0, nhi = a.nsteps;
+        uint32_t rel = 0;
+        if (a.release) {
+            rel = a.release[idx];
+            if (a.win) {
+                if (rel < (uint32_t)a.n_rel) {
+                    const int2 wv = a.win[rel];
+                    nlo = wv.x;
+                    nhi = wv.y;
+                } else {
+                    nlo = nhi = 0;
+                }
+            }
+        }
+        if (nlo >= nhi) continue;
+        ff lon = ff_make(a.lon[idx]);
+        ff lat = ff_make(a.lat[idx]);
+        ff p = ff_make(a.p[idx]);
+        const uint32_t pid = a.id[idx];
+        float up = 0.f, vp = 0.f, wp = 0.f;
+        if (use_meso) {
+            up = a.up[idx];
+            vp = a.vp[idx];
+            wp = a.wp[idx];
+        }
+        for (int sidx = nlo; sidx < nhi; ++sidx) {
+            Wind var{0.f, 0.f, 0.f};
+            if (MODE != MODE_DIFFUSE) {
+                // ---- module_advection: explicit midpoint ----
+                const float w0 = a.wt[2 * sidx], wm = a.wt[2 * sidx + 1];
+                const Cell c1 = locate(lon.hi, lat.hi, p.hi, g, s);
+                Wind V;
+                if (MODE == MODE_STEP && use_meso)
+                    eval_wind<ST, true>(a.m0, a.m1, s, c1, w0, g.nz, V, var);
+                else
+                    eval_wind<ST, false>(a.m0, a.m1, s, c1, w0, g.nz, V, var);
+                const float cl = coslat(lat);
+                ff lon_s = ff_add(lon, a.half_dt * a.kdeg * V.u / cl);
+                ff lat_s = ff_add(lat, a.half_dt * a.kdeg * V.v);
+                ff p_s = ff_add(p, a.half_dt * V.w);
+                position_bc(lon_s, lat_s, p_s, g);
+                const Cell c2 = locate(lon_s.hi, lat_s.hi, p_s.hi, g, s);
+                Wind V2, dummy;
+                eval_wind<ST, false>(a.m0, a.m1, s, c2, wm, g.nz, V2, dummy);
+                const float cl2 = coslat(lat_s);
+                lon = ff_add(lon, a.dt * a.kdeg * V2.u / cl2);
+                lat = ff_add(lat, a.dt * a.kdeg * V2.v);
+                p = ff_add(p, a.dt * V2.w);
+            } else if (use_meso) {
+                const float w0 = a.wt[2 * sidx];
+                const Cell c1 = locate(lon.hi, lat.hi, p.hi, g, s);
+                Wind V;
+                eval_wind<ST, true>(a.m0, a.m1, s, c1, w0, g.nz, V, var);
+            }
+            if (MODE != MODE_ADVECT && (use_turb || use_meso)) {
+                // ---- module_diffusion_turb / module_diffusion_meso ----
+                const uint32_t step = (uint32_t)(a.step0 + (uint64_t)sidx);
+                float dxm = 0.f, dym = 0.f, dpp = 0.f;
+                if (use_turb) {
+                    const uint4 wd = philox4x32_10(make_uint4(pid, step, 0u, rel), a.key0, a.key1);
+                    float z0, z1, z2, z3;
+                    box_muller(wd.x, wd.y, z0, z1);
+                    box_muller(wd.z, wd.w, z2, z3);
+                    dxm = a.sh * z0;
+                    dym = a.sh * z1;
+                    dpp = -p.hi * (a.sv * z2) * a.inv_H;
+                }
+                if (use_meso) {
+                    const uint4 wd = philox4x32_10(make_uint4(pid, step, 1u, rel), a.key0, a.key1);
+                    float m0, m1, m2, m3;
+                    box_muller(wd.x, wd.y, m0, m1);
+                    box_muller(wd.z, wd.w, m2, m3);
+                    up = fmaf(a.r_ar, up, a.a_ar * sqrtf(var.u) * m0);
+                    vp = fmaf(a.r_ar, vp, a.a_ar * sqrtf(var.v) * m1);
+                    wp = fmaf(a.r_ar, wp, a.a_ar * sqrtf(var.w) * m2);
+                    dxm += up * a.dt;
+                    dym += vp * a.dt;
+                    dpp += wp * a.dt;
+                }
+                const float c3 = coslat(lat);
+                lon = ff_add(lon, dxm * a.kdeg / c3);
+                lat = ff_add(lat, dym * a.kdeg);
+                p = ff_add(p, dpp);
+            }
+            // ---- module_position ----
+            position_bc(lon, lat, p, g);
+        }
+        a.lon[idx] = ff_val(lon);
+        a.lat[idx] = ff_val(lat);
+        a.p[idx] = ff_val(p);
+        if (use_meso) {
+            a.up[idx] = up;
+            a.vp[idx] = vp;
+            a.wp[idx] = wp;
+        }
+    }
+}
+
+// Release windows: for each release the contiguous range [lo, hi) of local
+// steps (n_begin + n) whose time t + (n_begin + n) dt lies in [t_start, t_end).  Same float64
+// expression as the host-side definition (no fused multiply-add).
+__global__ void k_windows(const double* ts, const double* te, int nrel, double t, double dt,
+                          int n_begin, int nsteps, int2* out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrel) return;
+    const double a = ts[r], b = te[r];
+    int lo = -1, hi = -1;
+    for (int n = 0; n < nsteps; ++n) {
+        const double tn = __dadd_rn(t, __dmul_rn((double)(n_begin + n), dt));
+        if (tn >= a && tn < b) {
+            if (lo < 0) lo = n;
+            hi = n + 1;
+        }
+    }
+    out[r] = (lo < 0) ? make_int2(0, 0) : make_int2(lo, hi);
+}
+
+template <int ST>
+__global__ void __launch_bounds__(kBlock) k_interp(Geo g, MetView m0, MetView m1, float w,
+                                                   int64_t n, const double* lon,
+                                                   const double* lat, const double* p,
+                                                   float* ou, float* ov, float* ow,
+                                                   float* ovar) {
+    __shared__ Smem s;
+    load_tables(s, g, m0, m1, ST != MPTRAC_FP32);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
+        const Cell c = locate(ff_make(lon[idx]).hi, ff_make(lat[idx]).hi, ff_make(p[idx]).hi, g, s);
+        Wind V, var;
+        eval_wind<ST, true>(m0, m1, s, c, w, g.nz, V, var);
+        ou[idx] = V.u;
+        ov[idx] = V.v;
+        ow[idx] = V.w;
+        if (ovar) {
+            ovar[idx] = var.u;
+            ovar[n + idx] = var.v;
+            ovar[2 * n + idx] = var.w;
+        }
+    }
+}
+
+__global__ void k_philox(const uint32_t* ctr, int64_t n, uint32_t k0, uint32_t k1,
+                         uint32_t* out, float* normals) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint4 c = make_uint4(ctr[i], ctr[n + i], ctr[2 * n + i], ctr[3 * n + i]);
+        const uint4 wd = philox4x32_10(c, k0, k1);
+        out[i] = wd.x;
+        out[n + i] = wd.y;
+        out[2 * n + i] = wd.z;
+        out[3 * n + i] = wd.w;
+        if (normals) {
+            float z0, z1, z2, z3;
+            box_muller(wd.x, wd.y, z0, z1);
+            box_muller(wd.z, wd.w, z2, z3);
+            normals[i] = z0;
+            normals[n + i] = z1;
+            normals[2 * n + i] = z2;
+            normals[3 * n + i] = z3;
+        }
+    }
+}
+
+int grid_for(int64_t n) {
+    int64_t b = (n + kBlock - 1) / kBlock;
+    if (b < 1) b = 1;
+    if (b > (1 << 20)) b = 1 << 20;
+    return (int)b;
+}
+
+template <int ST>
+cudaError_t launch_transport_st(int mode, const StepArgs& a, int grid, cudaStream_t s) {
+    switch (mode) {
+        case MODE_ADVECT: k_transport<ST, MODE_ADVECT><<<grid, kBlock, 0, s>>>(a); break;
+        case MODE_DIFFUSE: k_transport<ST, MODE_DIFFUSE><<<grid, kBlock, 0, s>>>(a); break;
+        default: k_transport<ST, MODE_STEP><<<grid, kBlock, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_transport(int storage, int mode, const StepArgs& a, int grid, cudaStream_t s) {
+    if (grid <= 0) grid = grid_for(a.n);
+    note_launches(1);
+    switch (storage) {
+        case MPTRAC_FP32: return launch_transport_st<MPTRAC_FP32>(mode, a, grid, s);
+        case MPTRAC_BF16: return launch_transport_st<MPTRAC_BF16>(mode, a, grid, s);
+        default: return launch_transport_st<MPTRAC_FP16>(mode, a, grid, s);
+    }
+}
+
+cudaError_t launch_windows(const double* ts, const double* te, int nrel, double t, double dt,
+                           int n_begin, int nsteps, int2* out, cudaStream_t s) {
+    note_launches(1);
+    k_windows<<<(nrel + 127) / 128, 128, 0, s>>>(ts, te, nrel, t, dt, n_begin, nsteps, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interp(int storage, const Geo& g, MetView m0, MetView m1, float w, int64_t n,
+                          const double* lon, const double* lat, const double* p, float* ou,
+                          float* ov, float* ow, float* ovar, cudaStream_t s) {
+    const int grid = grid_for(n);
+    note_launches(1);
+    switch (storage) {
+        case MPTRAC_FP32:
+            k_interp<MPTRAC_FP32><<<grid, kBlock, 0, s>>>(g, m0, m1, w, n, lon, lat, p, ou, ov, ow, ovar);
+            break;
+        case MPTRAC_BF16:
+            k_interp<MPTRAC_BF16><<<grid, kBlock, 0, s>>>(g, m0, m1, w, n, lon, lat, p, ou, ov, ow, ovar);
+            break;
+        default:
+            k_interp<MPTRAC_FP16><<<grid, kBlock, 0, s>>>(g, m0, m1, w, n, lon, lat, p, ou, ov, ow, ovar);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, int64_t n, uint32_t k0, uint32_t k1, uint32_t* out,
+                          float* normals, cudaStream_t s) {
+    note_launches(1);
+    k_philox<<<grid_for(n), kBlock, 0, s>>>(ctr, n, k0, k1, out, normals);
+    return cudaGetLastError();
+}
+
+}  // namespace mptrac

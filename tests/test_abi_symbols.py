@@ -1,0 +1,63 @@
+"""The C-ABI library builds, loads and exports every symbol include/mptrac.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "mptrac.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mptrac_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2211_12616_gb300 as M
+    return M.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/mptrac.h but not exported"
+
+
+def test_binding_covers_header():
+    import paper_2211_12616_gb300 as M
+    assert sorted(M.SIGNATURES) == _declared()
+
+
+def test_no_gpu_calls_fail_cleanly(lib):
+    """Without a CUDA device the library reports an error status instead of crashing."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import numpy as np
+    import paper_2211_12616_gb300 as M
+    from workloads import grid_2deg_20lev
+    with pytest.raises(M.MptracError) as ei:
+        M.Context(grid_2deg_20lev())
+    assert ei.value.code in (-3, -2)
+    assert lib.mptrac_last_error(None)
+
+
+def test_invalid_grid_rejected_on_host(lib):
+    import numpy as np
+    import paper_2211_12616_gb300 as M
+    from paper_2211_12616_gb300._native import GridDesc
+    plev = np.array([1e5, 5e4, 6e4])   # not decreasing
+    gd = GridDesc(10, 5, 3, 0.0, 36.0, -90.0, 45.0, plev.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0, 3)
+    h = ctypes.c_void_p()
+    assert lib.mptrac_init_grid(ctypes.byref(h), ctypes.byref(gd)) == -1
+    assert b"decreasing" in lib.mptrac_last_error(None)
+    gd = GridDesc(10, 5, 3, 0.0, 30.0, -90.0, 45.0, plev.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0, 3)
+    assert lib.mptrac_init_grid(ctypes.byref(h), ctypes.byref(gd)) == -1
+    assert lib.mptrac_sort_workspace_bytes(None, 1000) >= 60 * 1000
+    assert lib.mptrac_destroy(None) == 0

@@ -1,0 +1,189 @@
+"""Trajectory parity of the advect / diffuse / step kernels against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import met as omet
+from oracle import sort as osort
+from oracle import transport as tr
+from workloads import (cfg1_snapshot, column_releases, fourier_modes, fourier_snapshot,
+                       grid_2deg_20lev, grid_global, uniform_particles)
+
+from _gpu_common import M, TOL_DEG, TOL_P, assert_positions_close, by_id, make_ctx  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+T6H = 21600.0
+
+
+@pytest.fixture(scope="module")
+def cfg1(M):
+    grid = grid_2deg_20lev()
+    snap = cfg1_snapshot(grid)
+    ctx = make_ctx(M, grid, [snap, snap], [0.0, T6H])
+    met = tr.Met(grid, 0.0, snap, T6H, snap)
+    return grid, ctx, met
+
+
+def test_cfg1_advect_120_steps_within_tolerance(M, cfg1):
+    """2 degree analytic case, 1e4 particles, dt = 180 s, 120 steps."""
+    grid, ctx, met = cfg1
+    st0 = uniform_particles(10_000, grid.plev, seed=1)
+    parts = M.Particles.from_numpy(st0)
+    ctx.advect(parts, 0.0, 180.0, 120)
+    torch.cuda.synchronize()
+    got = parts.to_numpy()
+    ref = tr.advect(met, st0, 0.0, 180.0, 120)
+    assert_positions_close(got, ref, what="cfg1 advect")
+    np.testing.assert_array_equal(got["id"], st0["id"])
+
+
+def test_chunked_launches_equal_single(M, cfg1):
+    """200 steps (two kernel launches internally) and 3 x ~67 steps agree with the oracle."""
+    grid, ctx, met = cfg1
+    st0 = uniform_particles(3001, grid.plev, seed=11)
+    a = M.Particles.from_numpy(st0)
+    b = M.Particles.from_numpy(st0)
+    ctx.load_met(1, 2 * T6H, *(torch.from_numpy(v).cuda() for v in cfg1_snapshot(grid).values()))
+    ctx.advect(a, 0.0, 180.0, 200)
+    for t0, n in ((0.0, 67), (67 * 180.0, 67), (134 * 180.0, 66)):
+        ctx.advect(b, t0, 180.0, n)
+    torch.cuda.synchronize()
+    met2 = tr.Met(grid, 0.0, met.f0, 2 * T6H, met.f1)
+    ref = tr.advect(met2, st0, 0.0, 180.0, 200)
+    assert_positions_close(a.to_numpy(), ref, what="200 steps single")
+    assert_positions_close(b.to_numpy(), ref, what="200 steps chunked")
+    ctx.load_met(1, T6H, *(torch.from_numpy(v).cuda() for v in cfg1_snapshot(grid).values()))
+
+
+@pytest.fixture(scope="module")
+def fourier(M):
+    grid = grid_global(120, 61, 30)
+    m = fourier_modes(2)
+    f0 = fourier_snapshot(grid, m, 0.0)
+    f1 = fourier_snapshot(grid, m, T6H)
+    return grid, f0, f1
+
+
+@pytest.mark.parametrize("storage", [omet.FP32, omet.BF16, omet.FP16])
+@pytest.mark.parametrize("mode", ["advect", "diffuse", "step"])
+def test_fourier_modes_parity(M, fourier, storage, mode):
+    grid, f0, f1 = fourier
+    ctx = make_ctx(M, grid, [f0, f1], [0.0, T6H], storage=storage)
+    met = tr.Met(grid, 0.0, omet.stored_fields(f0, storage), T6H, omet.stored_fields(f1, storage))
+    st0 = uniform_particles(20_000, grid.plev, seed=3)
+    parts = M.Particles.from_numpy(st0)
+    prm = M.DiffParams()
+    t, dt, ns = 3600.0, 180.0, 20
+    if mode == "advect":
+        ctx.advect(parts, t, dt, ns)
+        ref = tr.advect(met, st0, t, dt, ns)
+    elif mode == "diffuse":
+        ctx.diffuse(parts, t, dt, prm, 99, 40, ns)
+        ref = tr.diffuse(met, st0, t, dt, tr.DiffParams(), 99, 40, ns)
+    else:
+        ctx.step(parts, t, dt, prm, 99, 40, ns)
+        ref = tr.step(met, st0, t, dt, tr.DiffParams(), 99, 40, ns)
+    torch.cuda.synchronize()
+    got = parts.to_numpy()
+    assert_positions_close(got, ref, what=f"{mode} storage {storage}")
+    if mode != "advect":
+        for k in ("up", "vp", "wp"):
+            scale = np.abs(ref[k]).max() + 1e-30
+            assert np.abs(got[k] - ref[k]).max() <= 1e-4 * scale, k
+
+
+def test_release_windows(M, fourier):
+    grid, f0, f1 = fourier
+    ctx = make_ctx(M, grid, [f0, f1], [0.0, T6H])
+    met = tr.Met(grid, 0.0, f0, T6H, f1)
+    rel = column_releases(16, seed=4, count_scale=2e-3)
+    st0 = rel.particles
+    ts = np.linspace(0, 3000, 16)
+    te = ts + np.linspace(500, 4000, 16)
+    ts[3], te[3] = 1e9, 2e9             # never active
+    ctx.set_releases(ts, te)
+    parts = M.Particles.from_numpy(st0)
+    prm = M.DiffParams()
+    ctx.step(parts, 0.0, 180.0, prm, 5, 0, 30)
+    torch.cuda.synchronize()
+    ref = tr.step(met, st0, 0.0, 180.0, tr.DiffParams(), 5, 0, 30, windows=(ts, te))
+    got = parts.to_numpy()
+    assert_positions_close(got, ref, what="release windows")
+    still = st0["release"] == 3
+    np.testing.assert_array_equal(got["lon"][still], st0["lon"][still])
+    ctx.set_releases([], [])
+
+
+def test_fused_identities(M, fourier):
+    grid, f0, f1 = fourier
+    ctx = make_ctx(M, grid, [f0, f1], [0.0, T6H])
+    st0 = uniform_particles(5000, grid.plev, seed=8)
+    a, b = M.Particles.from_numpy(st0), M.Particles.from_numpy(st0)
+    off = M.DiffParams(turb=False, meso=False)
+    ctx.advect(a, 0.0, 180.0, 15)
+    ctx.step(b, 0.0, 180.0, off, 1, 0, 15)
+    torch.cuda.synchronize()
+    for k in ("lon", "lat", "p"):
+        np.testing.assert_array_equal(getattr(a, k).cpu().numpy(), getattr(b, k).cpu().numpy())
+    zero = {k: np.zeros_like(v) for k, v in f0.items()}
+    ctx0 = make_ctx(M, grid, [zero, zero], [0.0, T6H])
+    c, d = M.Particles.from_numpy(st0), M.Particles.from_numpy(st0)
+    prm = M.DiffParams(meso=False)
+    ctx0.diffuse(c, 0.0, 180.0, prm, 3, 0, 15)
+    ctx0.step(d, 0.0, 180.0, prm, 3, 0, 15)
+    torch.cuda.synchronize()
+    for k in ("lon", "lat", "p"):
+        np.testing.assert_allclose(getattr(c, k).cpu().numpy(), getattr(d, k).cpu().numpy(), rtol=1e-12, atol=1e-9)
+
+
+def test_sort_invariance_bit_exact(M, fourier):
+    """step(sort(P)) == sort(step(P)) exactly: results depend on particle id, not slot."""
+    grid, f0, f1 = fourier
+    ctx = make_ctx(M, grid, [f0, f1], [0.0, T6H])
+    st0 = uniform_particles(30_000, grid.plev, seed=9)
+    a, b = M.Particles.from_numpy(st0), M.Particles.from_numpy(st0)
+    prm = M.DiffParams()
+    ctx.sort(a)
+    ctx.step(a, 0.0, 180.0, prm, 17, 0, 20)
+    ctx.step(b, 0.0, 180.0, prm, 17, 0, 20)
+    ctx.sort(b)
+    torch.cuda.synchronize()
+    ga, gb = by_id(a.to_numpy()), by_id(b.to_numpy())
+    for k in ("lon", "lat", "p", "up", "vp", "wp"):
+        np.testing.assert_array_equal(ga[k], gb[k])
+
+
+@pytest.mark.parametrize("n", [0, 1, 255, 257])
+def test_small_and_ragged_counts(M, cfg1, n):
+    grid, ctx, met = cfg1
+    st0 = uniform_particles(n, grid.plev, seed=12)
+    parts = M.Particles.from_numpy(st0)
+    ctx.step(parts, 0.0, 180.0, M.DiffParams(), 1, 0, 12)
+    torch.cuda.synchronize()
+    if n:
+        ref = tr.step(met, st0, 0.0, 180.0, tr.DiffParams(), 1, 0, 12)
+        assert_positions_close(parts.to_numpy(), ref, what=f"n={n}")
+
+
+def test_host_validation_errors(M, cfg1):
+    grid, ctx, met = cfg1
+    st0 = uniform_particles(10, grid.plev, seed=2)
+    parts = M.Particles.from_numpy(st0)
+    with pytest.raises(M.MptracError) as e:
+        ctx.advect(parts, 0.0, 180.0, 121)       # leaves [0, 6 h]
+    assert e.value.code == -4
+    with pytest.raises(M.MptracError) as e:
+        ctx.advect(parts, 0.0, -1.0, 1)
+    assert e.value.code == -1
+    noms = M.Particles.from_numpy(st0, meso=False)
+    with pytest.raises(M.MptracError) as e:
+        ctx.step(noms, 0.0, 180.0, M.DiffParams(), 1, 0, 1)
+    assert e.value.code == -1
+    host = M.Particles(*(torch.from_numpy(np.ascontiguousarray(v)) for v in
+                         (st0["lon"], st0["lat"], st0["p"], st0["id"].view(np.int32))))
+    with pytest.raises(M.MptracError) as e:
+        ctx.advect(host, 0.0, 180.0, 1)
+    assert e.value.code == -1
+    ctx.advect(parts, 0.0, 180.0, 0)             # no steps: no-op
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(parts.lon.cpu().numpy(), st0["lon"])
