@@ -72,11 +72,28 @@ def trilinear(f, loc):
     return s0 * (1 - fz) + s1 * fz
 
 
+def corner_weights(loc):
+    """Trilinear weights of the 8 corners, shape (8, n), same order as ``corners``."""
+    _, _, _, _, fx, fy, fz = loc
+    out = []
+    for wk in (1 - fz, fz):
+        for wj in (1 - fy, fy):
+            for wi in (1 - fx, fx):
+                out.append(wk * wj * wi)
+    return np.stack(out)
+
+
 def corner_variance(f, loc):
-    """Population variance of the 8 corner values of each particle's cell."""
+    """Subgrid variance: corner values' spread about the interpolated value,
+    weighted by the interpolation weights,  sum_c w_c (f_c - sum_c' w_c' f_c')^2.
+
+    At a cell face the weights of the far corners vanish, so the variance is
+    continuous across faces (both neighbouring cells give the same value).
+    """
     c = corners(f, loc)
-    m = c.mean(axis=0)
-    return ((c - m) ** 2).mean(axis=0)
+    w = corner_weights(loc)
+    m = (w * c).sum(axis=0)
+    return (w * (c - m) ** 2).sum(axis=0)
 
 
 def time_weight(t, t0, t1):

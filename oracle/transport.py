@@ -20,8 +20,10 @@ design notes of the repository):
   dp = -p dz / H with H = 7000 m.
 * Mesoscale diffusion: a per-particle AR(1) wind perturbation
   u' <- r u' + sqrt(1 - r^2) f sigma_u xi with r = 1 - 2 dt / (t1 - t0)
-  (clamped to [0, 1]) and sigma_u^2 the time-weighted population variance of
-  the 8 cell-corner values of u on the two snapshots; same for v and omega.
+  (clamped to [0, 1]) and sigma_u^2 the subgrid variance of u: on each
+  snapshot the spread of the 8 cell-corner values about the interpolated
+  value, weighted by the interpolation weights (continuous across cell
+  faces), then interpolated linearly in time; same for v and omega.
   The displacement is u' dt (converted like advection).  The corners are those
   of the first wind evaluation of the step (at x_n, t_n).
 * Diffusion displacements (turbulent + mesoscale) are converted at the

@@ -113,5 +113,37 @@ def test_corner_variance():
     const = np.full((4, 5, 8), 3.0)
     loc = interp.locate(grid, np.array([17.0]), np.array([10.0]), np.array([60000.0]))
     assert interp.corner_variance(const, loc)[0] == 0.0
-    chk = np.fromfunction(lambda k, j, i: np.where(i % 2 == 0, 1.0, -1.0), (4, 5, 8))
-    assert abs(interp.corner_variance(chk * 2.5, loc)[0] - 6.25) < 1e-14
+    # checkerboard +-A along longitude: w-weighted spread = 4 A^2 fx (1 - fx)
+    A = 2.5
+    chk = np.fromfunction(lambda k, j, i: np.where(i % 2 == 0, A, -A), (4, 5, 8))
+    for lon in (45.0, 50.0, 60.0, 67.5, 89.0):
+        loc = interp.locate(grid, np.array([lon]), np.array([10.0]), np.array([60000.0]))
+        fx = loc[4][0]
+        assert abs(interp.corner_variance(chk, loc)[0] - 4 * A * A * fx * (1 - fx)) < 1e-12
+
+
+def test_corner_variance_continuous_across_faces():
+    """Both cells sharing a face give the same variance on it."""
+    grid = grid_2deg_20lev()
+    rng = np.random.default_rng(7)
+    f = rng.standard_normal((grid.nz, grid.ny, grid.nx))
+    eps = 1e-9
+    lat = rng.uniform(-80, 80, 200)
+    p = rng.uniform(2e3, 9e4, 200)
+    face_lon = 2.0 * rng.integers(1, 170, 200)
+    a = interp.corner_variance(f, interp.locate(grid, face_lon - eps, lat, p))
+    b = interp.corner_variance(f, interp.locate(grid, face_lon + eps, lat, p))
+    np.testing.assert_allclose(a, b, atol=1e-6)
+    face_lat = -80.0 + 2.0 * rng.integers(1, 79, 200)
+    lon = rng.uniform(0, 358, 200)
+    a = interp.corner_variance(f, interp.locate(grid, lon, face_lat - eps, p))
+    b = interp.corner_variance(f, interp.locate(grid, lon, face_lat + eps, p))
+    np.testing.assert_allclose(a, b, atol=1e-6)
+    # brute force at one point: weighted spread about the weighted mean
+    loc = interp.locate(grid, np.array([33.3]), np.array([-12.7]), np.array([41234.0]))
+    w = interp.corner_weights(loc)[:, 0]
+    c = interp.corners(f, loc)[:, 0]
+    assert abs(w.sum() - 1) < 1e-15
+    m = sum(wi * ci for wi, ci in zip(w, c))
+    ref = sum(wi * (ci - m) ** 2 for wi, ci in zip(w, c))
+    assert abs(interp.corner_variance(f, loc)[0] - ref) < 1e-13
