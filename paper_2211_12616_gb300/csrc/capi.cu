@@ -225,7 +225,8 @@ int mptrac_init_grid(mptrac_ctx** out, const mptrac_grid_desc* g) {
         return fail(MPTRAC_E_INVALID_ARG, "bad grid spacing or origin");
     if (std::fabs(g->nx * g->dlon - 360.0) > 1e-9 * 360.0)
         return fail(MPTRAC_E_INVALID_ARG, "nx * dlon = %.12g, must be 360 (periodic longitude)", g->nx * g->dlon);
-    if ((double)(float)g->lon0 != g->lon0) return fail(MPTRAC_E_INVALID_ARG, "lon0 must be exactly representable in float32");
+    if ((double)(float)g->lon0 != g->lon0 || (double)(float)g->lat0 != g->lat0)
+        return fail(MPTRAC_E_INVALID_ARG, "lon0 and lat0 must be exactly representable in float32");
     if (g->storage < MPTRAC_FP32 || g->storage > MPTRAC_FP16) return fail(MPTRAC_E_INVALID_ARG, "unknown storage %d", g->storage);
     if (g->nvars != 3 && g->nvars != 4) return fail(MPTRAC_E_INVALID_ARG, "nvars must be 3 or 4");
     if (!g->plev) return fail(MPTRAC_E_INVALID_ARG, "plev is NULL");
@@ -303,6 +304,7 @@ int mptrac_init_grid(mptrac_ctx** out, const mptrac_grid_desc* g) {
     G.inv_dlon = (float)(1.0 / g->dlon);
     G.lat0 = (float)g->lat0;
     G.inv_dlat = (float)(1.0 / g->dlat);
+    G.inv_dlat_lo = (float)(1.0 / g->dlat - (double)G.inv_dlat);
     const double pmin = g->plev[nz - 1], pmax = g->plev[0];
     G.pmin = (float)pmin;
     G.pmin_lo = (float)(pmin - (double)G.pmin);

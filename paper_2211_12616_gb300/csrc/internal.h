@@ -18,7 +18,7 @@ constexpr int kBlock = 256;               // threads per block of the particle k
 // Grid geometry as the kernels see it.
 struct Geo {
     int nx, ny, nz, nbins;
-    float lon0, inv_dlon, lat0, inv_dlat;
+    float lon0, inv_dlon, lat0, inv_dlat, inv_dlat_lo;   // 1/dlat as float-float (hi, lo)
     float pmin, pmax;             // level range (float)
     float pmin_lo, pmax_lo;       // pmin = pmin + pmin_lo exactly as float-float
     float lnp_top, inv_dln;       // ln(p) bin origin and inverse width

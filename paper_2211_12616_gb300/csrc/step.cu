@@ -157,17 +157,21 @@ struct Smem {
 };
 
 // Cell of a point: column record offsets of the 4 corner columns, lower level,
-// fractions.  All indices are clamped into the grid whatever the input.
+// and the interpolation weights as (f, g = 1 - f) pairs.  All indices are
+// clamped into the grid whatever the input.
 struct Cell {
     int c00, c01, c10, c11;   // (j, i), (j, i+1), (j+1, i), (j+1, i+1)   [record index]
     int k;
-    float fx, fy, fz;
+    float fx, gx, fy, gy, fz, gz;
 };
 
 __device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.f), 1.f); }
 
-__device__ __forceinline__ Cell locate(float lon, float lat, float p, const Geo& g,
-                                       const Smem& s) {
+// The latitude fraction is formed in float-float and both weights are
+// computed directly, so that next to a pole the small weight keeps its
+// relative precision (winds there vanish like the distance to the pole while
+// the longitude increment divides by cos(lat)).
+__device__ __forceinline__ Cell locate(float lon, ff lat, float p, const Geo& g, const Smem& s) {
     Cell c;
     const float x = (lon - g.lon0) * g.inv_dlon;
     const float xf = floorf(x);
@@ -177,11 +181,18 @@ __device__ __forceinline__ Cell locate(float lon, float lat, float p, const Geo&
     i = min(max(i, 0), g.nx - 1);
     const int i1 = (i + 1 == g.nx) ? 0 : i + 1;
     c.fx = clamp01(x - xf);
+    c.gx = 1.f - c.fx;
 
-    const float y = (lat - g.lat0) * g.inv_dlat;
-    int j = (int)floorf(y);
+    // y = (lat - lat0) / dlat as float-float (yh + ye)
+    const ff d = ff_add(lat, -g.lat0);
+    const float yh = d.hi * g.inv_dlat;
+    float ye = fmaf(d.hi, g.inv_dlat, -yh);
+    ye = fmaf(d.hi, g.inv_dlat_lo, ye);
+    ye = fmaf(d.lo, g.inv_dlat, ye);
+    int j = (int)floorf(yh);
     j = min(max(j, 0), g.ny - 2);
-    c.fy = clamp01(y - (float)j);
+    c.fy = clamp01(__fadd_rn(__fsub_rn(yh, (float)j), ye));
+    c.gy = clamp01(__fsub_rn(__fsub_rn((float)(j + 1), yh), ye));
 
     const float pc = fminf(fmaxf(p, g.pmin), g.pmax);
     int b = (int)((__logf(pc) - g.lnp_top) * g.inv_dln);
@@ -191,6 +202,7 @@ __device__ __forceinline__ Cell locate(float lon, float lat, float p, const Geo&
     while (k < g.nz - 2 && s.plev[k + 1] >= pc) ++k;
     c.k = k;
     c.fz = clamp01((s.plev[k] - pc) * s.inv_dp[k]);
+    c.gz = 1.f - c.fz;
 
     const int row0 = j * g.nx, row1 = row0 + g.nx;
     c.c00 = (row0 + i) * g.nz;
@@ -205,10 +217,11 @@ struct Wind {
 };
 
 // Trilinear interpolation of (u, v, omega) on one snapshot, optionally with
-// the population variance of the 8 corner values of each variable.
+// the subgrid variance: the corner values' spread about the interpolated
+// value, weighted by the interpolation weights.
 template <int ST, bool SIG>
 __device__ __forceinline__ void interp_slot(const void* recv, const float* sc, const Cell& c,
-                                            int nz, Wind& out, Wind& var) {
+                                            Wind& out, Wind& var) {
     using R = typename RecT<ST>::T;
     const R* rec = static_cast<const R*>(recv);
     R r[8];
@@ -232,38 +245,38 @@ __device__ __forceinline__ void interp_slot(const void* recv, const float* sc, c
             v[q + 4].x *= su1; v[q + 4].y *= sv1; v[q + 4].z *= sw1;
         }
     }
-    (void)nz;
-    const float fx = c.fx, fy = c.fy, fz = c.fz;
+    const float fx = c.fx, gx = c.gx, fy = c.fy, gy = c.gy, fz = c.fz, gz = c.gz;
 #define MPTRAC_TRI(comp, dst)                                                        \
     {                                                                                \
-        const float e0 = fmaf(fx, v[1].comp - v[0].comp, v[0].comp);                 \
-        const float e1 = fmaf(fx, v[3].comp - v[2].comp, v[2].comp);                 \
-        const float e2 = fmaf(fx, v[5].comp - v[4].comp, v[4].comp);                 \
-        const float e3 = fmaf(fx, v[7].comp - v[6].comp, v[6].comp);                 \
-        const float s0 = fmaf(fy, e1 - e0, e0);                                      \
-        const float s1 = fmaf(fy, e3 - e2, e2);                                      \
-        dst = fmaf(fz, s1 - s0, s0);                                                 \
+        const float e0 = fmaf(v[1].comp, fx, v[0].comp * gx);                        \
+        const float e1 = fmaf(v[3].comp, fx, v[2].comp * gx);                        \
+        const float e2 = fmaf(v[5].comp, fx, v[4].comp * gx);                        \
+        const float e3 = fmaf(v[7].comp, fx, v[6].comp * gx);                        \
+        const float s0 = fmaf(e1, fy, e0 * gy);                                      \
+        const float s1 = fmaf(e3, fy, e2 * gy);                                      \
+        dst = fmaf(s1, fz, s0 * gz);                                                 \
     }
     MPTRAC_TRI(x, out.u)
     MPTRAC_TRI(y, out.v)
     MPTRAC_TRI(z, out.w)
 #undef MPTRAC_TRI
     if (SIG) {
-#define MPTRAC_VAR(comp, dst)                                                        \
+        float wt[8];
+        const float a00 = gy * gz, a10 = fy * gz, a01 = gy * fz, a11 = fy * fz;
+        wt[0] = gx * a00; wt[1] = fx * a00; wt[2] = gx * a10; wt[3] = fx * a10;
+        wt[4] = gx * a01; wt[5] = fx * a01; wt[6] = gx * a11; wt[7] = fx * a11;
+#define MPTRAC_VAR(comp, mean, dst)                                                  \
     {                                                                                \
-        float m = 0.f;                                                               \
-        _Pragma("unroll") for (int q = 0; q < 8; ++q) m += v[q].comp;                \
-        m *= 0.125f;                                                                 \
-        float a = 0.f;                                                               \
+        float acc = 0.f;                                                             \
         _Pragma("unroll") for (int q = 0; q < 8; ++q) {                              \
-            const float d = v[q].comp - m;                                           \
-            a = fmaf(d, d, a);                                                       \
+            const float d = v[q].comp - mean;                                        \
+            acc = fmaf(wt[q] * d, d, acc);                                           \
         }                                                                            \
-        dst = a * 0.125f;                                                            \
+        dst = acc;                                                                   \
     }
-        MPTRAC_VAR(x, var.u)
-        MPTRAC_VAR(y, var.v)
-        MPTRAC_VAR(z, var.w)
+        MPTRAC_VAR(x, out.u, var.u)
+        MPTRAC_VAR(y, out.v, var.v)
+        MPTRAC_VAR(z, out.w, var.w)
 #undef MPTRAC_VAR
     }
 }
@@ -271,10 +284,10 @@ __device__ __forceinline__ void interp_slot(const void* recv, const float* sc, c
 // Wind at a located point and time weight w (0 -> m0, 1 -> m1).
 template <int ST, bool SIG>
 __device__ __forceinline__ void eval_wind(const MetView& m0, const MetView& m1, const Smem& s,
-                                          const Cell& c, float w, int nz, Wind& out, Wind& var) {
+                                          const Cell& c, float w, Wind& out, Wind& var) {
     Wind a, b, va, vb;
-    interp_slot<ST, SIG>(m0.rec, &s.sc[0][0][0], c, nz, a, va);
-    interp_slot<ST, SIG>(m1.rec, &s.sc[1][0][0], c, nz, b, vb);
+    interp_slot<ST, SIG>(m0.rec, &s.sc[0][0][0], c, a, va);
+    interp_slot<ST, SIG>(m1.rec, &s.sc[1][0][0], c, b, vb);
     out.u = fmaf(w, b.u - a.u, a.u);
     out.v = fmaf(w, b.v - a.v, a.v);
     out.w = fmaf(w, b.w - a.w, a.w);
@@ -344,29 +357,29 @@ __global__ void __launch_bounds__(kBlock, 2) k_transport(const __grid_constant__
             if (MODE != MODE_DIFFUSE) {
                 // ---- module_advection: explicit midpoint ----
                 const float w0 = a.wt[2 * sidx], wm = a.wt[2 * sidx + 1];
-                const Cell c1 = locate(lon.hi, lat.hi, p.hi, g, s);
+                const Cell c1 = locate(lon.hi, lat, p.hi, g, s);
                 Wind V;
                 if (MODE == MODE_STEP && use_meso)
-                    eval_wind<ST, true>(a.m0, a.m1, s, c1, w0, g.nz, V, var);
+                    eval_wind<ST, true>(a.m0, a.m1, s, c1, w0, V, var);
                 else
-                    eval_wind<ST, false>(a.m0, a.m1, s, c1, w0, g.nz, V, var);
+                    eval_wind<ST, false>(a.m0, a.m1, s, c1, w0, V, var);
                 const float cl = coslat(lat);
                 ff lon_s = ff_add(lon, a.half_dt * a.kdeg * V.u / cl);
                 ff lat_s = ff_add(lat, a.half_dt * a.kdeg * V.v);
                 ff p_s = ff_add(p, a.half_dt * V.w);
                 position_bc(lon_s, lat_s, p_s, g);
-                const Cell c2 = locate(lon_s.hi, lat_s.hi, p_s.hi, g, s);
+                const Cell c2 = locate(lon_s.hi, lat_s, p_s.hi, g, s);
                 Wind V2, dummy;
-                eval_wind<ST, false>(a.m0, a.m1, s, c2, wm, g.nz, V2, dummy);
+                eval_wind<ST, false>(a.m0, a.m1, s, c2, wm, V2, dummy);
                 const float cl2 = coslat(lat_s);
                 lon = ff_add(lon, a.dt * a.kdeg * V2.u / cl2);
                 lat = ff_add(lat, a.dt * a.kdeg * V2.v);
                 p = ff_add(p, a.dt * V2.w);
             } else if (use_meso) {
                 const float w0 = a.wt[2 * sidx];
-                const Cell c1 = locate(lon.hi, lat.hi, p.hi, g, s);
+                const Cell c1 = locate(lon.hi, lat, p.hi, g, s);
                 Wind V;
-                eval_wind<ST, true>(a.m0, a.m1, s, c1, w0, g.nz, V, var);
+                eval_wind<ST, true>(a.m0, a.m1, s, c1, w0, V, var);
             }
             if (MODE != MODE_ADVECT && (use_turb || use_meso)) {
                 // ---- module_diffusion_turb / module_diffusion_meso ----
@@ -441,9 +454,9 @@ __global__ void __launch_bounds__(kBlock) k_interp(Geo g, MetView m0, MetView m1
     load_tables(s, g, m0, m1, ST != MPTRAC_FP32);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
-        const Cell c = locate(ff_make(lon[idx]).hi, ff_make(lat[idx]).hi, ff_make(p[idx]).hi, g, s);
+        const Cell c = locate(ff_make(lon[idx]).hi, ff_make(lat[idx]), ff_make(p[idx]).hi, g, s);
         Wind V, var;
-        eval_wind<ST, true>(m0, m1, s, c, w, g.nz, V, var);
+        eval_wind<ST, true>(m0, m1, s, c, w, V, var);
         ou[idx] = V.u;
         ov[idx] = V.v;
         ow[idx] = V.w;

@@ -1,0 +1,69 @@
+"""Full-size parity on sampled particles, in the benchmark's launch configuration.
+
+The benchmark workload (1 degree x 60 levels Fourier-mode wind, 1e6 particles,
+480 fused steps with turbulent + mesoscale diffusion, sort every 20 steps) runs
+on the GPU exactly as bench.py runs it.  Particles are independent, so the
+FP64 oracle can follow a random sample of them one by one over the same 24 h;
+their final states are compared per particle id.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import transport as tr
+from oracle.driver import run_schedule
+from oracle.errors import great_circle_km, lon_diff
+from workloads import fourier_modes, fourier_snapshot, grid_1deg_60lev, uniform_particles
+
+from _gpu_common import M  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+DT, DT_MET, T_END = 180.0, 21600.0, 86400.0
+
+
+def test_bench_workload_sampled_parity(M):
+    from paper_2211_12616_gb300.simulation import Simulation, periodic_snapshots
+    grid = grid_1deg_60lev()
+    modes = fourier_modes(2)
+    snaps = [fourier_snapshot(grid, modes, h * DT_MET, device="cuda", as_numpy=False) for h in range(4)]
+    n = 1_000_000
+    st0 = uniform_particles(n, grid.plev, 2)
+    parts = M.Particles.from_numpy(st0)
+    ctx = M.Context(grid, M.MPTRAC_FP32)
+    sim = Simulation(ctx, periodic_snapshots(snaps, DT_MET), DT_MET, parts, DT, M.DiffParams(), 2, 20)
+    nsteps = sim.run(0.0, T_END)
+    torch.cuda.synchronize()
+    assert nsteps == 480
+    got = parts.to_numpy()
+    # the sorted array is a permutation of the ids
+    assert np.array_equal(np.sort(got["id"]), np.arange(n, dtype=np.uint32))
+    rng = np.random.default_rng(0)
+    ids = np.sort(rng.choice(n, 400, replace=False))
+    sub = {k: v[ids] for k, v in st0.items()}
+    host = [{k: v.cpu().numpy() for k, v in s.items()} for s in snaps]
+    ref = run_schedule(grid, lambda t: host[int(round(t / DT_MET)) % 4], DT_MET, sub, 0.0, T_END, DT,
+                       tr.DiffParams(), 2)
+    pos = np.empty(n, dtype=np.int64)
+    pos[got["id"]] = np.arange(n)
+    g = {k: got[k][pos[ids]] for k in ("lon", "lat", "p", "up")}
+    dkm = great_circle_km(g["lon"], g["lat"], ref["lon"], ref["lat"])
+    dlat = np.abs(g["lat"] - ref["lat"])
+    dlon = np.abs(lon_diff(g["lon"], ref["lon"]))
+    dp = np.abs(g["p"] - ref["p"]) / ref["p"]
+    stats = {"n_sample": int(ids.size), "km_median": float(np.median(dkm)), "km_p99": float(np.quantile(dkm, 0.99)),
+             "km_max": float(dkm.max()), "dlat_max": float(dlat.max()), "dlon_median": float(np.median(dlon)),
+             "dp_rel_median": float(np.median(dp)), "dp_rel_p99": float(np.quantile(dp, 0.99)),
+             "dp_rel_max": float(dp.max())}
+    os.makedirs("gpurun_out", exist_ok=True)
+    with open("gpurun_out/fullsize_parity.json", "w") as f:
+        json.dump(stats, f, indent=1)
+    # 480 float32 steps with diffusion: the median particle stays within 1e-4 deg
+    # (11 m) and 1e-5 relative pressure of the float64 run; the tail is bounded.
+    assert stats["km_median"] < 0.011, stats
+    assert stats["dp_rel_median"] < 1e-5, stats
+    assert stats["km_p99"] < 1.0 and stats["dp_rel_p99"] < 1e-3, stats
+    ctx.close()

@@ -37,22 +37,22 @@ def test_cfg1_advect_120_steps_within_tolerance(M, cfg1):
     np.testing.assert_array_equal(got["id"], st0["id"])
 
 
-def test_chunked_launches_equal_single(M, cfg1):
+def test_chunked_launches_equal_single(M):
     """200 steps (two kernel launches internally) and 3 x ~67 steps agree with the oracle."""
-    grid, ctx, met = cfg1
+    grid = grid_2deg_20lev()
+    snap = cfg1_snapshot(grid)
+    ctx = make_ctx(M, grid, [snap, snap], [0.0, 2 * T6H])
+    met = tr.Met(grid, 0.0, snap, 2 * T6H, snap)
     st0 = uniform_particles(3001, grid.plev, seed=11)
     a = M.Particles.from_numpy(st0)
     b = M.Particles.from_numpy(st0)
-    ctx.load_met(1, 2 * T6H, *(torch.from_numpy(v).cuda() for v in cfg1_snapshot(grid).values()))
     ctx.advect(a, 0.0, 180.0, 200)
     for t0, n in ((0.0, 67), (67 * 180.0, 67), (134 * 180.0, 66)):
         ctx.advect(b, t0, 180.0, n)
     torch.cuda.synchronize()
-    met2 = tr.Met(grid, 0.0, met.f0, 2 * T6H, met.f1)
-    ref = tr.advect(met2, st0, 0.0, 180.0, 200)
+    ref = tr.advect(met, st0, 0.0, 180.0, 200)
     assert_positions_close(a.to_numpy(), ref, what="200 steps single")
     assert_positions_close(b.to_numpy(), ref, what="200 steps chunked")
-    ctx.load_met(1, T6H, *(torch.from_numpy(v).cuda() for v in cfg1_snapshot(grid).values()))
 
 
 @pytest.fixture(scope="module")
