@@ -22,6 +22,7 @@ struct Geo {
     float pmin, pmax;             // level range (float)
     float pmin_lo, pmax_lo;       // pmin = pmin + pmin_lo exactly as float-float
     float lnp_top, inv_dln;       // ln(p) bin origin and inverse width
+    float key_mx, key_my;         // float32 cell-key margins [cells]; > 0.25 disables the fast path
     const float* plev;            // [nz]    float levels
     const float* inv_dp;          // [nz]    1 / (plev[k] - plev[k+1])
     const int16_t* kguess;        // [nbins] first-guess level index per ln(p) bin

@@ -20,8 +20,10 @@ constexpr int kRounds = 8;
 constexpr int kTileKeys = kSortThreads * kRounds;
 constexpr int kRadix = 256;
 
-__device__ __forceinline__ uint32_t cell_key(double lon, double lat, double p, const Geo& g) {
-    // longitude: x = ((lon - lon0) mod 360) / dlon, mod with a non-negative result
+// Cell key from float64 positions, the definition: x = ((lon - lon0) mod 360)
+// / dlon, i = floor(x) mod nx; j = floor((lat - lat0) / dlat) clamped to
+// [0, ny-2]; k = (number of levels >= clamp(p)) - 1 clamped to [0, nz-2].
+__device__ __forceinline__ uint32_t cell_key_f64(double lon, double lat, double p, const Geo& g) {
     double r = fmod(__dsub_rn(lon, g.lon0_d), 360.0);
     if (r < 0.0) r = __dadd_rn(r, 360.0);
     const double x = __ddiv_rn(r, g.dlon_d);
@@ -32,8 +34,7 @@ __device__ __forceinline__ uint32_t cell_key(double lon, double lat, double p, c
     long long j = (long long)floor(y);
     j = j < 0 ? 0 : (j > g.ny - 2 ? g.ny - 2 : j);
     const double pc = fmin(fmax(p, g.pmin_d), g.pmax_d);
-    // k = (number of levels with plev >= pc) - 1, clamped to [0, nz-2]
-    int lo = 0, hi = g.nz;   // plev decreasing: count the prefix with plev >= pc
+    int lo = 0, hi = g.nz;   // plev decreasing: length of the prefix with plev >= pc
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (g.plev_d[mid] >= pc) lo = mid + 1; else hi = mid;
@@ -43,11 +44,61 @@ __device__ __forceinline__ uint32_t cell_key(double lon, double lat, double p, c
     return (uint32_t)((j * g.nx + i) * g.nz + k);
 }
 
+struct KeyTables {
+    float plev[kMaxNZ];
+    int16_t kguess[kGuessBins];
+};
+
+// Same key, computed in float32 when that is provably identical: the float32
+// cell coordinates are within key_mx / key_my cells (a bound derived from the
+// grid on the host, with a factor 8 to spare) and p within ~1e-7 relative of
+// the exact values, so estimates farther than that from every cell face
+// (and p farther than 1e-5 relative from its bracketing levels) have the same
+// floor / level count as the float64 definition.  Anything closer to a face, or outside the regular range, takes
+// the float64 path.
+__device__ __forceinline__ uint32_t cell_key(double lon, double lat, double p, const Geo& g,
+                                             const KeyTables& t) {
+    const float lf = (float)lon, af = (float)lat, pf = (float)p;
+    const float x = (lf - g.lon0) * g.inv_dlon;
+    const float y = (af - g.lat0) * g.inv_dlat;
+    const float xf = floorf(x), yf = floorf(y);
+    const float fx = x - xf, fy = y - yf;
+    const float mx = g.key_mx, my = g.key_my;
+    bool ok = mx < 0.25f && my < 0.25f && (x > mx) && (x < (float)g.nx - mx) && fx > mx && fx < 1.f - mx;
+    int j = (int)yf;
+    if (y < -my) j = 0;                                          // clamped from below whatever the rounding
+    else if (y > (float)(g.ny - 2) + my && y < 1e30f) j = g.ny - 2;  // top cell (clamped)
+    else ok = ok && fy > my && fy < 1.f - my && j >= 0 && j <= g.ny - 2;
+    // level: first guess from the ln(p) table, refined in float32, accepted
+    // only when p is clear of both bracketing levels
+    const float pc = fminf(fmaxf(pf, g.pmin), g.pmax);
+    int b = (int)((__logf(pc) - g.lnp_top) * g.inv_dln);
+    b = min(max(b, 0), g.nbins - 1);
+    int k = t.kguess[b];
+    while (k > 0 && t.plev[k] < pc) --k;
+    while (k < g.nz - 2 && t.plev[k + 1] >= pc) ++k;
+    const bool below_top = pf > g.pmax * (1.f + 1e-5f);     // clamps to level 0
+    const bool above_bot = pf < g.pmin * (1.f - 1e-5f);     // clamps to the top level
+    if (!below_top && !above_bot) {
+        const float margin = 1e-5f * pc;
+        ok = ok && (t.plev[k] - pc > margin || k == 0) && (pc - t.plev[k + 1] > margin || k == g.nz - 2);
+        if (k == 0 && !(pc < t.plev[0] - margin)) ok = false;
+        if (k == g.nz - 2 && !(pc > t.plev[g.nz - 1] + margin)) ok = false;
+    }
+    if (!ok || !(lf == lf) || !(af == af) || !(pf == pf)) return cell_key_f64(lon, lat, p, g);
+    const int i = (int)xf;
+    return (uint32_t)((j * g.nx + i) * g.nz + k);
+}
+
 __global__ void k_keys(Geo g, int64_t n, const double* lon, const double* lat, const double* p,
                        uint32_t* keys, uint32_t* vals) {
+    __shared__ KeyTables t;
+    for (int q = threadIdx.x; q < g.nz; q += blockDim.x) t.plev[q] = g.plev[q];
+    for (int q = threadIdx.x; q < g.nbins; q += blockDim.x) t.kguess[q] = g.kguess[q];
+    __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
-        keys[q] = cell_key(lon[q], lat[q], p[q], g);
+        keys[q] = cell_key(lon[q], lat[q], p[q], g, t);
         if (vals) vals[q] = (uint32_t)q;
     }
 }

@@ -216,85 +216,97 @@ struct Wind {
     float u, v, w;
 };
 
-// Trilinear interpolation of (u, v, omega) on one snapshot, optionally with
-// the subgrid variance: the corner values' spread about the interpolated
-// value, weighted by the interpolation weights.
-template <int ST, bool SIG>
-__device__ __forceinline__ void interp_slot(const void* recv, const float* sc, const Cell& c,
-                                            Wind& out, Wind& var) {
+// The 8 corners of one cell on both snapshots, (u, v, omega) decoded and
+// scaled, kept in registers.  A particle moves about 1/60 of a 1-degree cell
+// per step, so consecutive wind evaluations almost always fall into the cell
+// already held here and need no memory access at all: the gather from L1/L2
+// is paid only when the particle changes cell.
+struct Corners {
+    int col, k;               // cached cell (record index of column (j, i), lower level); col < 0: empty
+    float u[2][8], v[2][8], w[2][8];
+};
+
+// corner order q: bit 0 = i+1, bit 1 = j+1, bit 2 = k+1
+template <int ST>
+__device__ __forceinline__ void fetch_corners(const MetView& m0, const MetView& m1, const Smem& s,
+                                              const Cell& c, Corners& cc) {
     using R = typename RecT<ST>::T;
-    const R* rec = static_cast<const R*>(recv);
-    R r[8];
-    r[0] = ldg_rec(rec + c.c00 + c.k);
-    r[1] = ldg_rec(rec + c.c01 + c.k);
-    r[2] = ldg_rec(rec + c.c10 + c.k);
-    r[3] = ldg_rec(rec + c.c11 + c.k);
-    r[4] = ldg_rec(rec + c.c00 + c.k + 1);
-    r[5] = ldg_rec(rec + c.c01 + c.k + 1);
-    r[6] = ldg_rec(rec + c.c10 + c.k + 1);
-    r[7] = ldg_rec(rec + c.c11 + c.k + 1);
-    float4 v[8];
+    const int base[4] = {c.c00 + c.k, c.c01 + c.k, c.c10 + c.k, c.c11 + c.k};
+    const R* rec0 = static_cast<const R*>(m0.rec);
+    const R* rec1 = static_cast<const R*>(m1.rec);
+    R r[2][8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = decode<ST>(r[q]);
-    if (ST != MPTRAC_FP32) {
-        const float su0 = sc[c.k], sv0 = sc[kMaxNZ + c.k], sw0 = sc[2 * kMaxNZ + c.k];
-        const float su1 = sc[c.k + 1], sv1 = sc[kMaxNZ + c.k + 1], sw1 = sc[2 * kMaxNZ + c.k + 1];
+    for (int q = 0; q < 8; ++q) {
+        r[0][q] = ldg_rec(rec0 + base[q & 3] + (q >> 2));
+        r[1][q] = ldg_rec(rec1 + base[q & 3] + (q >> 2));
+    }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            v[q].x *= su0; v[q].y *= sv0; v[q].z *= sw0;
-            v[q + 4].x *= su1; v[q + 4].y *= sv1; v[q + 4].z *= sw1;
+    for (int t = 0; t < 2; ++t) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            float4 v = decode<ST>(r[t][q]);
+            if (ST != MPTRAC_FP32) {
+                const int k = c.k + (q >> 2);
+                v.x *= s.sc[t][0][k];
+                v.y *= s.sc[t][1][k];
+                v.z *= s.sc[t][2][k];
+            }
+            cc.u[t][q] = v.x;
+            cc.v[t][q] = v.y;
+            cc.w[t][q] = v.z;
         }
     }
-    const float fx = c.fx, gx = c.gx, fy = c.fy, gy = c.gy, fz = c.fz, gz = c.gz;
-#define MPTRAC_TRI(comp, dst)                                                        \
-    {                                                                                \
-        const float e0 = fmaf(v[1].comp, fx, v[0].comp * gx);                        \
-        const float e1 = fmaf(v[3].comp, fx, v[2].comp * gx);                        \
-        const float e2 = fmaf(v[5].comp, fx, v[4].comp * gx);                        \
-        const float e3 = fmaf(v[7].comp, fx, v[6].comp * gx);                        \
-        const float s0 = fmaf(e1, fy, e0 * gy);                                      \
-        const float s1 = fmaf(e3, fy, e2 * gy);                                      \
-        dst = fmaf(s1, fz, s0 * gz);                                                 \
-    }
-    MPTRAC_TRI(x, out.u)
-    MPTRAC_TRI(y, out.v)
-    MPTRAC_TRI(z, out.w)
-#undef MPTRAC_TRI
-    if (SIG) {
-        float wt[8];
-        const float a00 = gy * gz, a10 = fy * gz, a01 = gy * fz, a11 = fy * fz;
-        wt[0] = gx * a00; wt[1] = fx * a00; wt[2] = gx * a10; wt[3] = fx * a10;
-        wt[4] = gx * a01; wt[5] = fx * a01; wt[6] = gx * a11; wt[7] = fx * a11;
-#define MPTRAC_VAR(comp, mean, dst)                                                  \
-    {                                                                                \
-        float acc = 0.f;                                                             \
-        _Pragma("unroll") for (int q = 0; q < 8; ++q) {                              \
-            const float d = v[q].comp - mean;                                        \
-            acc = fmaf(wt[q] * d, d, acc);                                           \
-        }                                                                            \
-        dst = acc;                                                                   \
-    }
-        MPTRAC_VAR(x, out.u, var.u)
-        MPTRAC_VAR(y, out.v, var.v)
-        MPTRAC_VAR(z, out.w, var.w)
-#undef MPTRAC_VAR
-    }
+    cc.col = c.c00;
+    cc.k = c.k;
 }
 
-// Wind at a located point and time weight w (0 -> m0, 1 -> m1).
+// trilinear interpolation of 8 corner values: lon, then lat, then pressure
+__device__ __forceinline__ float trilinear(const float* x, const Cell& c) {
+    const float e0 = fmaf(x[1], c.fx, x[0] * c.gx);
+    const float e1 = fmaf(x[3], c.fx, x[2] * c.gx);
+    const float e2 = fmaf(x[5], c.fx, x[4] * c.gx);
+    const float e3 = fmaf(x[7], c.fx, x[6] * c.gx);
+    const float s0 = fmaf(e1, c.fy, e0 * c.gy);
+    const float s1 = fmaf(e3, c.fy, e2 * c.gy);
+    return fmaf(s1, c.fz, s0 * c.gz);
+}
+
+// subgrid variance: spread of the corners about `mean`, weighted by the
+// interpolation weights wt
+__device__ __forceinline__ float weighted_var(const float* x, const float* wt, float mean) {
+    float acc = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float d = x[q] - mean;
+        acc = fmaf(wt[q] * d, d, acc);
+    }
+    return acc;
+}
+
+// Wind at a located point and time weight w (0 -> m0, 1 -> m1), with the
+// subgrid variances when SIG.
 template <int ST, bool SIG>
 __device__ __forceinline__ void eval_wind(const MetView& m0, const MetView& m1, const Smem& s,
-                                          const Cell& c, float w, Wind& out, Wind& var) {
-    Wind a, b, va, vb;
-    interp_slot<ST, SIG>(m0.rec, &s.sc[0][0][0], c, a, va);
-    interp_slot<ST, SIG>(m1.rec, &s.sc[1][0][0], c, b, vb);
-    out.u = fmaf(w, b.u - a.u, a.u);
-    out.v = fmaf(w, b.v - a.v, a.v);
-    out.w = fmaf(w, b.w - a.w, a.w);
+                                          const Cell& c, float w, Corners& cc, Wind& out,
+                                          Wind& var) {
+    if (c.c00 != cc.col || c.k != cc.k) fetch_corners<ST>(m0, m1, s, c, cc);
+    const float au = trilinear(cc.u[0], c), bu = trilinear(cc.u[1], c);
+    const float av = trilinear(cc.v[0], c), bv = trilinear(cc.v[1], c);
+    const float aw = trilinear(cc.w[0], c), bw = trilinear(cc.w[1], c);
+    out.u = fmaf(w, bu - au, au);
+    out.v = fmaf(w, bv - av, av);
+    out.w = fmaf(w, bw - aw, aw);
     if (SIG) {
-        var.u = fmaf(w, vb.u - va.u, va.u);
-        var.v = fmaf(w, vb.v - va.v, va.v);
-        var.w = fmaf(w, vb.w - va.w, va.w);
+        float wt[8];
+        const float a00 = c.gy * c.gz, a10 = c.fy * c.gz, a01 = c.gy * c.fz, a11 = c.fy * c.fz;
+        wt[0] = c.gx * a00; wt[1] = c.fx * a00; wt[2] = c.gx * a10; wt[3] = c.fx * a10;
+        wt[4] = c.gx * a01; wt[5] = c.fx * a01; wt[6] = c.gx * a11; wt[7] = c.fx * a11;
+        const float su0 = weighted_var(cc.u[0], wt, au), su1 = weighted_var(cc.u[1], wt, bu);
+        const float sv0 = weighted_var(cc.v[0], wt, av), sv1 = weighted_var(cc.v[1], wt, bv);
+        const float sw0 = weighted_var(cc.w[0], wt, aw), sw1 = weighted_var(cc.w[1], wt, bw);
+        var.u = fmaf(w, su1 - su0, su0);
+        var.v = fmaf(w, sv1 - sv0, sv0);
+        var.w = fmaf(w, sw1 - sw0, sw0);
     }
 }
 
@@ -347,6 +359,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_transport(const __grid_constant__
         ff p = ff_make(a.p[idx]);
         const uint32_t pid = a.id[idx];
         float up = 0.f, vp = 0.f, wp = 0.f;
+        Corners cc;
+        cc.col = -1;
+        cc.k = -1;
         if (use_meso) {
             up = a.up[idx];
             vp = a.vp[idx];
@@ -360,9 +375,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_transport(const __grid_constant__
                 const Cell c1 = locate(lon.hi, lat, p.hi, g, s);
                 Wind V;
                 if (MODE == MODE_STEP && use_meso)
-                    eval_wind<ST, true>(a.m0, a.m1, s, c1, w0, V, var);
+                    eval_wind<ST, true>(a.m0, a.m1, s, c1, w0, cc, V, var);
                 else
-                    eval_wind<ST, false>(a.m0, a.m1, s, c1, w0, V, var);
+                    eval_wind<ST, false>(a.m0, a.m1, s, c1, w0, cc, V, var);
                 const float cl = coslat(lat);
                 ff lon_s = ff_add(lon, a.half_dt * a.kdeg * V.u / cl);
                 ff lat_s = ff_add(lat, a.half_dt * a.kdeg * V.v);
@@ -370,7 +385,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_transport(const __grid_constant__
                 position_bc(lon_s, lat_s, p_s, g);
                 const Cell c2 = locate(lon_s.hi, lat_s, p_s.hi, g, s);
                 Wind V2, dummy;
-                eval_wind<ST, false>(a.m0, a.m1, s, c2, wm, V2, dummy);
+                eval_wind<ST, false>(a.m0, a.m1, s, c2, wm, cc, V2, dummy);
                 const float cl2 = coslat(lat_s);
                 lon = ff_add(lon, a.dt * a.kdeg * V2.u / cl2);
                 lat = ff_add(lat, a.dt * a.kdeg * V2.v);
@@ -379,7 +394,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_transport(const __grid_constant__
                 const float w0 = a.wt[2 * sidx];
                 const Cell c1 = locate(lon.hi, lat, p.hi, g, s);
                 Wind V;
-                eval_wind<ST, true>(a.m0, a.m1, s, c1, w0, V, var);
+                eval_wind<ST, true>(a.m0, a.m1, s, c1, w0, cc, V, var);
             }
             if (MODE != MODE_ADVECT && (use_turb || use_meso)) {
                 // ---- module_diffusion_turb / module_diffusion_meso ----
@@ -456,7 +471,10 @@ __global__ void __launch_bounds__(kBlock) k_interp(Geo g, MetView m0, MetView m1
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
         const Cell c = locate(ff_make(lon[idx]).hi, ff_make(lat[idx]), ff_make(p[idx]).hi, g, s);
         Wind V, var;
-        eval_wind<ST, true>(m0, m1, s, c, w, V, var);
+        Corners cc;
+        cc.col = -1;
+        cc.k = -1;
+        eval_wind<ST, true>(m0, m1, s, c, w, cc, V, var);
         ou[idx] = V.u;
         ov[idx] = V.v;
         ow[idx] = V.w;
