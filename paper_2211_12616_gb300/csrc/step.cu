@@ -61,12 +61,27 @@ __device__ __forceinline__ bool ff_greater(ff a, float bh, float bl) {
     return a.hi > bh || (a.hi == bh && a.lo > bl);
 }
 
-// |cos(lat)| floored at cos(89.999 deg), from the colatitude so that it keeps
-// its relative precision next to the poles.
+// sin(x) for |x| <= pi/2 from its Taylor series through x^13 (truncation
+// error below (pi/2)^15 / 15! < 7e-10), in Horner form.
+__device__ __forceinline__ float sin_taylor(float x) {
+    const float x2 = x * x;
+    float q = 1.6059043836821613e-10f;             //  1/13!
+    q = fmaf(q, x2, -2.505210838544172e-08f);      // -1/11!
+    q = fmaf(q, x2, 2.755731922398589e-06f);       //  1/9!
+    q = fmaf(q, x2, -1.984126984126984e-04f);      // -1/7!
+    q = fmaf(q, x2, 8.333333333333333e-03f);       //  1/5!
+    q = fmaf(q, x2, -1.6666666666666666e-01f);     // -1/3!
+    q = fmaf(q, x2, 1.0f);
+    return x * q;
+}
+
+// |cos(lat)| floored at cos(89.999 deg), as sin of the colatitude so that it
+// keeps its relative precision next to the poles.
 __device__ __forceinline__ float coslat(ff lat) {
     float colat = (lat.hi >= 0.f) ? __fsub_rn(__fsub_rn(90.f, lat.hi), lat.lo)
                                   : __fadd_rn(__fadd_rn(90.f, lat.hi), lat.lo);
-    float c = fabsf(sinpif(colat * (1.0f / 180.0f)));
+    colat = fminf(fmaxf(colat, -90.f), 90.f);
+    const float c = fabsf(sin_taylor(colat * 0.017453292519943295f));
     return fmaxf(c, kCosFloor);
 }
 
@@ -117,12 +132,26 @@ __device__ __forceinline__ float u23(uint32_t x) {
     return (__uint2float_rn(x >> 9) + 0.5f) * kTwoPow23Inv;
 }
 
+// Box-Muller pair from two words.  -ln(u) comes from the hardware log2 where
+// it is at least 2^-6 (relative error ~1e-7 there) and from the series
+// t + t^2/2 + t^3/3 + t^4/4 of -ln(1 - t), t = 1 - u (exact), below that
+// (truncation < t^5/5 relative, < 2e-8); the angle 2 pi u_b is shifted to
+// (-pi, pi) where the hardware sine/cosine have absolute error < 4e-7.
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1) {
-    const float r = sqrtf(-2.0f * logf(u23(a)));
-    float s, c;
-    sincospif(2.0f * u23(b), &s, &c);
-    z0 = r * c;
-    z1 = r * s;
+    const float ua = u23(a), ub = u23(b);
+    const float t = 1.0f - ua;
+    float nl;
+    if (t < 0.015625f)
+        nl = t * fmaf(t, fmaf(t, fmaf(t, 0.25f, 0.33333333333333333f), 0.5f), 1.0f);
+    else
+        nl = -__log2f(ua) * 0.69314718055994531f;
+    const float r2 = 2.0f * nl;
+    const float r = r2 * rsqrtf(r2);
+    const float th = 6.2831853071795865f * (ub - 0.5f);
+    float sn, cs;
+    __sincosf(th, &sn, &cs);
+    z0 = -r * cs;
+    z1 = -r * sn;
 }
 
 // ---------------------------------------------------------------------------
@@ -156,12 +185,11 @@ struct Smem {
     float sc[2][3][kMaxNZ];   // scales of u, v, omega for slot 0 / 1 (16-bit storage)
 };
 
-// Cell of a point: column record offsets of the 4 corner columns, lower level,
-// and the interpolation weights as (f, g = 1 - f) pairs.  All indices are
-// clamped into the grid whatever the input.
+// Cell of a point: indices (lon i, lat j, lower level k) and the
+// interpolation weights as (f, g = 1 - f) pairs.  All indices are clamped into
+// the grid whatever the input.
 struct Cell {
-    int c00, c01, c10, c11;   // (j, i), (j, i+1), (j+1, i), (j+1, i+1)   [record index]
-    int k;
+    int i, j, k;
     float fx, gx, fy, gy, fz, gz;
 };
 
@@ -170,16 +198,18 @@ __device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.f), 
 // The latitude fraction is formed in float-float and both weights are
 // computed directly, so that next to a pole the small weight keeps its
 // relative precision (winds there vanish like the distance to the pole while
-// the longitude increment divides by cos(lat)).
-__device__ __forceinline__ Cell locate(float lon, ff lat, float p, const Geo& g, const Smem& s) {
+// the longitude increment divides by cos(lat)).  The level search starts from
+// `k_hint` (the level of the previous evaluation; < 0: none), else from the
+// ln(p) table, and walks to the bracketing pair.
+__device__ __forceinline__ Cell locate(float lon, ff lat, float p, const Geo& g, const Smem& s,
+                                       int k_hint) {
     Cell c;
     const float x = (lon - g.lon0) * g.inv_dlon;
     const float xf = floorf(x);
     int i = (int)xf;
     if (i >= g.nx) i -= g.nx;
     if (i < 0) i += g.nx;
-    i = min(max(i, 0), g.nx - 1);
-    const int i1 = (i + 1 == g.nx) ? 0 : i + 1;
+    c.i = min(max(i, 0), g.nx - 1);
     c.fx = clamp01(x - xf);
     c.gx = 1.f - c.fx;
 
@@ -191,24 +221,22 @@ __device__ __forceinline__ Cell locate(float lon, ff lat, float p, const Geo& g,
     ye = fmaf(d.lo, g.inv_dlat, ye);
     int j = (int)floorf(yh);
     j = min(max(j, 0), g.ny - 2);
+    c.j = j;
     c.fy = clamp01(__fadd_rn(__fsub_rn(yh, (float)j), ye));
     c.gy = clamp01(__fsub_rn(__fsub_rn((float)(j + 1), yh), ye));
 
     const float pc = fminf(fmaxf(p, g.pmin), g.pmax);
-    int b = (int)((__logf(pc) - g.lnp_top) * g.inv_dln);
-    b = min(max(b, 0), g.nbins - 1);
-    int k = s.kguess[b];
+    int k = k_hint;
+    if (k < 0) {
+        int b = (int)((__logf(pc) - g.lnp_top) * g.inv_dln);
+        b = min(max(b, 0), g.nbins - 1);
+        k = s.kguess[b];
+    }
     while (k > 0 && s.plev[k] < pc) --k;
     while (k < g.nz - 2 && s.plev[k + 1] >= pc) ++k;
     c.k = k;
     c.fz = clamp01((s.plev[k] - pc) * s.inv_dp[k]);
     c.gz = 1.f - c.fz;
-
-    const int row0 = j * g.nx, row1 = row0 + g.nx;
-    c.c00 = (row0 + i) * g.nz;
-    c.c01 = (row0 + i1) * g.nz;
-    c.c10 = (row1 + i) * g.nz;
-    c.c11 = (row1 + i1) * g.nz;
     return c;
 }
 
@@ -229,9 +257,12 @@ struct Corners {
 // corner order q: bit 0 = i+1, bit 1 = j+1, bit 2 = k+1
 template <int ST>
 __device__ __forceinline__ void fetch_corners(const MetView& m0, const MetView& m1, const Smem& s,
-                                              const Cell& c, Corners& cc) {
+                                              const Geo& g, const Cell& c, int col, Corners& cc) {
     using R = typename RecT<ST>::T;
-    const int base[4] = {c.c00 + c.k, c.c01 + c.k, c.c10 + c.k, c.c11 + c.k};
+    const int i1 = (c.i + 1 == g.nx) ? 0 : c.i + 1;
+    const int row1 = col - c.i + g.nx;
+    const int base[4] = {col * g.nz + c.k, (col - c.i + i1) * g.nz + c.k, (row1 + c.i) * g.nz + c.k,
+                         (row1 + i1) * g.nz + c.k};
     const R* rec0 = static_cast<const R*>(m0.rec);
     const R* rec1 = static_cast<const R*>(m1.rec);
     R r[2][8];
@@ -256,7 +287,7 @@ __device__ __forceinline__ void fetch_corners(const MetView& m0, const MetView& 
             cc.w[t][q] = v.z;
         }
     }
-    cc.col = c.c00;
+    cc.col = col;
     cc.k = c.k;
 }
 
@@ -287,9 +318,10 @@ __device__ __forceinline__ float weighted_var(const float* x, const float* wt, f
 // subgrid variances when SIG.
 template <int ST, bool SIG>
 __device__ __forceinline__ void eval_wind(const MetView& m0, const MetView& m1, const Smem& s,
-                                          const Cell& c, float w, Corners& cc, Wind& out,
-                                          Wind& var) {
-    if (c.c00 != cc.col || c.k != cc.k) fetch_corners<ST>(m0, m1, s, c, cc);
+                                          const Geo& g, const Cell& c, float w, Corners& cc,
+                                          Wind& out, Wind& var) {
+    const int col = c.j * g.nx + c.i;
+    if (col != cc.col || c.k != cc.k) fetch_corners<ST>(m0, m1, s, g, c, col, cc);
     const float au = trilinear(cc.u[0], c), bu = trilinear(cc.u[1], c);
     const float av = trilinear(cc.v[0], c), bv = trilinear(cc.v[1], c);
     const float aw = trilinear(cc.w[0], c), bw = trilinear(cc.w[1], c);
@@ -372,29 +404,29 @@ __global__ void __launch_bounds__(kBlock, 2) k_transport(const __grid_constant__
             if (MODE != MODE_DIFFUSE) {
                 // ---- module_advection: explicit midpoint ----
                 const float w0 = a.wt[2 * sidx], wm = a.wt[2 * sidx + 1];
-                const Cell c1 = locate(lon.hi, lat, p.hi, g, s);
+                const Cell c1 = locate(lon.hi, lat, p.hi, g, s, cc.k);
                 Wind V;
                 if (MODE == MODE_STEP && use_meso)
-                    eval_wind<ST, true>(a.m0, a.m1, s, c1, w0, cc, V, var);
+                    eval_wind<ST, true>(a.m0, a.m1, s, g, c1, w0, cc, V, var);
                 else
-                    eval_wind<ST, false>(a.m0, a.m1, s, c1, w0, cc, V, var);
+                    eval_wind<ST, false>(a.m0, a.m1, s, g, c1, w0, cc, V, var);
                 const float cl = coslat(lat);
                 ff lon_s = ff_add(lon, a.half_dt * a.kdeg * V.u / cl);
                 ff lat_s = ff_add(lat, a.half_dt * a.kdeg * V.v);
                 ff p_s = ff_add(p, a.half_dt * V.w);
                 position_bc(lon_s, lat_s, p_s, g);
-                const Cell c2 = locate(lon_s.hi, lat_s, p_s.hi, g, s);
+                const Cell c2 = locate(lon_s.hi, lat_s, p_s.hi, g, s, cc.k);
                 Wind V2, dummy;
-                eval_wind<ST, false>(a.m0, a.m1, s, c2, wm, cc, V2, dummy);
+                eval_wind<ST, false>(a.m0, a.m1, s, g, c2, wm, cc, V2, dummy);
                 const float cl2 = coslat(lat_s);
                 lon = ff_add(lon, a.dt * a.kdeg * V2.u / cl2);
                 lat = ff_add(lat, a.dt * a.kdeg * V2.v);
                 p = ff_add(p, a.dt * V2.w);
             } else if (use_meso) {
                 const float w0 = a.wt[2 * sidx];
-                const Cell c1 = locate(lon.hi, lat, p.hi, g, s);
+                const Cell c1 = locate(lon.hi, lat, p.hi, g, s, cc.k);
                 Wind V;
-                eval_wind<ST, true>(a.m0, a.m1, s, c1, w0, cc, V, var);
+                eval_wind<ST, true>(a.m0, a.m1, s, g, c1, w0, cc, V, var);
             }
             if (MODE != MODE_ADVECT && (use_turb || use_meso)) {
                 // ---- module_diffusion_turb / module_diffusion_meso ----
@@ -469,12 +501,12 @@ __global__ void __launch_bounds__(kBlock) k_interp(Geo g, MetView m0, MetView m1
     load_tables(s, g, m0, m1, ST != MPTRAC_FP32);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
-        const Cell c = locate(ff_make(lon[idx]).hi, ff_make(lat[idx]), ff_make(p[idx]).hi, g, s);
+        const Cell c = locate(ff_make(lon[idx]).hi, ff_make(lat[idx]), ff_make(p[idx]).hi, g, s, -1);
         Wind V, var;
         Corners cc;
         cc.col = -1;
         cc.k = -1;
-        eval_wind<ST, true>(m0, m1, s, c, w, cc, V, var);
+        eval_wind<ST, true>(m0, m1, s, g, c, w, cc, V, var);
         ou[idx] = V.u;
         ov[idx] = V.v;
         ow[idx] = V.w;
