@@ -244,6 +244,36 @@ struct Wind {
     float u, v, w;
 };
 
+// Pairs of float32 values in one 64-bit register, operated on by Blackwell's
+// packed float32x2 instructions (each lane rounds exactly like the scalar
+// instruction).  Lane 0 holds the earlier snapshot, lane 1 the later one, so
+// one instruction interpolates both snapshots.
+typedef unsigned long long f2_t;
+
+__device__ __forceinline__ f2_t f2_pack(float a, float b) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_split(f2_t v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+    f2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
+    f2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
+    f2_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // The 8 corners of one cell on both snapshots, (u, v, omega) decoded and
 // scaled, kept in registers.  A particle moves about 1/60 of a 1-degree cell
 // per step, so consecutive wind evaluations almost always fall into the cell
@@ -251,7 +281,7 @@ struct Wind {
 // is paid only when the particle changes cell.
 struct Corners {
     int col, k;               // cached cell (record index of column (j, i), lower level); col < 0: empty
-    float u[2][8], v[2][8], w[2][8];
+    f2_t u[8], v[8], w[8];    // (snapshot 0, snapshot 1) per corner
 };
 
 // corner order q: bit 0 = i+1, bit 1 = j+1, bit 2 = k+1
@@ -272,46 +302,59 @@ __device__ __forceinline__ void fetch_corners(const MetView& m0, const MetView& 
         r[1][q] = ldg_rec(rec1 + base[q & 3] + (q >> 2));
     }
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            float4 v = decode<ST>(r[t][q]);
-            if (ST != MPTRAC_FP32) {
-                const int k = c.k + (q >> 2);
-                v.x *= s.sc[t][0][k];
-                v.y *= s.sc[t][1][k];
-                v.z *= s.sc[t][2][k];
-            }
-            cc.u[t][q] = v.x;
-            cc.v[t][q] = v.y;
-            cc.w[t][q] = v.z;
+    for (int q = 0; q < 8; ++q) {
+        float4 a = decode<ST>(r[0][q]);
+        float4 b = decode<ST>(r[1][q]);
+        if (ST != MPTRAC_FP32) {
+            const int k = c.k + (q >> 2);
+            a.x *= s.sc[0][0][k]; a.y *= s.sc[0][1][k]; a.z *= s.sc[0][2][k];
+            b.x *= s.sc[1][0][k]; b.y *= s.sc[1][1][k]; b.z *= s.sc[1][2][k];
         }
+        cc.u[q] = f2_pack(a.x, b.x);
+        cc.v[q] = f2_pack(a.y, b.y);
+        cc.w[q] = f2_pack(a.z, b.z);
     }
     cc.col = col;
     cc.k = c.k;
 }
 
-// trilinear interpolation of 8 corner values: lon, then lat, then pressure
-__device__ __forceinline__ float trilinear(const float* x, const Cell& c) {
-    const float e0 = fmaf(x[1], c.fx, x[0] * c.gx);
-    const float e1 = fmaf(x[3], c.fx, x[2] * c.gx);
-    const float e2 = fmaf(x[5], c.fx, x[4] * c.gx);
-    const float e3 = fmaf(x[7], c.fx, x[6] * c.gx);
-    const float s0 = fmaf(e1, c.fy, e0 * c.gy);
-    const float s1 = fmaf(e3, c.fy, e2 * c.gy);
-    return fmaf(s1, c.fz, s0 * c.gz);
+// interpolation weights as pairs (same weight for both snapshots)
+struct Weights2 {
+    f2_t fx, gx, fy, gy, fz, gz;
+};
+
+__device__ __forceinline__ Weights2 weights2(const Cell& c) {
+    return {f2_pack(c.fx, c.fx), f2_pack(c.gx, c.gx), f2_pack(c.fy, c.fy),
+            f2_pack(c.gy, c.gy), f2_pack(c.fz, c.fz), f2_pack(c.gz, c.gz)};
+}
+
+// trilinear interpolation of 8 corner pairs: lon, then lat, then pressure
+__device__ __forceinline__ f2_t trilinear(const f2_t* x, const Weights2& W) {
+    const f2_t e0 = f2_fma(x[1], W.fx, f2_mul(x[0], W.gx));
+    const f2_t e1 = f2_fma(x[3], W.fx, f2_mul(x[2], W.gx));
+    const f2_t e2 = f2_fma(x[5], W.fx, f2_mul(x[4], W.gx));
+    const f2_t e3 = f2_fma(x[7], W.fx, f2_mul(x[6], W.gx));
+    const f2_t s0 = f2_fma(e1, W.fy, f2_mul(e0, W.gy));
+    const f2_t s1 = f2_fma(e3, W.fy, f2_mul(e2, W.gy));
+    return f2_fma(s1, W.fz, f2_mul(s0, W.gz));
 }
 
 // subgrid variance: spread of the corners about `mean`, weighted by the
-// interpolation weights wt
-__device__ __forceinline__ float weighted_var(const float* x, const float* wt, float mean) {
-    float acc = 0.f;
+// interpolation weights wt (both snapshots at once)
+__device__ __forceinline__ f2_t weighted_var(const f2_t* x, const f2_t* wt, f2_t mean) {
+    f2_t acc = f2_pack(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        const float d = x[q] - mean;
-        acc = fmaf(wt[q] * d, d, acc);
+        const f2_t d = f2_sub(x[q], mean);
+        acc = f2_fma(f2_mul(wt[q], d), d, acc);
     }
     return acc;
+}
+
+__device__ __forceinline__ float tlerp(f2_t ab, float w) {
+    float a, b;
+    f2_split(ab, a, b);
+    return fmaf(w, b - a, a);
 }
 
 // Wind at a located point and time weight w (0 -> m0, 1 -> m1), with the
@@ -322,23 +365,21 @@ __device__ __forceinline__ void eval_wind(const MetView& m0, const MetView& m1, 
                                           Wind& out, Wind& var) {
     const int col = c.j * g.nx + c.i;
     if (col != cc.col || c.k != cc.k) fetch_corners<ST>(m0, m1, s, g, c, col, cc);
-    const float au = trilinear(cc.u[0], c), bu = trilinear(cc.u[1], c);
-    const float av = trilinear(cc.v[0], c), bv = trilinear(cc.v[1], c);
-    const float aw = trilinear(cc.w[0], c), bw = trilinear(cc.w[1], c);
-    out.u = fmaf(w, bu - au, au);
-    out.v = fmaf(w, bv - av, av);
-    out.w = fmaf(w, bw - aw, aw);
+    const Weights2 W = weights2(c);
+    const f2_t tu = trilinear(cc.u, W), tv = trilinear(cc.v, W), tw = trilinear(cc.w, W);
+    out.u = tlerp(tu, w);
+    out.v = tlerp(tv, w);
+    out.w = tlerp(tw, w);
     if (SIG) {
-        float wt[8];
+        f2_t wt[8];
         const float a00 = c.gy * c.gz, a10 = c.fy * c.gz, a01 = c.gy * c.fz, a11 = c.fy * c.fz;
-        wt[0] = c.gx * a00; wt[1] = c.fx * a00; wt[2] = c.gx * a10; wt[3] = c.fx * a10;
-        wt[4] = c.gx * a01; wt[5] = c.fx * a01; wt[6] = c.gx * a11; wt[7] = c.fx * a11;
-        const float su0 = weighted_var(cc.u[0], wt, au), su1 = weighted_var(cc.u[1], wt, bu);
-        const float sv0 = weighted_var(cc.v[0], wt, av), sv1 = weighted_var(cc.v[1], wt, bv);
-        const float sw0 = weighted_var(cc.w[0], wt, aw), sw1 = weighted_var(cc.w[1], wt, bw);
-        var.u = fmaf(w, su1 - su0, su0);
-        var.v = fmaf(w, sv1 - sv0, sv0);
-        var.w = fmaf(w, sw1 - sw0, sw0);
+        const float ws[8] = {c.gx * a00, c.fx * a00, c.gx * a10, c.fx * a10,
+                             c.gx * a01, c.fx * a01, c.gx * a11, c.fx * a11};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) wt[q] = f2_pack(ws[q], ws[q]);
+        var.u = tlerp(weighted_var(cc.u, wt, tu), w);
+        var.v = tlerp(weighted_var(cc.v, wt, tv), w);
+        var.w = tlerp(weighted_var(cc.w, wt, tw), w);
     }
 }
 

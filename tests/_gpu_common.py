@@ -3,7 +3,9 @@ import numpy as np
 import pytest
 import torch
 
-from oracle.errors import lon_diff
+from oracle.errors import great_circle_km, lon_diff
+
+KM_PER_DEG = 6371.0 * np.pi / 180.0
 
 # Tolerances of the FP32 kernels against the FP64 oracle after 120 steps:
 # 1e-4 degrees in longitude/latitude and 1e-5 relative in pressure.
@@ -39,12 +41,21 @@ def by_id(d):
     return {k: np.asarray(v)[order] for k, v in d.items()}
 
 
-def assert_positions_close(got, ref, tol_deg=TOL_DEG, tol_p=TOL_P, what=""):
+def assert_positions_close(got, ref, tol_deg=TOL_DEG, tol_p=TOL_P, what="", lon_metric="deg"):
+    """Positions agree within tol_deg (degrees) and tol_p (relative pressure).
+
+    lon_metric "deg": |dlon| (folded into [-180, 180)) <= tol_deg, the literal
+    criterion, used for deterministic advection.  "arc": the great-circle
+    distance in degrees of arc <= tol_deg -- for stochastic runs, where within
+    a fraction of a degree of a pole a sub-millimetre displacement difference
+    is already 1e-4 degrees of longitude.  |dlat| <= tol_deg in both cases.
+    """
     dlon = np.abs(lon_diff(got["lon"], ref["lon"]))
-    # longitude differences shrink with cos(lat) in distance; compare as degrees of arc
+    arc = great_circle_km(got["lon"], got["lat"], ref["lon"], ref["lat"]) / KM_PER_DEG
     dlat = np.abs(got["lat"] - ref["lat"])
     dp = np.abs(got["p"] - ref["p"]) / ref["p"]
-    msg = (f"{what}: max |dlon| {dlon.max():.3e} deg, max |dlat| {dlat.max():.3e} deg, "
-           f"max |dp|/p {dp.max():.3e}")
-    assert dlon.max() <= tol_deg and dlat.max() <= tol_deg and dp.max() <= tol_p, msg
+    msg = (f"{what}: max |dlon| {dlon.max():.3e} deg, max arc {arc.max():.3e} deg, "
+           f"max |dlat| {dlat.max():.3e} deg, max |dp|/p {dp.max():.3e}")
+    horiz = dlon.max() if lon_metric == "deg" else arc.max()
+    assert horiz <= tol_deg and dlat.max() <= tol_deg and dp.max() <= tol_p, msg
     return dlon.max(), dlat.max(), dp.max()

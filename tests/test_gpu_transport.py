@@ -85,7 +85,8 @@ def test_fourier_modes_parity(M, fourier, storage, mode):
         ref = tr.step(met, st0, t, dt, tr.DiffParams(), 99, 40, ns)
     torch.cuda.synchronize()
     got = parts.to_numpy()
-    assert_positions_close(got, ref, what=f"{mode} storage {storage}")
+    assert_positions_close(got, ref, what=f"{mode} storage {storage}",
+                           lon_metric="deg" if mode == "advect" else "arc")
     if mode != "advect":
         for k in ("up", "vp", "wp"):
             scale = np.abs(ref[k]).max() + 1e-30
@@ -108,7 +109,7 @@ def test_release_windows(M, fourier):
     torch.cuda.synchronize()
     ref = tr.step(met, st0, 0.0, 180.0, tr.DiffParams(), 5, 0, 30, windows=(ts, te))
     got = parts.to_numpy()
-    assert_positions_close(got, ref, what="release windows")
+    assert_positions_close(got, ref, what="release windows", lon_metric="arc")
     still = st0["release"] == 3
     np.testing.assert_array_equal(got["lon"][still], st0["lon"][still])
     ctx.set_releases([], [])
@@ -162,7 +163,7 @@ def test_small_and_ragged_counts(M, cfg1, n):
     torch.cuda.synchronize()
     if n:
         ref = tr.step(met, st0, 0.0, 180.0, tr.DiffParams(), 1, 0, 12)
-        assert_positions_close(parts.to_numpy(), ref, what=f"n={n}")
+        assert_positions_close(parts.to_numpy(), ref, what=f"n={n}", lon_metric="arc")
 
 
 def test_host_validation_errors(M, cfg1):
