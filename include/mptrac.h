@@ -194,6 +194,24 @@ size_t mptrac_sort_workspace_bytes(const mptrac_ctx* ctx, int64_t n);
 int mptrac_sort(mptrac_ctx* ctx, const mptrac_particles* parts, void* workspace,
                 size_t ws_bytes, uintptr_t stream);
 
+/* Sort without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory (a host
+ * that must not bypass another framework's pool allocator, a pipeline in which
+ * cudaMalloc's implicit device synchronisation is not allowed, or a process
+ * with a device memory budget fixed at start-up).  It does what mptrac_sort
+ * does, with the same result, but its scratch memory is a 16 MiB array that is
+ * part of the library image (held by every GPU that loads the library until
+ * exit) instead of a caller workspace; it calls no allocating routine.
+ *   - At most MPTRAC_SORT_NOALLOC_MAX_N particles, else E_INVALID_ARG
+ *     (nothing is launched).
+ *   - The first call on a device looks up the array's device address on that
+ *     (current) device; make that first call before any stream capture.
+ *   - All calls on one device share the array: calls that overlap on the GPU
+ *     race and must be serialised by the caller.
+ * Errors: as mptrac_sort (without E_WORKSPACE for a missing workspace). */
+#define MPTRAC_SORT_NOALLOC_MAX_N 262144
+int mptrac_sort_noalloc(mptrac_ctx* ctx, const mptrac_particles* parts, uintptr_t stream);
+
 /* ---- inspection entry points (used by the parity tests) ---------------- */
 
 /* Cell keys of the sort, written to DEVICE array keys[n]. */

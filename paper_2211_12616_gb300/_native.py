@@ -67,6 +67,7 @@ SIGNATURES = {
                                        C.POINTER(C.c_double), C.POINTER(C.c_size_t)]),
     "mptrac_met_slot_copy": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mptrac_kernel_launches": (C.c_uint64, []),
+    "mptrac_sort_noalloc": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_void_p]),
 }
 
 _lib = None

@@ -498,3 +498,75 @@ int mptrac_met_slot_copy(const mptrac_ctx* c, int slot, void* rec_out, float* sc
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Sorting without any device allocation.
+//
+// Some callers cannot allocate device memory at all: code that runs while
+// another framework owns the device heap (a pool allocator that must not be
+// bypassed), code that is not allowed to call cudaMalloc because it would
+// synchronise the device in the middle of an asynchronous pipeline, or
+// embedded hosts with a fixed memory budget checked at start-up.  For them
+// mptrac_sort_noalloc sorts with scratch memory that lives in a file-scope
+// device array of fixed size instead of a caller-provided workspace.
+//
+// The array is part of the library image: every GPU that loads the library
+// holds its 16 MiB until the process exits.  Its device address is looked up
+// once per device (cudaGetSymbolAddress, with that device current) on the first
+// call made on that device; in host code the array's name is only a host-side
+// stand-in, never a device address.  No part of the scratch has to start at
+// zero: every call writes each scratch byte before it reads it.  All calls on
+// a device share the one array, so calls whose work overlaps on the GPU (other
+// streams, other threads, other contexts on the same device) race on it and
+// must be serialised by the caller.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoallocScratchBytes = (size_t)16 << 20;
+__device__ __align__(256) static unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+constexpr int kMaxDevices = 128;
+std::atomic<void*> g_noalloc_ptr[kMaxDevices];
+
+// Device address of the scratch array on the current device (looked up once).
+int noalloc_scratch(void** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        (void)cudaGetLastError();
+        return fail(MPTRAC_E_CUDA, "no usable CUDA device for the static sort scratch (%s)",
+                    e != cudaSuccess ? cudaGetErrorString(e) : "device index out of range");
+    }
+    void* p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            (void)cudaGetLastError();
+            return fail(MPTRAC_E_CUDA, "cudaGetSymbolAddress of the static sort scratch failed: %s",
+                        cudaGetErrorString(e));
+        }
+        g_noalloc_ptr[dev].store(p, std::memory_order_release);
+    }
+    *out = p;
+    return MPTRAC_OK;
+}
+
+}  // namespace
+
+extern "C" int mptrac_sort_noalloc(mptrac_ctx* c, const mptrac_particles* P, uintptr_t stream) {
+    if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    int rc = check_particles(P, false);
+    if (rc) return rc;
+    if (P->n > MPTRAC_SORT_NOALLOC_MAX_N)
+        return fail(MPTRAC_E_INVALID_ARG,
+                    "mptrac_sort_noalloc sorts at most %d particles (got %lld); use mptrac_sort with a workspace",
+                    MPTRAC_SORT_NOALLOC_MAX_N, (long long)P->n);
+    if (P->n == 0) return ok();
+    if (sort_workspace_bytes(P->n) > kNoallocScratchBytes)
+        return fail(MPTRAC_E_WORKSPACE, "static sort scratch too small for %lld particles", (long long)P->n);
+    void* ws = nullptr;
+    if ((rc = noalloc_scratch(&ws))) return rc;
+    MPTRAC_CUDA(run_sort(c->geo, *P, ws, c->key_bits, reinterpret_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
