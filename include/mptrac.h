@@ -194,6 +194,25 @@ size_t mptrac_sort_workspace_bytes(const mptrac_ctx* ctx, int64_t n);
 int mptrac_sort(mptrac_ctx* ctx, const mptrac_particles* parts, void* workspace,
                 size_t ws_bytes, uintptr_t stream);
 
+/* Sort for runs with a release table: as mptrac_sort, except that particles
+ * whose release is not active at time t (t outside [t_start, t_end) of its
+ * release, or a release index outside the table) are keyed after every cell,
+ * so active particles fill the front of the arrays and whole warps of the
+ * step kernel work on active particles.  Equal keys keep their order.  Without
+ * a release table, or with parts->release == NULL, this is mptrac_sort. */
+int mptrac_sort_at(mptrac_ctx* ctx, const mptrac_particles* parts, double t, void* workspace,
+                   size_t ws_bytes, uintptr_t stream);
+
+/* Launch configuration of the fused step kernel (a project tuning knob; the
+ * paper has none).  Results do not depend on it.
+ *   variant     0: 256 threads per block, >= 2 resident blocks per SM (128 registers)
+ *               1: 128 threads per block, >= 4 resident blocks per SM (128 registers)
+ *               2: 128 threads per block, >= 5 resident blocks per SM (96 registers)
+ *   persistent  non-zero: one wave of blocks (SMs x resident blocks per SM) strides
+ *               over the particles; zero: one thread per particle.
+ * Errors: E_INVALID_ARG for an unknown variant. */
+int mptrac_set_launch(mptrac_ctx* ctx, int variant, int persistent);
+
 /* Sort without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory (a host
  * that must not bypass another framework's pool allocator, a pipeline in which

@@ -29,3 +29,21 @@ def sort_permutation(grid, state) -> np.ndarray:
 def sort_state(grid, state) -> dict:
     perm = sort_permutation(grid, state)
     return {k: np.asarray(v)[perm] for k, v in state.items()}
+
+
+def sort_permutation_at(grid, state, t, windows):
+    """Stable sort by cell key, with particles of releases inactive at time t last.
+
+    A release r is active at t if t_start[r] <= t < t_end[r]; particles whose
+    release index is outside the table are inactive.  Inactive particles get a
+    key above every cell key, so they follow all active particles in their
+    previous relative order.
+    """
+    keys = cell_keys(grid, state["lon"], state["lat"], state["p"]).astype(np.int64)
+    ts, te = (np.asarray(a, dtype=np.float64) for a in windows)
+    rel = np.asarray(state["release"]).astype(np.int64)
+    inside = rel < ts.size
+    r = np.where(inside, rel, 0)
+    active = inside & (t >= ts[r]) & (t < te[r])
+    keys = np.where(active, keys, grid.nx * grid.ny * grid.nz)
+    return np.argsort(keys, kind="stable")

@@ -68,6 +68,9 @@ SIGNATURES = {
     "mptrac_met_slot_copy": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mptrac_kernel_launches": (C.c_uint64, []),
     "mptrac_sort_noalloc": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_void_p]),
+    "mptrac_sort_at": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_double, C.c_void_p, C.c_size_t,
+                                 C.c_void_p]),
+    "mptrac_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
 }
 
 _lib = None
@@ -241,6 +244,17 @@ class Context:
         check(load().mptrac_sort(self.h, C.byref(parts.desc()), _ptr(workspace), workspace.numel(),
                                  _stream(stream)), self.h)
         return workspace
+
+    def sort_at(self, parts: Particles, t, workspace: torch.Tensor | None = None, stream=None):
+        nbytes = self.sort_workspace_bytes(parts.n)
+        if workspace is None:
+            workspace = torch.empty(nbytes, dtype=torch.uint8, device=parts.lon.device)
+        check(load().mptrac_sort_at(self.h, C.byref(parts.desc()), float(t), _ptr(workspace), workspace.numel(),
+                                    _stream(stream)), self.h)
+        return workspace
+
+    def set_launch(self, variant: int = 0, persistent: bool = False):
+        check(load().mptrac_set_launch(self.h, int(variant), int(persistent)), self.h)
 
     def cell_keys(self, parts: Particles, stream=None) -> torch.Tensor:
         keys = torch.empty(parts.n, dtype=torch.int32, device=parts.lon.device)

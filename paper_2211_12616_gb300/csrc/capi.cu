@@ -36,6 +36,8 @@ struct mptrac_ctx {
     int2* d_win = nullptr;
     int n_rel = 0;
     int key_bits = 0;
+    int launch_variant = 0;
+    bool persistent = false;
     Geo geo{};
 };
 
@@ -199,7 +201,7 @@ int run_transport(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
             a.wt[2 * q + 1] = (float)((tn + 0.5 * dt - t0) / (t1 - t0));
         }
         if (use_win) MPTRAC_CUDA(launch_windows(c->d_rel_ts, c->d_rel_te, c->n_rel, t, dt, n0, cnt, c->d_win, st));
-        MPTRAC_CUDA(launch_transport(c->storage, mode, a, grid, st));
+        MPTRAC_CUDA(launch_transport(c->storage, mode, a, grid, c->launch_variant, c->persistent, st));
     }
     return ok();
 }
@@ -429,6 +431,34 @@ int mptrac_sort(mptrac_ctx* c, const mptrac_particles* P, void* ws, size_t ws_by
         return fail(MPTRAC_E_WORKSPACE, "sort workspace must be 256-byte aligned device memory of >= %zu bytes (got %p, %zu)", need, ws, ws_bytes);
     if (!device_accessible(ws)) return fail(MPTRAC_E_WORKSPACE, "sort workspace is not device memory");
     MPTRAC_CUDA(run_sort(c->geo, *P, ws, c->key_bits, reinterpret_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
+int mptrac_sort_at(mptrac_ctx* c, const mptrac_particles* P, double t, void* ws, size_t ws_bytes,
+                   uintptr_t stream) {
+    if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    if (!std::isfinite(t)) return fail(MPTRAC_E_INVALID_ARG, "t must be finite");
+    int rc = check_particles(P, false);
+    if (rc) return rc;
+    if (P->n == 0) return ok();
+    const size_t need = sort_workspace_bytes(P->n);
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < need)
+        return fail(MPTRAC_E_WORKSPACE, "sort workspace must be 256-byte aligned device memory of >= %zu bytes (got %p, %zu)", need, ws, ws_bytes);
+    if (!device_accessible(ws)) return fail(MPTRAC_E_WORKSPACE, "sort workspace is not device memory");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!P->release || c->n_rel == 0) {
+        MPTRAC_CUDA(run_sort(c->geo, *P, ws, c->key_bits, st));
+    } else {
+        MPTRAC_CUDA(run_sort_at(c->geo, *P, ws, c->key_bits, t, c->d_rel_ts, c->d_rel_te, c->n_rel, st));
+    }
+    return ok();
+}
+
+int mptrac_set_launch(mptrac_ctx* c, int variant, int persistent) {
+    if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    if (variant < 0 || variant > 2) return fail(MPTRAC_E_INVALID_ARG, "launch variant must be 0, 1 or 2 (got %d)", variant);
+    c->launch_variant = variant;
+    c->persistent = persistent != 0;
     return ok();
 }
 

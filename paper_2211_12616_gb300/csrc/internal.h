@@ -68,7 +68,8 @@ enum Mode { MODE_ADVECT = 0, MODE_DIFFUSE = 1, MODE_STEP = 2 };
 void note_launches(int n);
 
 // ---- launchers (each returns a cudaError_t of the launch) -------------------
-cudaError_t launch_transport(int storage, int mode, const StepArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_transport(int storage, int mode, const StepArgs& a, int grid, int variant,
+                             bool persistent, cudaStream_t s);
 cudaError_t launch_windows(const double* ts, const double* te, int nrel, double t, double dt,
                            int n_begin, int nsteps, int2* out, cudaStream_t s);
 cudaError_t launch_interp(int storage, const Geo& g, MetView m0, MetView m1, float w, int64_t n,
@@ -86,5 +87,9 @@ cudaError_t launch_cell_keys(const Geo& g, int64_t n, const double* lon, const d
                              const double* p, uint32_t* keys, cudaStream_t s);
 cudaError_t run_sort(const Geo& g, const mptrac_particles& P, void* ws, int key_bits,
                      cudaStream_t s);
+// As run_sort, but particles whose release is inactive at time t (window from
+// ts/te, or release index >= nrel) get the key 2^key_bits, after every cell key.
+cudaError_t run_sort_at(const Geo& g, const mptrac_particles& P, void* ws, int key_bits, double t,
+                        const double* ts, const double* te, int nrel, cudaStream_t s);
 
 }  // namespace mptrac

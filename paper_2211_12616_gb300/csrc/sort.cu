@@ -103,6 +103,23 @@ __global__ void k_keys(Geo g, int64_t n, const double* lon, const double* lat, c
     }
 }
 
+// Keys for the batched run: the cell key, or 2^key_bits (after every cell key)
+// for particles whose release is inactive at time t.
+__global__ void k_keys_at(Geo g, int64_t n, const double* lon, const double* lat, const double* p,
+                          const uint32_t* release, double t, const double* ts, const double* te,
+                          int nrel, uint32_t inactive_key, uint32_t* keys) {
+    __shared__ KeyTables tb;
+    for (int q = threadIdx.x; q < g.nz; q += blockDim.x) tb.plev[q] = g.plev[q];
+    for (int q = threadIdx.x; q < g.nbins; q += blockDim.x) tb.kguess[q] = g.kguess[q];
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
+        const uint32_t r = release[q];
+        const bool active = r < (uint32_t)nrel && t >= ts[r] && t < te[r];
+        keys[q] = active ? cell_key(lon[q], lat[q], p[q], g, tb) : inactive_key;
+    }
+}
+
 // hist[d * ntiles + tile] = number of keys of `tile` with digit d
 __global__ void __launch_bounds__(kSortThreads) k_hist(const uint32_t* __restrict__ keys, int64_t n,
                                                        int shift, uint32_t* hist, int ntiles) {
@@ -287,10 +304,12 @@ cudaError_t launch_cell_keys(const Geo& g, int64_t n, const double* lon, const d
     return cudaGetLastError();
 }
 
-cudaError_t run_sort(const Geo& g, const mptrac_particles& P, void* ws, int key_bits,
-                     cudaStream_t s) {
+namespace {
+
+// LSD radix passes over the keys already in the workspace's keys_a, then the
+// gather of every particle array in sorted order.
+cudaError_t sort_from_keys(const mptrac_particles& P, void* ws, int key_bits, cudaStream_t s) {
     const int64_t n = P.n;
-    if (n <= 0) return cudaSuccess;
     const WsLayout L = ws_layout(n);
     char* w = static_cast<char*>(ws);
     uint32_t* ka = reinterpret_cast<uint32_t*>(w + L.keys_a);
@@ -300,12 +319,9 @@ cudaError_t run_sort(const Geo& g, const mptrac_particles& P, void* ws, int key_
     uint32_t* hist = reinterpret_cast<uint32_t*>(w + L.hist);
     uint32_t* tot = reinterpret_cast<uint32_t*>(w + L.tot);
     const int ntiles = (int)ntiles_for(n);
-
-    k_keys<<<grid_for(n), 256, 0, s>>>(g, n, P.lon, P.lat, P.p, ka, nullptr);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     const int passes = key_bits <= 0 ? 1 : (key_bits + 7) / 8;
-    note_launches(2 + 3 * passes);
+    note_launches(1 + 3 * passes);
     bool first = true;
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * pass;
@@ -315,8 +331,8 @@ cudaError_t run_sort(const Geo& g, const mptrac_particles& P, void* ws, int key_
                                                   tot, ntiles);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         first = false;
-        uint32_t* t = ka; ka = kb; kb = t;
-        t = va; va = vb; vb = t;
+        uint32_t* tmp = ka; ka = kb; kb = tmp;
+        tmp = va; va = vb; vb = tmp;
     }
     // copy the arrays aside, then gather them back in sorted order
     PermArgs pa{};
@@ -348,6 +364,35 @@ cudaError_t run_sort(const Geo& g, const mptrac_particles& P, void* ws, int key_
     }
     k_permute<<<grid_for(n), 256, 0, s>>>(pa);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t run_sort(const Geo& g, const mptrac_particles& P, void* ws, int key_bits,
+                     cudaStream_t s) {
+    const int64_t n = P.n;
+    if (n <= 0) return cudaSuccess;
+    const WsLayout L = ws_layout(n);
+    uint32_t* ka = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.keys_a);
+    note_launches(1);
+    k_keys<<<grid_for(n), 256, 0, s>>>(g, n, P.lon, P.lat, P.p, ka, nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return sort_from_keys(P, ws, key_bits, s);
+}
+
+cudaError_t run_sort_at(const Geo& g, const mptrac_particles& P, void* ws, int key_bits, double t,
+                        const double* ts, const double* te, int nrel, cudaStream_t s) {
+    const int64_t n = P.n;
+    if (n <= 0) return cudaSuccess;
+    const WsLayout L = ws_layout(n);
+    uint32_t* ka = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.keys_a);
+    note_launches(1);
+    k_keys_at<<<grid_for(n), 256, 0, s>>>(g, n, P.lon, P.lat, P.p, P.release, t, ts, te, nrel,
+                                          1u << key_bits, ka);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return sort_from_keys(P, ws, key_bits + 1, s);
 }
 
 }  // namespace mptrac

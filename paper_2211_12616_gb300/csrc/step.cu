@@ -21,6 +21,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace mptrac {
@@ -403,8 +405,8 @@ __device__ __forceinline__ void load_tables(Smem& s, const Geo& g, const MetView
 // ---------------------------------------------------------------------------
 // The particle kernel
 // ---------------------------------------------------------------------------
-template <int ST, int MODE>
-__global__ void __launch_bounds__(kBlock, 2) k_transport(const __grid_constant__ StepArgs a) {
+template <int ST, int MODE, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant__ StepArgs a) {
     __shared__ Smem s;
     load_tables(s, a.geo, a.m0, a.m1, ST != MPTRAC_FP32);
     const Geo& g = a.geo;
@@ -588,25 +590,61 @@ int grid_for(int64_t n) {
     return (int)b;
 }
 
+// Launch variants of the fused step (threads per block, minimum resident blocks
+// per SM -- which caps the registers): 0 = (256, 2) 128 registers, 1 = (128, 4)
+// 128 registers in finer blocks, 2 = (128, 5) 96 registers, 20 warps per SM.
+template <int ST, int BLOCK, int MINB>
+cudaError_t launch_step_variant(const StepArgs& a, int grid, bool persistent, cudaStream_t s) {
+    auto kern = k_transport<ST, MODE_STEP, BLOCK, MINB>;
+    if (persistent) {
+        static int per_sm = 0;   // resident blocks per SM of this instantiation (same on every GB300)
+        if (per_sm <= 0) {
+            int v = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, BLOCK, 0) != cudaSuccess) {
+                (void)cudaGetLastError();
+                v = MINB;
+            }
+            per_sm = v;
+        }
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t need = (a.n + BLOCK - 1) / BLOCK;
+        grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(per_sm, 1), need));
+    } else {
+        grid = (int)std::max<int64_t>(1, std::min<int64_t>((a.n + BLOCK - 1) / BLOCK, (int64_t)1 << 20));
+    }
+    kern<<<grid, BLOCK, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int ST>
-cudaError_t launch_transport_st(int mode, const StepArgs& a, int grid, cudaStream_t s) {
+cudaError_t launch_transport_st(int mode, const StepArgs& a, int grid, int variant, bool persistent,
+                                cudaStream_t s) {
+    if (mode == MODE_STEP) {
+        switch (variant) {
+            case 1: return launch_step_variant<ST, 128, 4>(a, grid, persistent, s);
+            case 2: return launch_step_variant<ST, 128, 5>(a, grid, persistent, s);
+            default: return launch_step_variant<ST, kBlock, 2>(a, grid, persistent, s);
+        }
+    }
     switch (mode) {
-        case MODE_ADVECT: k_transport<ST, MODE_ADVECT><<<grid, kBlock, 0, s>>>(a); break;
-        case MODE_DIFFUSE: k_transport<ST, MODE_DIFFUSE><<<grid, kBlock, 0, s>>>(a); break;
-        default: k_transport<ST, MODE_STEP><<<grid, kBlock, 0, s>>>(a); break;
+        case MODE_ADVECT: k_transport<ST, MODE_ADVECT, kBlock, 2><<<grid, kBlock, 0, s>>>(a); break;
+        default: k_transport<ST, MODE_DIFFUSE, kBlock, 2><<<grid, kBlock, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_transport(int storage, int mode, const StepArgs& a, int grid, cudaStream_t s) {
+cudaError_t launch_transport(int storage, int mode, const StepArgs& a, int grid, int variant,
+                             bool persistent, cudaStream_t s) {
     if (grid <= 0) grid = grid_for(a.n);
     note_launches(1);
     switch (storage) {
-        case MPTRAC_FP32: return launch_transport_st<MPTRAC_FP32>(mode, a, grid, s);
-        case MPTRAC_BF16: return launch_transport_st<MPTRAC_BF16>(mode, a, grid, s);
-        default: return launch_transport_st<MPTRAC_FP16>(mode, a, grid, s);
+        case MPTRAC_FP32: return launch_transport_st<MPTRAC_FP32>(mode, a, grid, variant, persistent, s);
+        case MPTRAC_BF16: return launch_transport_st<MPTRAC_BF16>(mode, a, grid, variant, persistent, s);
+        default: return launch_transport_st<MPTRAC_FP16>(mode, a, grid, variant, persistent, s);
     }
 }
 

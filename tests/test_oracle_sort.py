@@ -32,3 +32,23 @@ def test_sorted_stable_permutation():
     assert np.all(np.diff(perm)[same] > 0)
     out = osort.sort_state(grid, st)
     np.testing.assert_array_equal(out["id"], st["id"][perm])
+
+
+def test_inactive_releases_sorted_last_in_order():
+    grid = grid_2deg_20lev()
+    st = uniform_particles(12, grid.plev, seed=5)
+    st["release"] = np.array([0, 1, 2, 0, 1, 2, 5, 0, 1, 2, 0, 1], np.uint32)
+    ts = np.array([0.0, 100.0, 0.0])
+    te = np.array([50.0, 200.0, 1e9])
+    # at t = 60: release 0 ended, release 1 not started, release 2 active, 5 unknown
+    perm = osort.sort_permutation_at(grid, st, 60.0, (ts, te))
+    active = np.flatnonzero(st["release"] == 2)
+    inactive = np.flatnonzero(st["release"] != 2)
+    keys = osort.cell_keys(grid, st["lon"], st["lat"], st["p"])
+    np.testing.assert_array_equal(perm[:active.size], active[np.argsort(keys[active], kind="stable")])
+    np.testing.assert_array_equal(perm[active.size:], inactive)
+    # without windows the rule reduces to the plain sort when everything is active
+    all_on = (np.zeros(6), np.full(6, 1e9))
+    st["release"][:] = 0
+    np.testing.assert_array_equal(osort.sort_permutation_at(grid, st, 5.0, all_on),
+                                  osort.sort_permutation(grid, st))
