@@ -415,6 +415,95 @@ def run_batch(args, rank, world):
     ctx.close()
 
 
+# --------------------------------------------------------------------------
+# precision: 0.3 degree x 137 levels, u/v/omega/T in fp32 / bf16 / fp16 storage
+# --------------------------------------------------------------------------
+PREC_T_END, PREC_SEED, PREC_N, PREC_SUB = 12 * 3600.0, 3, 10_000_000, 10_000
+
+
+def run_precision(args, rank, world):
+    import torch
+
+    import paper_2211_12616_gb300 as M
+    from oracle import transport as tr
+    from oracle.driver import run_schedule
+    from oracle.errors import great_circle_km
+    from paper_2211_12616_gb300.simulation import Simulation, periodic_snapshots
+    from workloads import fourier_modes, fourier_snapshot, grid_03deg_137lev, uniform_particles
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    grid = grid_03deg_137lev()
+    modes = fourier_modes(PREC_SEED, n_modes=256, multiscale=True, with_T=True)
+    snaps = [fourier_snapshot(grid, modes, h * DT_MET, device=dev, as_numpy=False) for h in range(3)]
+    n = args.particles if args.particles != N_PART else PREC_N
+    st0 = uniform_particles(n, grid.plev, PREC_SEED)
+    init = M.Particles.from_numpy(st0, device=dev)
+    prm = M.DiffParams()
+    stream = torch.cuda.Stream(device=dev)
+    sub_ids = np.linspace(0, n - 1, min(PREC_SUB, n)).astype(np.int64)
+    psteps = n * int(round(PREC_T_END / DT))
+    at = lambda t: (snaps[int(round(t / DT_MET))]["u"], snaps[int(round(t / DT_MET))]["v"],
+                    snaps[int(round(t / DT_MET))]["w"], snaps[int(round(t / DT_MET))]["T"])
+    results = {}
+    finals = {}
+    for name, storage in (("fp32", M.MPTRAC_FP32), ("bf16", M.MPTRAC_BF16), ("fp16", M.MPTRAC_FP16)):
+        ctx = M.Context(grid, storage, nvars=4)
+        ctx.set_launch(2, False)
+        work = init.clone()
+        sim = Simulation(ctx, at, DT_MET, work, DT, prm, SEED_RNG, SORT_EVERY)
+
+        def one_pass():
+            with torch.cuda.stream(stream):
+                work.copy_(init)
+                sim.run(0.0, PREC_T_END, stream=stream)
+        for _ in range(args.warmup):
+            one_pass()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            one_pass()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.steps
+        got = work.to_numpy()
+        pos = np.empty(n, dtype=np.int64)
+        pos[got["id"]] = np.arange(n)
+        finals[name] = {k: got[k][pos[sub_ids]] for k in ("lon", "lat", "p")}
+        results[name] = {"ms_per_pass": ms, "particle_steps_per_s": psteps / (ms / 1000.0),
+                         "slot_bytes": int(grid.npoints * (16 if storage == M.MPTRAC_FP32 else 8))}
+        ctx.close()
+        del work, sim
+        torch.cuda.empty_cache()
+    # float64 oracle on the subset, from the float32 fields (the stored-value error of
+    # bf16/fp16 plus the float32 arithmetic of every storage)
+    host = [{k: v.cpu().numpy() for k, v in s.items() if k in ("u", "v", "w")} for s in snaps]
+    del snaps
+    torch.cuda.empty_cache()
+    sub = {k: v[sub_ids] for k, v in st0.items()}
+    t0 = time.perf_counter()
+    ref = run_schedule(grid, lambda t: host[int(round(t / DT_MET))], DT_MET, sub, 0.0, PREC_T_END, DT,
+                       tr.DiffParams(), SEED_RNG)
+    oracle_s = time.perf_counter() - t0
+    for name, fin in finals.items():
+        km = great_circle_km(fin["lon"], fin["lat"], ref["lon"], ref["lat"])
+        dp = np.abs(fin["p"] - ref["p"]) / ref["p"]
+        results[name].update({"km_median": float(np.median(km)), "km_p99": float(np.quantile(km, 0.99)),
+                              "km_max": float(km.max()), "dp_rel_median": float(np.median(dp)),
+                              "dp_rel_p99": float(np.quantile(dp, 0.99))})
+        results[name]["speedup_vs_fp32"] = results["fp32"]["ms_per_pass"] / results[name]["ms_per_pass"]
+    line = {"metric": METRIC, "value": results["bf16"]["particle_steps_per_s"], "unit": "particle-steps/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": results["bf16"]["ms_per_pass"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 storage / f32 arithmetic", "data": "synthetic",
+            "config": {"workload": "0.3deg 1200x601x137 multiscale Fourier wind (256 modes), u/v/omega/T, "
+                                   f"{n} particles, 12 h (240 fused steps), sort every 20; error vs the float64 "
+                                   f"oracle on {sub_ids.size} particles", "oracle_seconds": oracle_s},
+            "precision": results}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -424,7 +513,7 @@ def main():
     ap.add_argument("--particles", type=int, default=N_PART)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="transport", choices=["transport", "batch"])
+    ap.add_argument("--workload", default="transport", choices=["transport", "batch", "precision"])
     ap.add_argument("--count-scale", type=float, default=1.0)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -440,6 +529,8 @@ def main():
         __graft_entry__.build()
         if args.workload == "batch":
             run_batch(args, rank, world)
+        elif args.workload == "precision":
+            run_precision(args, rank, world)
         else:
             run_ours(args, rank, world)
     if world > 1:
