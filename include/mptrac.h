@@ -231,6 +231,82 @@ int mptrac_set_launch(mptrac_ctx* ctx, int variant, int persistent);
 #define MPTRAC_SORT_NOALLOC_MAX_N 262144
 int mptrac_sort_noalloc(mptrac_ctx* ctx, const mptrac_particles* parts, uintptr_t stream);
 
+/* ---- learned displacement surrogate (the project's addition; the paper has
+ * no learned component) -----------------------------------------------------
+ * A small MLP maps a particle's local wind stencil to its displacement over
+ * one 30-minute segment (10 plain midpoint substeps of 180 s):
+ *   features (MPTRAC_SURR_NFEAT = 168, zero-padded to MPTRAC_SURR_KPAD = 176):
+ *     u, v, omega at the 3x3x3 grid nodes around the nearest node on both
+ *     snapshots, ordered [snapshot][variable][dk][dj][di]; the offsets of the
+ *     position from that node in grid units (lon, lat, fractional level); the
+ *     time weight; sin(lat), cos(lat);
+ *   x_hat = (x - mu_x)/sd_x, z1 = x_hat W1 + b1, h1 = gelu(z1), z2 = h1 W2 + b2,
+ *   h2 = gelu(z2), y_hat = h2 W3 + b3, y = y_hat sd_y + mu_y, with
+ *   gelu(x) = x/2 (1 + erf(x/sqrt 2));
+ *   outputs: east and north displacement [m] at the start latitude, ln(p1/p0).
+ * Parameters: one float32 vector of MPTRAC_SURR_NPARAM values laid out as
+ * W1 [176][128] (row-major, rows 168..175 unused), b1 [128], W2 [128][128],
+ * b2 [128], W3 [128][3], b3 [3].  GEMMs run on tensor cores in bfloat16 with
+ * float32 accumulation; loss, biases and Adam in float32. */
+#define MPTRAC_SURR_NFEAT   168
+#define MPTRAC_SURR_KPAD    176
+#define MPTRAC_SURR_HIDDEN  128
+#define MPTRAC_SURR_NOUT    3
+#define MPTRAC_SURR_NPARAM  39555
+
+typedef struct mptrac_surr mptrac_surr;   /* opaque: parameters, Adam state, activations */
+
+/* Creates a surrogate able to process up to max_batch samples per call (device
+ * buffers sized for it); parameters, Adam moments and the normalisation start
+ * at zero / identity. */
+int mptrac_surr_create(mptrac_surr** out, int64_t max_batch);
+int mptrac_surr_destroy(mptrac_surr* s);
+/* HOST arrays of MPTRAC_SURR_NPARAM floats (copied synchronously). */
+int mptrac_surr_set_params(mptrac_surr* s, const float* params);
+int mptrac_surr_get_params(const mptrac_surr* s, float* params);
+/* Gradients of the last mptrac_surr_grads / mptrac_surr_train_step (HOST out). */
+int mptrac_surr_get_grads(const mptrac_surr* s, float* grads);
+/* Feature and target normalisation, HOST arrays: mu_x, sd_x of KPAD entries
+ * (entries >= NFEAT ignored), mu_y, sd_y of NOUT entries; sd > 0. */
+int mptrac_surr_set_norm(mptrac_surr* s, const float* mu_x, const float* sd_x, const float* mu_y,
+                         const float* sd_y);
+/* Raw features of every particle at time t (t within the loaded snapshots)
+ * into DEVICE feat [n][KPAD].  Grid needs nx, ny, nz >= 3. */
+int mptrac_surr_features(mptrac_ctx* ctx, const mptrac_particles* parts, double t, float* feat,
+                         uintptr_t stream);
+/* Targets from start and end positions (DEVICE float64 arrays of n) into
+ * DEVICE y [n][NOUT]: dx = R cos(lat0) dlon, dy = R dlat (radians, dlon folded
+ * into [-180, 180) degrees), dz = ln(p1/p0). */
+int mptrac_surr_targets(int64_t n, const double* lon0, const double* lat0, const double* p0,
+                        const double* lon1, const double* lat1, const double* p1, float* y,
+                        uintptr_t stream);
+/* Adds the column sums and sums of squares of DEVICE data [n][ncol] (float32)
+ * to DEVICE sum[ncol], sumsq[ncol] (float64; the caller zeroes them). */
+int mptrac_surr_colstats(const float* data, int64_t n, int ncol, double* sum, double* sumsq,
+                         uintptr_t stream);
+/* Normalised outputs y_hat of n <= max_batch DEVICE raw feature rows into
+ * DEVICE y_hat [n][8] (columns 3..7 are zero padding). */
+int mptrac_surr_forward(mptrac_surr* s, const float* x, int64_t n, float* y_hat, uintptr_t stream);
+/* Loss (mean squared error in normalised units, ADDED to DEVICE *loss) and
+ * gradients for n <= max_batch samples (DEVICE x [n][KPAD], y [n][NOUT] raw). */
+int mptrac_surr_grads(mptrac_surr* s, const float* x, const float* y, int64_t n, float* loss,
+                      uintptr_t stream);
+/* mptrac_surr_grads followed by one Adam step (beta1 0.9, beta2 0.999,
+ * eps 1e-8, bias correction with step >= 1) at learning rate lr. */
+int mptrac_surr_train_step(mptrac_surr* s, const float* x, const float* y, int64_t n, float lr,
+                           int step, float* loss, uintptr_t stream);
+/* One 30-minute surrogate segment from time t (segment length dt_seg [s]):
+ * particles inside the training envelope (|lat| <= 80 deg, every standardised
+ * feature within +-4, [t, t + dt_seg] inside the loaded snapshots) move by
+ * the predicted displacement followed by the position rules; the others are
+ * left in place with fallback[i] = 1 (DEVICE uint8 [n]) for the plain
+ * integrator (mptrac_advect_masked).  Any n (processed in max_batch chunks). */
+int mptrac_surr_advance(mptrac_ctx* ctx, mptrac_surr* s, const mptrac_particles* parts, double t,
+                        double dt_seg, uint8_t* fallback, uintptr_t stream);
+/* mptrac_advect restricted to particles with mask[i] != 0 (DEVICE uint8 [n]). */
+int mptrac_advect_masked(mptrac_ctx* ctx, const mptrac_particles* parts, const uint8_t* mask,
+                         double t, double dt, int nsteps, uintptr_t stream);
+
 /* ---- inspection entry points (used by the parity tests) ---------------- */
 
 /* Cell keys of the sort, written to DEVICE array keys[n]. */

@@ -4,8 +4,10 @@ The computation lives in ``libmptrac.so`` (hand-written CUDA for sm_103a behind
 the C ABI of ``include/mptrac.h``); this package is its thin ctypes binding.
 PyTorch provides device memory and streams only.
 """
-from ._native import (Context, DiffParams, MptracError, Particles, load, philox,
+from ._native import (Context, DiffParams, MptracError, Particles, Surrogate, advect_masked, colstats,
+                      load, philox, surr_features, surr_targets,
                       MPTRAC_BF16, MPTRAC_FP16, MPTRAC_FP32, SIGNATURES, LIB_PATH)
 
-__all__ = ["Context", "DiffParams", "MptracError", "Particles", "load", "philox",
+__all__ = ["Context", "DiffParams", "MptracError", "Particles", "Surrogate", "advect_masked", "colstats",
+           "load", "philox", "surr_features", "surr_targets",
            "MPTRAC_FP32", "MPTRAC_BF16", "MPTRAC_FP16", "SIGNATURES", "LIB_PATH"]

@@ -71,6 +71,24 @@ SIGNATURES = {
     "mptrac_sort_at": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_double, C.c_void_p, C.c_size_t,
                                  C.c_void_p]),
     "mptrac_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "mptrac_advect_masked": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_void_p, C.c_double, C.c_double,
+                                       C.c_int, C.c_void_p]),
+    "mptrac_surr_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int64]),
+    "mptrac_surr_destroy": (C.c_int, [C.c_void_p]),
+    "mptrac_surr_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mptrac_surr_get_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mptrac_surr_get_grads": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mptrac_surr_set_norm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mptrac_surr_features": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_double, C.c_void_p, C.c_void_p]),
+    "mptrac_surr_targets": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mptrac_surr_colstats": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mptrac_surr_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "mptrac_surr_grads": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "mptrac_surr_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_int,
+                                         C.c_void_p, C.c_void_p]),
+    "mptrac_surr_advance": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(ParticlesDesc), C.c_double, C.c_double,
+                                      C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -295,3 +313,102 @@ def philox(ctr: torch.Tensor, seed: int, with_normals: bool = False, stream=None
     z = torch.empty(4, n, dtype=torch.float32, device=ctr.device) if with_normals else None
     check(load().mptrac_philox(_ptr(ctr), n, int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out), _ptr(z), _stream(stream)))
     return (out, z) if with_normals else out
+
+
+# ---------------------------------------------------------------------------
+# learned surrogate
+# ---------------------------------------------------------------------------
+SURR_NFEAT, SURR_KPAD, SURR_HIDDEN, SURR_NOUT, SURR_NPARAM = 168, 176, 128, 3, 39555
+
+
+class Surrogate:
+    """Handle of ``mptrac_surr``: parameters, Adam state and activation buffers on the device."""
+
+    def __init__(self, max_batch: int = 65536):
+        h = C.c_void_p()
+        check(load().mptrac_surr_create(C.byref(h), int(max_batch)))
+        self.h, self.max_batch = h, int(max_batch)
+        self._loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+
+    def close(self):
+        if getattr(self, "h", None):
+            check(load().mptrac_surr_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.size == SURR_NPARAM
+        check(load().mptrac_surr_set_params(self.h, a.ctypes.data))
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(SURR_NPARAM, dtype=np.float32)
+        check(load().mptrac_surr_get_params(self.h, a.ctypes.data))
+        return a
+
+    def get_grads(self) -> np.ndarray:
+        a = np.empty(SURR_NPARAM, dtype=np.float32)
+        check(load().mptrac_surr_get_grads(self.h, a.ctypes.data))
+        return a
+
+    def set_norm(self, mu_x, sd_x, mu_y, sd_y):
+        arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float32)) for a in (mu_x, sd_x, mu_y, sd_y)]
+        check(load().mptrac_surr_set_norm(self.h, *[a.ctypes.data for a in arrs]))
+
+    def forward(self, x: torch.Tensor, stream=None) -> torch.Tensor:
+        n = x.shape[0]
+        y = torch.empty(n, 8, dtype=torch.float32, device=x.device)
+        check(load().mptrac_surr_forward(self.h, _ptr(x), n, _ptr(y), _stream(stream)))
+        return y
+
+    def grads(self, x: torch.Tensor, y: torch.Tensor, stream=None) -> torch.Tensor:
+        self._loss.zero_()
+        check(load().mptrac_surr_grads(self.h, _ptr(x), _ptr(y), x.shape[0], _ptr(self._loss), _stream(stream)))
+        return self._loss
+
+    def train_step(self, x: torch.Tensor, y: torch.Tensor, lr: float, step: int, loss: torch.Tensor,
+                   stream=None):
+        """One Adam step; the batch loss is added to the 1-element device tensor ``loss``."""
+        check(load().mptrac_surr_train_step(self.h, _ptr(x), _ptr(y), x.shape[0], float(lr), int(step),
+                                            _ptr(loss), _stream(stream)))
+
+    def advance(self, ctx: "Context", parts: "Particles", t, dt_seg, fallback: torch.Tensor, stream=None):
+        check(load().mptrac_surr_advance(ctx.h, self.h, C.byref(parts.desc()), float(t), float(dt_seg),
+                                         _ptr(fallback), _stream(stream)), ctx.h)
+
+
+def surr_features(ctx: "Context", parts: "Particles", t, out: torch.Tensor | None = None, stream=None):
+    if out is None:
+        out = torch.empty(parts.n, SURR_KPAD, dtype=torch.float32, device=parts.lon.device)
+    check(load().mptrac_surr_features(ctx.h, C.byref(parts.desc()), float(t), _ptr(out), _stream(stream)), ctx.h)
+    return out
+
+
+def surr_targets(p0: "Particles", p1: "Particles", out: torch.Tensor | None = None, stream=None):
+    n = p0.n
+    if out is None:
+        out = torch.empty(n, SURR_NOUT, dtype=torch.float32, device=p0.lon.device)
+    check(load().mptrac_surr_targets(n, _ptr(p0.lon), _ptr(p0.lat), _ptr(p0.p), _ptr(p1.lon), _ptr(p1.lat),
+                                     _ptr(p1.p), _ptr(out), _stream(stream)))
+    return out
+
+
+def colstats(data: torch.Tensor, stream=None):
+    """Column mean and standard deviation of a [n][ncol] float32 device tensor (synchronises)."""
+    n, ncol = data.shape
+    s = torch.zeros(ncol, dtype=torch.float64, device=data.device)
+    s2 = torch.zeros(ncol, dtype=torch.float64, device=data.device)
+    check(load().mptrac_surr_colstats(_ptr(data), n, ncol, _ptr(s), _ptr(s2), _stream(stream)))
+    mean = (s / n).cpu().numpy()
+    var = np.maximum((s2 / n).cpu().numpy() - mean * mean, 0.0)
+    return mean, np.sqrt(var)
+
+
+def advect_masked(ctx: "Context", parts: "Particles", mask: torch.Tensor, t, dt, nsteps, stream=None):
+    check(load().mptrac_advect_masked(ctx.h, C.byref(parts.desc()), _ptr(mask), float(t), float(dt), int(nsteps),
+                                      _stream(stream)), ctx.h)

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmptrac.so")
-SOURCES = ["capi.cu", "step.cu", "met_pack.cu", "sort.cu"]
+SOURCES = ["capi.cu", "step.cu", "met_pack.cu", "sort.cu", "surrogate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -128,7 +128,7 @@ int ordered_slots(const mptrac_ctx* c, int& a, int& b) {
 
 int run_transport(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
                   const mptrac_diff_params* prm, uint64_t seed, uint64_t step0, int nsteps,
-                  uintptr_t stream, int mode) {
+                  uintptr_t stream, int mode, const uint8_t* mask = nullptr) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(MPTRAC_E_INVALID_ARG, "dt must be finite and > 0 (got %g)", dt);
     if (!std::isfinite(t)) return fail(MPTRAC_E_INVALID_ARG, "t must be finite");
@@ -173,6 +173,7 @@ int run_transport(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
     a.wp = P->wp;
     const bool use_win = P->release && c->n_rel > 0;
     a.win = use_win ? c->d_win : nullptr;
+    a.mask = mask;
     a.n_rel = c->n_rel;
     a.dt = (float)dt;
     a.half_dt = (float)(0.5 * dt);
@@ -524,6 +525,205 @@ int mptrac_met_slot_copy(const mptrac_ctx* c, int slot, void* rec_out, float* sc
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (rec_out) MPTRAC_CUDA(cudaMemcpyAsync(rec_out, c->d_met[slot], c->rec_bytes, cudaMemcpyDeviceToDevice, st));
     if (sc_out) MPTRAC_CUDA(cudaMemcpyAsync(sc_out, c->d_scales[slot], 4 * c->nz * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return ok();
+}
+
+int mptrac_advect_masked(mptrac_ctx* c, const mptrac_particles* P, const uint8_t* mask, double t,
+                         double dt, int nsteps, uintptr_t stream) {
+    if (P && P->n > 0 && !device_accessible(mask))
+        return fail(MPTRAC_E_INVALID_ARG, "mask must be device memory");
+    return run_transport(c, P, t, dt, nullptr, 0, 0, nsteps, stream, MODE_ADVECT, mask);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Learned surrogate: C ABI over surrogate.cu
+// ---------------------------------------------------------------------------
+struct mptrac_surr {
+    mptrac::Surrogate S;
+};
+
+extern "C" {
+
+int mptrac_surr_create(mptrac_surr** out, int64_t max_batch) {
+    if (!out) return fail(MPTRAC_E_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (max_batch < 64 || max_batch > (1 << 22))
+        return fail(MPTRAC_E_INVALID_ARG, "max_batch must be in [64, 4194304] (got %lld)", (long long)max_batch);
+    mptrac_surr* s = new (std::nothrow) mptrac_surr();
+    if (!s) return fail(MPTRAC_E_OOM, "host allocation failed");
+    cudaError_t e = surr_alloc(s->S, max_batch);
+    if (e == cudaSuccess) {
+        // identity normalisation
+        std::vector<float> one(MPTRAC_SURR_KPAD, 1.f);
+        e = cudaMemcpy(s->S.isd_x, one.data(), MPTRAC_SURR_KPAD * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(s->S.isd_y, one.data(), 8 * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(s->S.sd_y, one.data(), 8 * 4, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        surr_free(s->S);
+        delete s;
+        return fail(e == cudaErrorMemoryAllocation ? MPTRAC_E_OOM : MPTRAC_E_CUDA, "surrogate allocation failed: %s",
+                    cudaGetErrorString(e));
+    }
+    *out = s;
+    return ok();
+}
+
+int mptrac_surr_destroy(mptrac_surr* s) {
+    if (!s) return ok();
+    cudaDeviceSynchronize();
+    surr_free(s->S);
+    delete s;
+    return ok();
+}
+
+int mptrac_surr_set_params(mptrac_surr* s, const float* params) {
+    if (!s || !params) return fail(MPTRAC_E_INVALID_ARG, "NULL argument");
+    MPTRAC_CUDA(cudaMemcpy(s->S.theta, params, MPTRAC_SURR_NPARAM * 4, cudaMemcpyHostToDevice));
+    MPTRAC_CUDA(cudaMemset(s->S.m, 0, MPTRAC_SURR_NPARAM * 4));
+    MPTRAC_CUDA(cudaMemset(s->S.v, 0, MPTRAC_SURR_NPARAM * 4));
+    MPTRAC_CUDA(surr_cast(s->S, 0));
+    MPTRAC_CUDA(cudaDeviceSynchronize());
+    return ok();
+}
+
+int mptrac_surr_get_params(const mptrac_surr* s, float* params) {
+    if (!s || !params) return fail(MPTRAC_E_INVALID_ARG, "NULL argument");
+    MPTRAC_CUDA(cudaDeviceSynchronize());
+    MPTRAC_CUDA(cudaMemcpy(params, s->S.theta, MPTRAC_SURR_NPARAM * 4, cudaMemcpyDeviceToHost));
+    return ok();
+}
+
+int mptrac_surr_get_grads(const mptrac_surr* s, float* grads) {
+    if (!s || !grads) return fail(MPTRAC_E_INVALID_ARG, "NULL argument");
+    MPTRAC_CUDA(cudaDeviceSynchronize());
+    MPTRAC_CUDA(cudaMemcpy(grads, s->S.grad, MPTRAC_SURR_NPARAM * 4, cudaMemcpyDeviceToHost));
+    return ok();
+}
+
+int mptrac_surr_set_norm(mptrac_surr* s, const float* mu_x, const float* sd_x, const float* mu_y,
+                         const float* sd_y) {
+    if (!s || !mu_x || !sd_x || !mu_y || !sd_y) return fail(MPTRAC_E_INVALID_ARG, "NULL argument");
+    float mx[MPTRAC_SURR_KPAD], ix[MPTRAC_SURR_KPAD], my[8] = {0}, iy[8], sy[8];
+    for (int c = 0; c < MPTRAC_SURR_KPAD; ++c) {
+        const bool used = c < MPTRAC_SURR_NFEAT;
+        if (used && !(sd_x[c] > 0.f)) return fail(MPTRAC_E_INVALID_ARG, "sd_x[%d] must be > 0", c);
+        mx[c] = used ? mu_x[c] : 0.f;
+        ix[c] = used ? 1.f / sd_x[c] : 1.f;
+    }
+    for (int c = 0; c < 8; ++c) {
+        const bool used = c < MPTRAC_SURR_NOUT;
+        if (used && !(sd_y[c] > 0.f)) return fail(MPTRAC_E_INVALID_ARG, "sd_y[%d] must be > 0", c);
+        my[c] = used ? mu_y[c] : 0.f;
+        sy[c] = used ? sd_y[c] : 1.f;
+        iy[c] = 1.f / sy[c];
+    }
+    MPTRAC_CUDA(cudaMemcpy(s->S.mu_x, mx, sizeof(mx), cudaMemcpyHostToDevice));
+    MPTRAC_CUDA(cudaMemcpy(s->S.isd_x, ix, sizeof(ix), cudaMemcpyHostToDevice));
+    MPTRAC_CUDA(cudaMemcpy(s->S.mu_y, my, sizeof(my), cudaMemcpyHostToDevice));
+    MPTRAC_CUDA(cudaMemcpy(s->S.isd_y, iy, sizeof(iy), cudaMemcpyHostToDevice));
+    MPTRAC_CUDA(cudaMemcpy(s->S.sd_y, sy, sizeof(sy), cudaMemcpyHostToDevice));
+    return ok();
+}
+
+int mptrac_surr_features(mptrac_ctx* c, const mptrac_particles* P, double t, float* feat, uintptr_t stream) {
+    if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    int rc = check_particles(P, false);
+    if (rc) return rc;
+    if (c->nx < 3 || c->ny < 3 || c->nz < 3) return fail(MPTRAC_E_INVALID_ARG, "surrogate features need nx, ny, nz >= 3");
+    int s0, s1;
+    if ((rc = ordered_slots(c, s0, s1))) return rc;
+    const double t0 = c->t_slot[s0], t1 = c->t_slot[s1];
+    if (!(t >= t0 && t <= t1)) return fail(MPTRAC_E_TIME_RANGE, "t = %g outside [%g, %g]", t, t0, t1);
+    if (P->n == 0) return ok();
+    if (!device_accessible(feat)) return fail(MPTRAC_E_INVALID_ARG, "feat must be device memory");
+    MPTRAC_CUDA(launch_surr_features(c->storage, c->geo, MetView{c->d_met[s0], c->d_scales[s0]},
+                                     MetView{c->d_met[s1], c->d_scales[s1]}, P->n, P->lon, P->lat, P->p,
+                                     (float)((t - t0) / (t1 - t0)), feat, reinterpret_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
+int mptrac_surr_targets(int64_t n, const double* lon0, const double* lat0, const double* p0, const double* lon1,
+                        const double* lat1, const double* p1, float* y, uintptr_t stream) {
+    if (n < 0) return fail(MPTRAC_E_INVALID_ARG, "n < 0");
+    if (n == 0) return ok();
+    const void* ptrs[] = {lon0, lat0, p0, lon1, lat1, p1, y};
+    for (const void* q : ptrs)
+        if (!device_accessible(q)) return fail(MPTRAC_E_INVALID_ARG, "target arrays must be device memory");
+    MPTRAC_CUDA(launch_surr_targets(n, lon0, lat0, p0, lon1, lat1, p1, y, reinterpret_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
+int mptrac_surr_colstats(const float* data, int64_t n, int ncol, double* sum, double* sumsq, uintptr_t stream) {
+    if (n < 0 || ncol <= 0 || ncol > 4096) return fail(MPTRAC_E_INVALID_ARG, "bad size");
+    if (n == 0) return ok();
+    if (!device_accessible(data) || !device_accessible(sum) || !device_accessible(sumsq))
+        return fail(MPTRAC_E_INVALID_ARG, "colstats arrays must be device memory");
+    MPTRAC_CUDA(launch_colstats(data, n, ncol, sum, sumsq, reinterpret_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
+int mptrac_surr_forward(mptrac_surr* s, const float* x, int64_t n, float* y_hat, uintptr_t stream) {
+    if (!s) return fail(MPTRAC_E_NOT_INIT, "surrogate is NULL");
+    if (n < 0 || n > s->S.max_batch) return fail(MPTRAC_E_INVALID_ARG, "n must be in [0, max_batch]");
+    if (n == 0) return ok();
+    if (!device_accessible(x) || (y_hat && !device_accessible(y_hat)))
+        return fail(MPTRAC_E_INVALID_ARG, "x and y_hat must be device memory");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    MPTRAC_CUDA(surr_forward(s->S, x, n, st));
+    if (y_hat) MPTRAC_CUDA(cudaMemcpyAsync(y_hat, s->S.Yh, (size_t)n * 8 * 4, cudaMemcpyDeviceToDevice, st));
+    return ok();
+}
+
+int mptrac_surr_grads(mptrac_surr* s, const float* x, const float* y, int64_t n, float* loss, uintptr_t stream) {
+    if (!s) return fail(MPTRAC_E_NOT_INIT, "surrogate is NULL");
+    if (n <= 0 || n > s->S.max_batch) return fail(MPTRAC_E_INVALID_ARG, "n must be in [1, max_batch]");
+    if (!device_accessible(x) || !device_accessible(y) || !device_accessible(loss))
+        return fail(MPTRAC_E_INVALID_ARG, "x, y and loss must be device memory");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    MPTRAC_CUDA(surr_forward(s->S, x, n, st));
+    MPTRAC_CUDA(surr_backward(s->S, y, n, loss, st));
+    return ok();
+}
+
+int mptrac_surr_train_step(mptrac_surr* s, const float* x, const float* y, int64_t n, float lr, int step,
+                           float* loss, uintptr_t stream) {
+    if (step < 1 || !(lr > 0.f)) return fail(MPTRAC_E_INVALID_ARG, "step must be >= 1 and lr > 0");
+    int rc = mptrac_surr_grads(s, x, y, n, loss, stream);
+    if (rc) return rc;
+    MPTRAC_CUDA(surr_adam(s->S, lr, step, reinterpret_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
+int mptrac_surr_advance(mptrac_ctx* c, mptrac_surr* s, const mptrac_particles* P, double t, double dt_seg,
+                        uint8_t* fallback, uintptr_t stream) {
+    if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    if (!s) return fail(MPTRAC_E_NOT_INIT, "surrogate is NULL");
+    int rc = check_particles(P, false);
+    if (rc) return rc;
+    if (c->nx < 3 || c->ny < 3 || c->nz < 3) return fail(MPTRAC_E_INVALID_ARG, "surrogate needs nx, ny, nz >= 3");
+    int s0, s1;
+    if ((rc = ordered_slots(c, s0, s1))) return rc;
+    const double t0 = c->t_slot[s0], t1 = c->t_slot[s1];
+    if (!(t >= t0 && t <= t1)) return fail(MPTRAC_E_TIME_RANGE, "t = %g outside [%g, %g]", t, t0, t1);
+    if (!(dt_seg > 0)) return fail(MPTRAC_E_INVALID_ARG, "dt_seg must be > 0");
+    if (P->n == 0) return ok();
+    if (!device_accessible(fallback)) return fail(MPTRAC_E_INVALID_ARG, "fallback must be device memory");
+    const int window_ok = (t + dt_seg <= t1 + 1e-9 * (t1 - t0)) ? 1 : 0;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const float w = (float)((t - t0) / (t1 - t0));
+    for (int64_t o = 0; o < P->n; o += s->S.max_batch) {
+        const int64_t cnt = std::min<int64_t>(s->S.max_batch, P->n - o);
+        MPTRAC_CUDA(launch_surr_features(c->storage, c->geo, MetView{c->d_met[s0], c->d_scales[s0]},
+                                         MetView{c->d_met[s1], c->d_scales[s1]}, cnt, P->lon + o, P->lat + o,
+                                         P->p + o, w, s->S.Xraw, st));
+        MPTRAC_CUDA(surr_forward(s->S, s->S.Xraw, cnt, st));
+        MPTRAC_CUDA(launch_surr_apply(s->S, cnt, window_ok, P->lon + o, P->lat + o, P->p + o, fallback + o,
+                                      c->lon0, c->geo.pmin_d, c->geo.pmax_d, st));
+    }
     return ok();
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <cstdint>
 #include <cstddef>
 
@@ -51,6 +52,7 @@ struct StepArgs {
     float* vp;
     float* wp;
     const int2* win;              // per-release active step window, or null
+    const uint8_t* mask;          // particles with mask[i] == 0 are left untouched, or null
     int n_rel;
     int nsteps;
     float dt, half_dt, kdeg;      // kdeg = 180 / (pi R)  [deg per metre]
@@ -91,5 +93,35 @@ cudaError_t run_sort(const Geo& g, const mptrac_particles& P, void* ws, int key_
 // ts/te, or release index >= nrel) get the key 2^key_bits, after every cell key.
 cudaError_t run_sort_at(const Geo& g, const mptrac_particles& P, void* ws, int key_bits, double t,
                         const double* ts, const double* te, int nrel, cudaStream_t s);
+
+// ---- learned surrogate (surrogate.cu) ------------------------------------
+struct Surrogate {
+    int64_t max_batch = 0;
+    float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    __nv_bfloat16 *W1b = nullptr, *W2b = nullptr, *W3b = nullptr;
+    float* b3p = nullptr;
+    float *mu_x = nullptr, *isd_x = nullptr, *mu_y = nullptr, *isd_y = nullptr, *sd_y = nullptr;
+    __nv_bfloat16 *Xh = nullptr, *H1 = nullptr, *H2 = nullptr, *dY = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
+    float *Z1 = nullptr, *Z2 = nullptr, *Yh = nullptr, *Xraw = nullptr;
+    uint8_t* env = nullptr;
+    float* loss_tmp = nullptr;
+};
+
+
+cudaError_t surr_alloc(Surrogate& S, int64_t max_batch);
+void surr_free(Surrogate& S);
+cudaError_t surr_cast(Surrogate& S, cudaStream_t s);
+cudaError_t surr_forward(Surrogate& S, const float* X, int64_t B, cudaStream_t s);
+cudaError_t surr_backward(Surrogate& S, const float* Yt, int64_t B, float* loss, cudaStream_t s);
+cudaError_t surr_adam(Surrogate& S, float lr, int step, cudaStream_t s);
+cudaError_t launch_surr_features(int storage, const Geo& g, MetView m0, MetView m1, int64_t n,
+                                 const double* lon, const double* lat, const double* p, float w,
+                                 float* X, cudaStream_t s);
+cudaError_t launch_surr_targets(int64_t n, const double* lon0, const double* lat0, const double* p0,
+                                const double* lon1, const double* lat1, const double* p1, float* Y,
+                                cudaStream_t s);
+cudaError_t launch_colstats(const float* D, int64_t n, int ncol, double* sum, double* sumsq, cudaStream_t s);
+cudaError_t launch_surr_apply(Surrogate& S, int64_t n, int window_ok, double* lon, double* lat, double* p,
+                              uint8_t* fallback, double lon0, double pmin, double pmax, cudaStream_t s);
 
 }  // namespace mptrac

@@ -24,6 +24,7 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "met_record.cuh"
 
 namespace mptrac {
 namespace {
@@ -159,24 +160,6 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, fl
 // ---------------------------------------------------------------------------
 // Met record access
 // ---------------------------------------------------------------------------
-template <int ST> struct RecT;
-template <> struct RecT<MPTRAC_FP32> { using T = float4; };
-template <> struct RecT<MPTRAC_BF16> { using T = uint2; };
-template <> struct RecT<MPTRAC_FP16> { using T = uint2; };
-
-template <int ST> __device__ __forceinline__ float4 decode(typename RecT<ST>::T r);
-template <> __device__ __forceinline__ float4 decode<MPTRAC_FP32>(float4 r) { return r; }
-template <> __device__ __forceinline__ float4 decode<MPTRAC_BF16>(uint2 r) {
-    return make_float4(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xFFFF0000u),
-                       __uint_as_float(r.y << 16), __uint_as_float(r.y & 0xFFFF0000u));
-}
-template <> __device__ __forceinline__ float4 decode<MPTRAC_FP16>(uint2 r) {
-    return make_float4(__half2float(__ushort_as_half((unsigned short)(r.x & 0xFFFFu))),
-                       __half2float(__ushort_as_half((unsigned short)(r.x >> 16))),
-                       __half2float(__ushort_as_half((unsigned short)(r.y & 0xFFFFu))),
-                       __half2float(__ushort_as_half((unsigned short)(r.y >> 16))));
-}
-
 template <typename T> __device__ __forceinline__ T ldg_rec(const T* p) { return __ldg(p); }
 
 // Shared-memory tables of one block.
@@ -414,6 +397,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
     const bool use_turb = (MODE != MODE_ADVECT) && a.turb;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < a.n; idx += stride) {
+        if (a.mask && !a.mask[idx]) continue;
         int nlo = 0, nhi = a.nsteps;
         uint32_t rel = 0;
         if (a.release) {

@@ -1,0 +1,557 @@
+// Learned displacement surrogate: stencil features, BF16 tensor-core MLP
+// (forward, backward, Adam) and inference with an envelope test.  The paper
+// has no learned component; this is the project's addition on top of the
+// advection module (arxiv 2211.12616, Section 3.2).
+//
+// Network (per sample): x_hat = (x - mu_x)/sd_x (176 = 168 features + 8 zero
+// pad), z1 = x_hat W1 + b1, h1 = gelu(z1), z2 = h1 W2 + b2, h2 = gelu(z2),
+// y_hat = h2 W3 + b3 (3 outputs, padded to 8 columns), y = y_hat sd_y + mu_y.
+// GEMM operands are bfloat16 with float32 accumulation (mma.sync m16n8k16);
+// biases, GELU, the loss and Adam run in float32 on float32 master weights.
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+#include "met_record.cuh"
+
+namespace mptrac {
+namespace {
+
+constexpr int NF = MPTRAC_SURR_NFEAT, KP = MPTRAC_SURR_KPAD, HID = MPTRAC_SURR_HIDDEN,
+              NO = MPTRAC_SURR_NOUT, NOP = 8;
+// offsets of the flat parameter vector
+constexpr int OW1 = 0, OB1 = OW1 + KP * HID, OW2 = OB1 + HID, OB2 = OW2 + HID * HID,
+              OW3 = OB2 + HID, OB3 = OW3 + HID * NO, NPAR = OB3 + NO;
+static_assert(NPAR == MPTRAC_SURR_NPARAM, "parameter count");
+
+constexpr double kR = 6371000.0;
+constexpr double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// features and targets
+// ---------------------------------------------------------------------------
+struct FeatArgs {
+    Geo g;
+    MetView m0, m1;
+    int64_t n;
+    const double *lon, *lat, *p;
+    float w;
+    float* X;            // [n][KP]
+};
+
+template <int ST>
+__global__ void __launch_bounds__(128) k_features(const FeatArgs a) {
+    const Geo& g = a.g;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    using R = typename RecT<ST>::T;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
+        const double lon = a.lon[q], lat = a.lat[q], p = a.p[q];
+        // nearest node, float64 like the definition
+        double r = fmod(lon - g.lon0_d, 360.0);
+        if (r < 0.0) r += 360.0;
+        const double x = r / g.dlon_d;
+        const double xr = floor(x + 0.5);
+        long long i0 = (long long)xr % g.nx;
+        if (i0 < 0) i0 += g.nx;
+        const double y = (lat - g.lat0_d) / g.dlat_d;
+        long long j0 = (long long)floor(y + 0.5);
+        j0 = j0 < 1 ? 1 : (j0 > g.ny - 2 ? g.ny - 2 : j0);
+        const double pc = fmin(fmax(p, g.pmin_d), g.pmax_d);
+        int lo = 0, hi = g.nz;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (g.plev_d[mid] >= pc) lo = mid + 1; else hi = mid;
+        }
+        int k = lo - 1;
+        k = k < 0 ? 0 : (k > g.nz - 2 ? g.nz - 2 : k);
+        double fz = (g.plev_d[k] - pc) / (g.plev_d[k] - g.plev_d[k + 1]);
+        fz = fmin(fmax(fz, 0.0), 1.0);
+        const double z = k + fz;
+        long long k0 = (long long)floor(z + 0.5);
+        k0 = k0 < 1 ? 1 : (k0 > g.nz - 2 ? g.nz - 2 : k0);
+        float* X = a.X + q * KP;
+        const R* rec[2] = {static_cast<const R*>(a.m0.rec), static_cast<const R*>(a.m1.rec)};
+        const float* sc[2] = {a.m0.scales, a.m1.scales};
+        for (int s = 0; s < 2; ++s) {
+            int col = 0;
+            for (int dk = -1; dk <= 1; ++dk) {
+                const int kk = (int)k0 + dk;
+                for (int dj = -1; dj <= 1; ++dj) {
+                    const int jj = (int)j0 + dj;
+                    for (int di = -1; di <= 1; ++di) {
+                        int ii = (int)i0 + di;
+                        ii = ii < 0 ? ii + g.nx : (ii >= g.nx ? ii - g.nx : ii);
+                        float4 v = decode<ST>(__ldg(rec[s] + ((int64_t)jj * g.nx + ii) * g.nz + kk));
+                        if (ST != MPTRAC_FP32) {
+                            v.x *= sc[s][kk];
+                            v.y *= sc[s][g.nz + kk];
+                            v.z *= sc[s][2 * g.nz + kk];
+                        }
+                        X[s * 81 + col] = v.x;
+                        X[s * 81 + 27 + col] = v.y;
+                        X[s * 81 + 54 + col] = v.z;
+                        ++col;
+                    }
+                }
+            }
+        }
+        // columns: [snapshot][variable][dk][dj][di] (2 x 3 x 27), then the extras
+        X[162] = (float)(x - xr);
+        X[163] = (float)(y - (double)j0);
+        X[164] = (float)(z - (double)k0);
+        X[165] = a.w;
+        double sn, cs;
+        sincos(lat * (kPi / 180.0), &sn, &cs);
+        X[166] = (float)sn;
+        X[167] = (float)cs;
+#pragma unroll
+        for (int c = NF; c < KP; ++c) X[c] = 0.f;
+    }
+}
+
+__global__ void k_targets(int64_t n, const double* lon0, const double* lat0, const double* p0,
+                          const double* lon1, const double* lat1, const double* p1, float* Y) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
+        double dl = fmod(lon1[q] - lon0[q] + 180.0, 360.0);
+        if (dl < 0.0) dl += 360.0;
+        dl -= 180.0;
+        const double c = cos(lat0[q] * (kPi / 180.0));
+        Y[3 * q + 0] = (float)(kR * c * dl * (kPi / 180.0));
+        Y[3 * q + 1] = (float)(kR * (lat1[q] - lat0[q]) * (kPi / 180.0));
+        Y[3 * q + 2] = (float)log(p1[q] / p0[q]);
+    }
+}
+
+// column sums and sums of squares (float partials per block, float64 totals)
+__global__ void k_colstats(const float* __restrict__ D, int64_t n, int ncol, int rows_per_block,
+                           double* sum, double* sumsq) {
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t r1 = min(n, r0 + rows_per_block);
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+        float s = 0.f, s2 = 0.f, comp = 0.f, comp2 = 0.f;
+        for (int64_t r = r0; r < r1; ++r) {
+            const float v = D[r * ncol + c];
+            // compensated summation keeps the float partials accurate
+            float yv = v - comp, t = s + yv;
+            comp = (t - s) - yv;
+            s = t;
+            float y2 = v * v - comp2, t2 = s2 + y2;
+            comp2 = (t2 - s2) - y2;
+            s2 = t2;
+        }
+        atomicAdd(&sum[c], (double)s);
+        atomicAdd(&sumsq[c], (double)s2);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// BF16 tensor-core GEMM (mma.sync m16n8k16, f32 accumulate) with epilogues
+// C[M x N] = A[M x K] * B[K x N]; element (m, k) of A at A[m*sam + k*sak],
+// element (k, n) of B at B[k*sbk + n*sbn]; optional split over K.
+// ---------------------------------------------------------------------------
+enum Epi { EPI_ATOMIC_F32 = 0, EPI_BIAS_GELU = 1, EPI_BIAS_F32 = 2, EPI_GELU_BWD = 3 };
+
+struct GemmArgs {
+    const __nv_bfloat16* A;
+    const __nv_bfloat16* B;
+    int64_t M, N, K;
+    int64_t sam, sak, sbk, sbn;
+    int64_t kchunk;         // K range per blockIdx.z
+    // epilogue
+    float* Cf;              // f32 output (atomic accumulate / pre-activation / y_hat)
+    __nv_bfloat16* Cb;      // bf16 output (activation / gradient)
+    const float* bias;
+    const float* Zin;       // pre-activation for the GELU derivative
+    int64_t ldc;
+    int64_t n_valid;        // columns >= n_valid are not written
+};
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x) {
+    return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+constexpr int TM = 64, TN = 64, TK = 32, TKP = TK + 8;
+
+template <int EPI>
+__global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
+    __shared__ __nv_bfloat16 As[TM][TKP];   // [m][k]
+    __shared__ __nv_bfloat16 Bs[TN][TKP];   // [n][k]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 1, wn = warp & 1;          // 2 x 2 warps, 32 x 32 each
+    const int gq = lane >> 2, tq = lane & 3;
+    const int64_t m0 = (int64_t)blockIdx.x * TM, n0 = (int64_t)blockIdx.y * TN;
+    const int64_t kb0 = (int64_t)blockIdx.z * g.kchunk;
+    const int64_t kend = min(g.K, kb0 + g.kchunk);
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
+    const __nv_bfloat16 zero = __float2bfloat16(0.f);
+    const bool a_mfast = g.sam == 1, b_nfast = g.sbn == 1;
+    for (int64_t kb = kb0; kb < kend; kb += TK) {
+        for (int e = tid; e < TM * TK; e += 128) {
+            const int r = a_mfast ? (e % TM) : (e / TK), c = a_mfast ? (e / TM) : (e % TK);
+            const int64_t m = m0 + r, k = kb + c;
+            As[r][c] = (m < g.M && k < kend) ? g.A[m * g.sam + k * g.sak] : zero;
+        }
+        for (int e = tid; e < TN * TK; e += 128) {
+            const int r = b_nfast ? (e % TN) : (e / TK), c = b_nfast ? (e / TN) : (e % TK);
+            const int64_t n = n0 + r, k = kb + c;
+            Bs[r][c] = (n < g.N && k < kend) ? g.B[k * g.sbk + n * g.sbn] : zero;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; kk += 16) {
+            uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm * 32 + i * 16 + gq;
+                af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * tq]);
+                af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * tq]);
+                af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * tq + 8]);
+                af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * tq + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int nn = wn * 32 + j * 8 + gq;
+                bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[nn][kk + 2 * tq]);
+                bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[nn][kk + 2 * tq + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
+        }
+        __syncthreads();
+    }
+    // epilogue: c0,c1 -> (row gq, cols 2tq, 2tq+1); c2,c3 -> (row gq+8, same cols)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int64_t m = m0 + wm * 32 + i * 16 + gq + (c >> 1) * 8;
+                const int64_t n = n0 + wn * 32 + j * 8 + 2 * tq + (c & 1);
+                if (m >= g.M || n >= g.N || n >= g.n_valid) continue;
+                const float v = acc[i][j][c];
+                const int64_t o = m * g.ldc + n;
+                if (EPI == EPI_ATOMIC_F32) {
+                    atomicAdd(&g.Cf[o], v);
+                } else if (EPI == EPI_BIAS_GELU) {
+                    const float z = v + g.bias[n];
+                    g.Cf[o] = z;
+                    g.Cb[o] = __float2bfloat16_rn(gelu(z));
+                } else if (EPI == EPI_BIAS_F32) {
+                    g.Cf[o] = v + g.bias[n];
+                } else {
+                    g.Cb[o] = __float2bfloat16_rn(v * gelu_grad(g.Zin[o]));
+                }
+            }
+}
+
+// x_hat = bf16((x - mu)/sd), zero pad; one warp per row; env[row] = max |x_hat| <= 4
+__global__ void k_normalise(const float* __restrict__ X, int64_t n, const float* mu, const float* isd,
+                            __nv_bfloat16* Xh, uint8_t* env) {
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    float mx = 0.f;
+    for (int c = lane; c < KP; c += 32) {
+        float v = 0.f;
+        if (c < NF) {
+            v = (X[row * KP + c] - mu[c]) * isd[c];
+            mx = fmaxf(mx, fabsf(v));
+        }
+        Xh[row * KP + c] = __float2bfloat16_rn(v);
+    }
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (env && lane == 0) env[row] = (mx <= 4.f) ? 1 : 0;
+}
+
+// loss = mean (y_hat - t_hat)^2 over the 3 outputs; dY = 2 (y_hat - t_hat)/(3B) (bf16, 8 columns);
+// db3 += column sums of dY (float32)
+__global__ void k_loss(const float* __restrict__ Yh, const float* __restrict__ Yt, int64_t B,
+                       const float* mu_y, const float* isd_y, __nv_bfloat16* dY, float* loss, float* db3) {
+    __shared__ float red[4][32];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    float l = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
+    const float scale = 2.f / (3.f * (float)B);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < B; q += stride) {
+        float dd[NO];
+#pragma unroll
+        for (int j = 0; j < NO; ++j) {
+            const float r = Yh[q * NOP + j] - (Yt[q * NO + j] - mu_y[j]) * isd_y[j];
+            l += r * r;
+            dd[j] = scale * r;
+            dY[q * NOP + j] = __float2bfloat16_rn(dd[j]);
+        }
+#pragma unroll
+        for (int j = NO; j < NOP; ++j) dY[q * NOP + j] = __float2bfloat16(0.f);
+        d0 += dd[0];
+        d1 += dd[1];
+        d2 += dd[2];
+    }
+    float v[4] = {l, d0, d1, d2};
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        float x = v[c];
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        if (lane == 0) red[c][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        float x = 0.f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) x += red[threadIdx.x][i];
+        if (threadIdx.x == 0) atomicAdd(loss, x / (3.f * (float)B));
+        else atomicAdd(&db3[threadIdx.x - 1], x);
+    }
+}
+
+// out[c] += sum over rows of D[row][c] (bf16 input), c < 128
+__global__ void k_colsum_bf16(const __nv_bfloat16* __restrict__ D, int64_t n, int rows_per_block, float* out) {
+    const int c = threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block, r1 = min(n, r0 + rows_per_block);
+    float s = 0.f;
+    for (int64_t r = r0; r < r1; ++r) s += __bfloat162float(D[r * HID + c]);
+    atomicAdd(&out[c], s);
+}
+
+// Adam (Kingma & Ba) on the float32 master parameters, then the bf16 weight copies
+__global__ void k_adam(float* theta, const float* grad, float* m, float* v, int n, float lr, float b1,
+                       float b2, float eps, float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = grad[i];
+    const float mi = b1 * m[i] + (1.f - b1) * g;
+    const float vi = b2 * v[i] + (1.f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    theta[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void k_cast_weights(const float* theta, __nv_bfloat16* W1b, __nv_bfloat16* W2b,
+                               __nv_bfloat16* W3b, float* b3p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < KP * HID) W1b[i] = __float2bfloat16_rn(theta[OW1 + i]);
+    if (i < HID * HID) W2b[i] = __float2bfloat16_rn(theta[OW2 + i]);
+    if (i < HID * NOP) {
+        const int r = i / NOP, c = i % NOP;
+        W3b[i] = __float2bfloat16_rn(c < NO ? theta[OW3 + r * NO + c] : 0.f);
+    }
+    if (i < NOP) b3p[i] = i < NO ? theta[OB3 + i] : 0.f;
+}
+
+// Apply predicted displacements to in-envelope particles; flag the others for
+// the plain integrator.  Envelope: |lat| <= 80 deg and every standardised
+// feature within +-4 (env from k_normalise) and the window inside the interval.
+__global__ void k_apply(int64_t n, const float* __restrict__ Yh, const float* mu_y, const float* sd_y,
+                        const uint8_t* env, int window_ok, double* lon, double* lat, double* p,
+                        uint8_t* fallback, double lon0, double pmin, double pmax) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
+        const double la = lat[q];
+        const bool ok = window_ok && env[q] && fabs(la) <= 80.0;
+        fallback[q] = ok ? 0 : 1;
+        if (!ok) continue;
+        const double dx = (double)(Yh[q * NOP + 0] * sd_y[0] + mu_y[0]);
+        const double dy = (double)(Yh[q * NOP + 1] * sd_y[1] + mu_y[1]);
+        const double dz = (double)(Yh[q * NOP + 2] * sd_y[2] + mu_y[2]);
+        double lo = lon[q] + dx / (kR * cos(la * (kPi / 180.0))) * (180.0 / kPi);
+        double lt = la + dy / kR * (180.0 / kPi);
+        double pp = p[q] * exp(dz);
+        if (lt > 90.0) { lt = 180.0 - lt; lo += 180.0; }
+        else if (lt < -90.0) { lt = -180.0 - lt; lo += 180.0; }
+        double r = fmod(lo - lon0, 360.0);
+        if (r < 0.0) r += 360.0;
+        if (r >= 360.0) r -= 360.0;
+        lon[q] = lon0 + r;
+        lat[q] = lt;
+        p[q] = fmin(fmax(pp, pmin), pmax);
+    }
+}
+
+int grid1(int64_t n, int block) {
+    int64_t b = (n + block - 1) / block;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 1 << 20));
+}
+
+template <int EPI>
+cudaError_t gemm(const GemmArgs& g, int splits, cudaStream_t s) {
+    GemmArgs a = g;
+    if (splits < 1) splits = 1;
+    a.kchunk = ((g.K + splits - 1) / splits + TK - 1) / TK * TK;
+    if (a.kchunk <= 0) a.kchunk = TK;
+    const int gz = (int)((g.K + a.kchunk - 1) / a.kchunk);
+    dim3 grid((unsigned)((g.M + TM - 1) / TM), (unsigned)((g.N + TN - 1) / TN), (unsigned)std::max(gz, 1));
+    note_launches(1);
+    k_gemm<EPI><<<grid, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// model object
+// ---------------------------------------------------------------------------
+cudaError_t surr_alloc(Surrogate& S, int64_t B) {
+    S.max_batch = B;
+    void** ptrs[] = {(void**)&S.theta, (void**)&S.grad, (void**)&S.m, (void**)&S.v, (void**)&S.W1b,
+                     (void**)&S.W2b, (void**)&S.W3b, (void**)&S.b3p, (void**)&S.mu_x, (void**)&S.isd_x,
+                     (void**)&S.mu_y, (void**)&S.isd_y, (void**)&S.sd_y, (void**)&S.Xh, (void**)&S.H1,
+                     (void**)&S.H2, (void**)&S.dY, (void**)&S.dZ2, (void**)&S.dZ1, (void**)&S.Z1,
+                     (void**)&S.Z2, (void**)&S.Yh, (void**)&S.Xraw, (void**)&S.env, (void**)&S.loss_tmp};
+    const size_t sizes[] = {NPAR * 4, NPAR * 4, NPAR * 4, NPAR * 4, KP * HID * 2, HID * HID * 2, HID * NOP * 2,
+                            NOP * 4, KP * 4, KP * 4, NOP * 4, NOP * 4, NOP * 4, (size_t)B * KP * 2,
+                            (size_t)B * HID * 2, (size_t)B * HID * 2, (size_t)B * NOP * 2,
+                            (size_t)B * HID * 2, (size_t)B * HID * 2, (size_t)B * HID * 4,
+                            (size_t)B * HID * 4, (size_t)B * NOP * 4, (size_t)B * KP * 4, (size_t)B, 16};
+    for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]); ++i) {
+        cudaError_t e = cudaMalloc(ptrs[i], sizes[i]);
+        if (e != cudaSuccess) return e;
+        e = cudaMemset(*ptrs[i], 0, sizes[i]);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+void surr_free(Surrogate& S) {
+    void* ptrs[] = {S.theta, S.grad, S.m, S.v, S.W1b, S.W2b, S.W3b, S.b3p, S.mu_x, S.isd_x, S.mu_y,
+                    S.isd_y, S.sd_y, S.Xh, S.H1, S.H2, S.dY, S.dZ2, S.dZ1, S.Z1, S.Z2, S.Yh, S.Xraw,
+                    S.env, S.loss_tmp};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+cudaError_t surr_cast(Surrogate& S, cudaStream_t s) {
+    note_launches(1);
+    k_cast_weights<<<grid1(KP * HID, 256), 256, 0, s>>>(S.theta, S.W1b, S.W2b, S.W3b, S.b3p);
+    return cudaGetLastError();
+}
+
+// Forward of B rows of raw features X (device, [B][KP]) into S.Yh (normalised outputs).
+cudaError_t surr_forward(Surrogate& S, const float* X, int64_t B, cudaStream_t s) {
+    note_launches(1);
+    k_normalise<<<grid1(B * 32, 256), 256, 0, s>>>(X, B, S.mu_x, S.isd_x, S.Xh, S.env);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    GemmArgs g{};
+    g.A = S.Xh; g.B = S.W1b; g.M = B; g.N = HID; g.K = KP;
+    g.sam = KP; g.sak = 1; g.sbk = HID; g.sbn = 1;
+    g.Cf = S.Z1; g.Cb = S.H1; g.bias = S.theta + OB1; g.ldc = HID; g.n_valid = HID;
+    if ((e = gemm<EPI_BIAS_GELU>(g, 1, s)) != cudaSuccess) return e;
+    g.A = S.H1; g.B = S.W2b; g.K = HID; g.sam = HID;
+    g.Cf = S.Z2; g.Cb = S.H2; g.bias = S.theta + OB2;
+    if ((e = gemm<EPI_BIAS_GELU>(g, 1, s)) != cudaSuccess) return e;
+    g.A = S.H2; g.B = S.W3b; g.N = NOP; g.sbk = NOP;
+    g.Cf = S.Yh; g.Cb = nullptr; g.bias = S.b3p; g.ldc = NOP; g.n_valid = NOP;
+    return gemm<EPI_BIAS_F32>(g, 1, s);
+}
+
+// Gradients of the loss for B samples into S.grad (zeroed first); loss added to *loss.
+cudaError_t surr_backward(Surrogate& S, const float* Yt, int64_t B, float* loss, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(S.grad, 0, NPAR * 4, s);
+    if (e != cudaSuccess) return e;
+    note_launches(1);
+    k_loss<<<grid1(B, 256), 256, 0, s>>>(S.Yh, Yt, B, S.mu_y, S.isd_y, S.dY, loss, S.grad + OB3);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, B / 512));
+    GemmArgs g{};
+    // dW3 = H2^T dY  [HID x NO]
+    g.A = S.H2; g.sam = 1; g.sak = HID; g.B = S.dY; g.sbk = NOP; g.sbn = 1;
+    g.M = HID; g.N = NOP; g.K = B; g.Cf = S.grad + OW3; g.ldc = NO; g.n_valid = NO;
+    if ((e = gemm<EPI_ATOMIC_F32>(g, splits, s)) != cudaSuccess) return e;
+    // dZ2 = (dY W3^T) * gelu'(Z2)
+    g = GemmArgs{};
+    g.A = S.dY; g.sam = NOP; g.sak = 1; g.B = S.W3b; g.sbk = 1; g.sbn = NOP;
+    g.M = B; g.N = HID; g.K = NOP; g.Cb = S.dZ2; g.Zin = S.Z2; g.ldc = HID; g.n_valid = HID;
+    if ((e = gemm<EPI_GELU_BWD>(g, 1, s)) != cudaSuccess) return e;
+    // dW2 = H1^T dZ2, db2
+    g = GemmArgs{};
+    g.A = S.H1; g.sam = 1; g.sak = HID; g.B = S.dZ2; g.sbk = HID; g.sbn = 1;
+    g.M = HID; g.N = HID; g.K = B; g.Cf = S.grad + OW2; g.ldc = HID; g.n_valid = HID;
+    if ((e = gemm<EPI_ATOMIC_F32>(g, splits, s)) != cudaSuccess) return e;
+    const int rpb = 512;
+    note_launches(1);
+    k_colsum_bf16<<<grid1(B, rpb), HID, 0, s>>>(S.dZ2, B, rpb, S.grad + OB2);
+    // dZ1 = (dZ2 W2^T) * gelu'(Z1)
+    g = GemmArgs{};
+    g.A = S.dZ2; g.sam = HID; g.sak = 1; g.B = S.W2b; g.sbk = 1; g.sbn = HID;
+    g.M = B; g.N = HID; g.K = HID; g.Cb = S.dZ1; g.Zin = S.Z1; g.ldc = HID; g.n_valid = HID;
+    if ((e = gemm<EPI_GELU_BWD>(g, 1, s)) != cudaSuccess) return e;
+    // dW1 = Xh^T dZ1, db1
+    g = GemmArgs{};
+    g.A = S.Xh; g.sam = 1; g.sak = KP; g.B = S.dZ1; g.sbk = HID; g.sbn = 1;
+    g.M = KP; g.N = HID; g.K = B; g.Cf = S.grad + OW1; g.ldc = HID; g.n_valid = HID;
+    if ((e = gemm<EPI_ATOMIC_F32>(g, splits, s)) != cudaSuccess) return e;
+    note_launches(1);
+    k_colsum_bf16<<<grid1(B, rpb), HID, 0, s>>>(S.dZ1, B, rpb, S.grad + OB1);
+    return cudaGetLastError();
+}
+
+cudaError_t surr_adam(Surrogate& S, float lr, int step, cudaStream_t s) {
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    note_launches(1);
+    k_adam<<<grid1(NPAR, 256), 256, 0, s>>>(S.theta, S.grad, S.m, S.v, NPAR, lr, b1, b2, eps, c1, c2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return surr_cast(S, s);
+}
+
+cudaError_t launch_surr_features(int storage, const Geo& g, MetView m0, MetView m1, int64_t n,
+                                 const double* lon, const double* lat, const double* p, float w,
+                                 float* X, cudaStream_t s) {
+    FeatArgs a{g, m0, m1, n, lon, lat, p, w, X};
+    note_launches(1);
+    const int grid = grid1(n, 128);
+    switch (storage) {
+        case MPTRAC_FP32: k_features<MPTRAC_FP32><<<grid, 128, 0, s>>>(a); break;
+        case MPTRAC_BF16: k_features<MPTRAC_BF16><<<grid, 128, 0, s>>>(a); break;
+        default: k_features<MPTRAC_FP16><<<grid, 128, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_surr_targets(int64_t n, const double* lon0, const double* lat0, const double* p0,
+                                const double* lon1, const double* lat1, const double* p1, float* Y,
+                                cudaStream_t s) {
+    note_launches(1);
+    k_targets<<<grid1(n, 256), 256, 0, s>>>(n, lon0, lat0, p0, lon1, lat1, p1, Y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colstats(const float* D, int64_t n, int ncol, double* sum, double* sumsq, cudaStream_t s) {
+    const int rpb = 2048;
+    note_launches(1);
+    k_colstats<<<grid1(n, rpb), 256, 0, s>>>(D, n, ncol, rpb, sum, sumsq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_surr_apply(Surrogate& S, int64_t n, int window_ok, double* lon, double* lat, double* p,
+                              uint8_t* fallback, double lon0, double pmin, double pmax, cudaStream_t s) {
+    note_launches(1);
+    k_apply<<<grid1(n, 256), 256, 0, s>>>(n, S.Yh, S.mu_y, S.sd_y, S.env, window_ok, lon, lat, p, fallback,
+                                          lon0, pmin, pmax);
+    return cudaGetLastError();
+}
+
+}  // namespace mptrac

@@ -1,0 +1,204 @@
+"""Learned surrogate: GPU kernels against the float64 oracle, and what training gains."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import met as omet
+from oracle import surrogate as S
+from oracle import transport as tr
+from workloads import fourier_modes, fourier_snapshot, grid_global, uniform_particles
+
+from _gpu_common import M, make_ctx  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+T6H = 21600.0
+
+
+@pytest.fixture(scope="module")
+def field(M):
+    grid = grid_global(120, 61, 30)
+    m = fourier_modes(2)
+    f0 = fourier_snapshot(grid, m, 0.0)
+    f1 = fourier_snapshot(grid, m, T6H)
+    ctx = make_ctx(M, grid, [f0, f1], [0.0, T6H])
+    return grid, f0, f1, ctx
+
+
+def _bf16(a):
+    return omet.bf16_value(omet.bf16_code(np.asarray(a, np.float32))).reshape(np.shape(a))
+
+
+def test_features_match_oracle(M, field):
+    grid, f0, f1, ctx = field
+    st = uniform_particles(20_000, grid.plev, seed=3)
+    parts = M.Particles.from_numpy(st)
+    t = 5000.0
+    X = M.surr_features(ctx, parts, t).cpu().numpy()
+    ref = S.features(grid, f0, f1, t, 0.0, T6H, st["lon"], st["lat"], st["p"]).astype(np.float32)
+    # the nearest node is chosen in float64 on both sides: identical stencils
+    np.testing.assert_array_equal(X[:, :162], ref[:, :162])
+    np.testing.assert_allclose(X[:, 162:], ref[:, 162:], rtol=0, atol=2e-7)
+
+
+def test_targets_match_oracle(M):
+    rng = np.random.default_rng(1)
+    n = 5000
+    a = {"lon": rng.uniform(0, 360, n), "lat": rng.uniform(-80, 80, n), "p": rng.uniform(2e3, 9e4, n),
+         "id": np.arange(n, dtype=np.uint32)}
+    b = {"lon": np.mod(a["lon"] + rng.uniform(-1, 1, n), 360), "lat": a["lat"] + rng.uniform(-.5, .5, n),
+         "p": a["p"] * np.exp(rng.uniform(-.1, .1, n)), "id": a["id"]}
+    Y = M.surr_targets(M.Particles.from_numpy(a), M.Particles.from_numpy(b)).cpu().numpy()
+    ref = S.targets(a["lon"], a["lat"], a["p"], b["lon"], b["lat"], b["p"])
+    np.testing.assert_allclose(Y, ref, rtol=2e-7, atol=1e-6)
+
+
+def _random_model(seed, n):
+    rng = np.random.default_rng(seed)
+    P = S.init_params(seed)
+    P["b1"] = rng.standard_normal(S.HIDDEN) * 0.1
+    P["b2"] = rng.standard_normal(S.HIDDEN) * 0.1
+    P["b3"] = rng.standard_normal(S.NOUT) * 0.1
+    mu_x = rng.standard_normal(S.KPAD)
+    sd_x = rng.uniform(0.5, 2.0, S.KPAD)
+    mu_y = rng.standard_normal(S.NOUT)
+    sd_y = rng.uniform(0.5, 2.0, S.NOUT)
+    X = (mu_x + sd_x * rng.standard_normal((n, S.KPAD))).astype(np.float32)
+    X[:, S.NFEAT:] = 0
+    Y = (mu_y + sd_y * rng.standard_normal((n, S.NOUT))).astype(np.float32)
+    return P, mu_x, sd_x, mu_y, sd_y, X, Y
+
+
+def _oracle_bf16_inputs(P, mu_x, sd_x, X):
+    """The oracle network on the same bf16-rounded weights and standardised inputs as the GPU."""
+    xh = S.normalise(X, mu_x.astype(np.float32), sd_x.astype(np.float32))
+    xh[:, S.NFEAT:] = 0
+    Pb = {k: (_bf16(v) if k.startswith("W") else np.asarray(v, np.float32).astype(np.float64))
+          for k, v in P.items()}
+    return Pb, _bf16(xh)
+
+
+def test_forward_matches_oracle(M):
+    P, mu_x, sd_x, mu_y, sd_y, X, _ = _random_model(7, 4096)
+    sur = M.Surrogate(8192)
+    sur.set_params(S.flatten(P).astype(np.float32))
+    sur.set_norm(mu_x, sd_x, mu_y, sd_y)
+    yh = sur.forward(torch.from_numpy(X).cuda()).cpu().numpy()
+    Pb, xb = _oracle_bf16_inputs(P, mu_x, sd_x, X)
+    ref, _ = S.forward(Pb, xb)
+    assert np.all(yh[:, 3:] == 0)
+    err = np.linalg.norm(yh[:, :3] - ref) / np.linalg.norm(ref)
+    assert err < 1e-2, err            # bf16 rounding of the two hidden activations only
+
+
+def test_gradients_match_oracle(M):
+    P, mu_x, sd_x, mu_y, sd_y, X, Y = _random_model(8, 4096)
+    sur = M.Surrogate(8192)
+    sur.set_params(S.flatten(P).astype(np.float32))
+    sur.set_norm(mu_x, sd_x, mu_y, sd_y)
+    loss = sur.grads(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()).item()
+    g = S.unflatten(sur.get_grads().astype(np.float64))
+    Pb, xb = _oracle_bf16_inputs(P, mu_x, sd_x, X)
+    yt = (Y.astype(np.float64) - mu_y.astype(np.float32)) / sd_y.astype(np.float32)
+    rl, rg = S.loss_and_grads(Pb, xb, yt)
+    assert abs(loss - rl) / rl < 1e-2
+    for k in rg:
+        ref = rg[k][:S.NFEAT] if k == "W1" else rg[k]
+        got = g[k][:S.NFEAT] if k == "W1" else g[k]
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err < 3e-2, (k, err)
+    assert np.all(g["W1"][S.NFEAT:] == 0)
+
+
+def test_adam_step_matches_oracle(M):
+    P, mu_x, sd_x, mu_y, sd_y, X, Y = _random_model(9, 2048)
+    sur = M.Surrogate(4096)
+    theta0 = S.flatten(P).astype(np.float32)
+    sur.set_params(theta0)
+    sur.set_norm(mu_x, sd_x, mu_y, sd_y)
+    loss = torch.zeros(1, device="cuda")
+    sur.train_step(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), 1e-3, 1, loss)
+    theta1 = sur.get_params()
+    grad = sur.get_grads()
+    ref, _, _ = S.adam_step(theta0.astype(np.float64), grad.astype(np.float64), np.zeros_like(theta0, np.float64),
+                            np.zeros_like(theta0, np.float64), 1, 1e-3)
+    np.testing.assert_allclose(theta1, ref, rtol=1e-6, atol=1e-7)
+
+
+def _dataset(M, grid, ctx, f0, f1, n, seed):
+    st = uniform_particles(n, grid.plev, seed=seed, lat_max=75.0)
+    parts = M.Particles.from_numpy(st, meso=False, release=False)
+    t = 3600.0
+    X = M.surr_features(ctx, parts, t)
+    p1 = parts.clone()
+    ctx.advect(p1, t, 180.0, 10)
+    Y = M.surr_targets(parts, p1)
+    return st, X, Y, p1
+
+
+def test_advance_applies_prediction_and_flags_fallback(M, field):
+    grid, f0, f1, ctx = field
+    st, X, Y, _ = _dataset(M, grid, ctx, f0, f1, 3000, 11)
+    st["lat"][:5] = [85.0, -86.0, 81.0, 10.0, 20.0]
+    parts = M.Particles.from_numpy(st, meso=False, release=False)
+    Xh = M.surr_features(ctx, parts, 3600.0)
+    P = S.init_params(3)
+    sur = M.Surrogate(1024)                      # several chunks
+    sur.set_params(S.flatten(P).astype(np.float32))
+    mu_x, sd_x = M.colstats(Xh)
+    mu_y, sd_y = M.colstats(Y)
+    sd_x = np.where(sd_x > 1e-12, sd_x, 1.0)
+    sur.set_norm(mu_x, sd_x, mu_y, sd_y)
+    yh = torch.cat([sur.forward(Xh[o:o + 1024]) for o in range(0, 3000, 1024)]).cpu().numpy()
+    fb = torch.zeros(3000, dtype=torch.uint8, device="cuda")
+    sur.advance(ctx, parts, 3600.0, 1800.0, fb)
+    torch.cuda.synchronize()
+    fbn = fb.cpu().numpy()
+    got = parts.to_numpy()
+    xh = S.normalise(Xh.cpu().numpy(), mu_x, sd_x)
+    env = S.in_envelope(xh, st["lat"])
+    # envelope decisions agree except where a standardised feature sits at +-4 within rounding
+    near = np.any(np.abs(np.abs(xh[:, :S.NFEAT]) - 4.0) < 1e-4, axis=1)
+    np.testing.assert_array_equal(fbn[~near] == 0, env[~near])
+    assert fbn[0] == 1 and fbn[1] == 1 and fbn[2] == 1
+    inside = (fbn == 0)
+    y = yh[:, :3] * sd_y + mu_y
+    lon1, lat1, p1 = S.apply_displacement(st["lon"], st["lat"], st["p"], y.astype(np.float64))
+    lon1, lat1, p1 = tr.position_bc(lon1, lat1, p1, 0.0, grid.plev[-1], grid.plev[0])
+    np.testing.assert_allclose(got["lat"][inside], lat1[inside], atol=1e-9)
+    np.testing.assert_allclose(np.mod(got["lon"][inside] - lon1[inside] + 180, 360) - 180, 0, atol=1e-9)
+    np.testing.assert_allclose(got["p"][inside], p1[inside], rtol=1e-12)
+    np.testing.assert_array_equal(got["lon"][~inside], st["lon"][~inside])
+    # the window must fit inside the loaded interval, else everything falls back
+    sur.advance(ctx, parts, T6H - 900.0, 1800.0, fb)
+    torch.cuda.synchronize()
+    assert fb.cpu().numpy().all()
+
+
+def test_training_gains_over_untrained_and_first_order(M, field):
+    """A short training run learns the 30-minute displacement far better than the
+    untrained network and than a first-order step with the start-point wind."""
+    from paper_2211_12616_gb300.learn import evaluate, train
+    grid, f0, f1, ctx = field
+    st, X, Y, p1 = _dataset(M, grid, ctx, f0, f1, 200_000, 12)
+    sur = M.Surrogate(8192)
+    sur.set_params(S.flatten(S.init_params(5)).astype(np.float32))
+    hist, val = train(sur, X, Y, epochs=20, batch=4096, lr=2e-3, lr_min=1e-4)
+    assert hist[-1] < hist[0]
+    # untrained network with the same normalisation: loss of order 1
+    raw = M.Surrogate(8192)
+    raw.set_params(S.flatten(S.init_params(5)).astype(np.float32))
+    mu_x, sd_x = M.colstats(X)
+    mu_y, sd_y = M.colstats(Y)
+    raw.set_norm(mu_x, np.where(sd_x > 1e-12, sd_x, 1.0), mu_y, sd_y)
+    untrained = evaluate(raw, X[:20000], Y[:20000])
+    assert val < 0.05 * untrained, (val, untrained)
+    # first-order step u(x0, t0) * 1800 s from the stencil's centre node, in the same normalised units
+    Xn, Yn = X[:20000].cpu().numpy(), Y[:20000].cpu().numpy()
+    yn_true = (Yn - mu_y) / sd_y
+    cen = 13                                              # (dk, dj, di) = (0, 0, 0)
+    w = Xn[:, 165]
+    u = (1 - w) * Xn[:, cen] + w * Xn[:, 81 + cen]
+    v = (1 - w) * Xn[:, 27 + cen] + w * Xn[:, 81 + 27 + cen]
+    first = np.stack([u * 1800.0, v * 1800.0, Yn[:, 2]], axis=1)   # (dz taken exact: favours the baseline)
+    first_loss = np.mean(((first - mu_y) / sd_y - yn_true)[:, :2] ** 2) * 2 / 3
+    assert val < first_loss, (val, first_loss)
