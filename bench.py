@@ -504,6 +504,91 @@ def run_precision(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------
+# learned surrogate: train on plain trajectories, then 48 h runs
+# --------------------------------------------------------------------------
+SURR_SEED, SURR_T_END = 5, 48 * 3600.0
+
+
+def run_surrogate_bench(args, rank, world):
+    import torch
+
+    import paper_2211_12616_gb300 as M
+    from oracle.errors import great_circle_km
+    from paper_2211_12616_gb300 import learn
+    from paper_2211_12616_gb300.simulation import periodic_snapshots
+    from workloads import fourier_modes, fourier_snapshot, grid_1deg_60lev, uniform_particles
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    grid = grid_1deg_60lev()
+    modes = fourier_modes(SEED_FIELD)
+    snaps = [fourier_snapshot(grid, modes, h * DT_MET, device=dev, as_numpy=False) for h in range(4)]
+    at = periodic_snapshots(snaps, DT_MET)
+    ctx = M.Context(grid, M.MPTRAC_FP32)
+    ctx.set_launch(2, False)
+    n_train = args.train_samples
+    src = lambda count, seed: uniform_particles(count, grid.plev, SURR_SEED * 100000 + seed, lat_max=80.0)
+    t0 = time.perf_counter()
+    X, Y = learn.make_dataset(ctx, at, DT_MET, n_train, src)
+    t_data = time.perf_counter() - t0
+    sur = M.Surrogate(65536)
+    from oracle import surrogate as oS      # initial weights only (uniform fan-in init from a seed)
+    sur.set_params(oS.flatten(oS.init_params(SURR_SEED)).astype(np.float32))
+    t0 = time.perf_counter()
+    hist, val = learn.train(sur, X, Y, epochs=args.epochs, batch=8192, lr=2e-3, lr_min=2e-5)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del X, Y
+    torch.cuda.empty_cache()
+    n = args.particles
+    st0 = uniform_particles(n, grid.plev, SURR_SEED)
+    init = M.Particles.from_numpy(st0, device=dev, meso=False, release=False)
+    stream = torch.cuda.Stream(device=dev)
+
+    def timed(fn, parts):
+        parts.copy_(init)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        with torch.cuda.stream(stream):
+            out = fn(parts)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), out
+
+    runs = {}
+    plain = init.clone()
+    ms_plain, _ = timed(lambda P: learn.run_plain(ctx, P, at, DT_MET, 0.0, SURR_T_END, stream=stream), plain)
+    coarse = init.clone()
+    ms_coarse, _ = timed(lambda P: learn.run_plain(ctx, P, at, DT_MET, 0.0, SURR_T_END, dt=learn.DT_SEG,
+                                                   stream=stream), coarse)
+    sur_p = init.clone()
+    ms_sur, fb = timed(lambda P: learn.run_surrogate(ctx, sur, P, at, DT_MET, 0.0, SURR_T_END, stream=stream),
+                       sur_p)
+    ref = plain.to_numpy()
+    substeps = n * int(round(SURR_T_END / DT))
+    for name, parts, ms in (("plain_dt180", plain, ms_plain), ("midpoint_dt1800", coarse, ms_coarse),
+                            ("surrogate", sur_p, ms_sur)):
+        got = parts.to_numpy()
+        km = great_circle_km(got["lon"], got["lat"], ref["lon"], ref["lat"])
+        dp = np.abs(got["p"] - ref["p"]) / ref["p"]
+        runs[name] = {"ms_per_48h": ms, "substep_equivalents_per_s": substeps / (ms / 1000.0),
+                      "speedup_vs_plain": ms_plain / ms, "km_median": float(np.median(km)),
+                      "km_p99": float(np.quantile(km, 0.99)), "dp_rel_median": float(np.median(dp)),
+                      "dp_rel_p99": float(np.quantile(dp, 0.99))}
+    runs["surrogate"]["fallback_fraction"] = float(fb)
+    line = {"metric": METRIC, "value": runs["surrogate"]["substep_equivalents_per_s"], "unit": "particle-steps/s",
+            "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": ms_sur, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 MLP / f32", "data": "synthetic",
+            "config": {"workload": f"surrogate: trained on {n_train} plain 30-min trajectories (1deg field), "
+                                   f"{n} particles, 48 h; value in 180-s substep equivalents per second",
+                       "train_seconds": t_train, "dataset_seconds": t_data, "epochs": args.epochs,
+                       "train_loss": hist, "val_loss": val},
+            "surrogate": runs}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -513,7 +598,9 @@ def main():
     ap.add_argument("--particles", type=int, default=N_PART)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="transport", choices=["transport", "batch", "precision"])
+    ap.add_argument("--workload", default="transport", choices=["transport", "batch", "precision", "surrogate"])
+    ap.add_argument("--train-samples", type=int, default=10_000_000)
+    ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--count-scale", type=float, default=1.0)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -531,6 +618,10 @@ def main():
             run_batch(args, rank, world)
         elif args.workload == "precision":
             run_precision(args, rank, world)
+        elif args.workload == "surrogate":
+            if args.particles == N_PART:
+                args.particles = 10_000_000
+            run_surrogate_bench(args, rank, world)
         else:
             run_ours(args, rank, world)
     if world > 1:
