@@ -715,15 +715,9 @@ int mptrac_surr_advance(mptrac_ctx* c, mptrac_surr* s, const mptrac_particles* P
     const int window_ok = (t + dt_seg <= t1 + 1e-9 * (t1 - t0)) ? 1 : 0;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const float w = (float)((t - t0) / (t1 - t0));
-    for (int64_t o = 0; o < P->n; o += s->S.max_batch) {
-        const int64_t cnt = std::min<int64_t>(s->S.max_batch, P->n - o);
-        MPTRAC_CUDA(launch_surr_features(c->storage, c->geo, MetView{c->d_met[s0], c->d_scales[s0]},
-                                         MetView{c->d_met[s1], c->d_scales[s1]}, cnt, P->lon + o, P->lat + o,
-                                         P->p + o, w, s->S.Xraw, st));
-        MPTRAC_CUDA(surr_forward(s->S, s->S.Xraw, cnt, st));
-        MPTRAC_CUDA(launch_surr_apply(s->S, cnt, window_ok, P->lon + o, P->lat + o, P->p + o, fallback + o,
-                                      c->lon0, c->geo.pmin_d, c->geo.pmax_d, st));
-    }
+    MPTRAC_CUDA(launch_surr_fused(c->storage, s->S, c->geo, MetView{c->d_met[s0], c->d_scales[s0]},
+                                  MetView{c->d_met[s1], c->d_scales[s1]}, P->n, P->lon, P->lat, P->p, w,
+                                  window_ok, fallback, c->lon0, st));
     return ok();
 }
 

@@ -389,6 +389,272 @@ __global__ void k_apply(int64_t n, const float* __restrict__ Yh, const float* mu
     }
 }
 
+// ---------------------------------------------------------------------------
+// Fused inference: stencil gather -> standardise (shared memory, bf16) ->
+// three tensor-core layers -> displacement, for tiles of 128 particles.
+// 256 threads: in the gather each (particle, snapshot) pair has one thread;
+// in the MLP each warp owns 16 rows of the tile through all three layers, so
+// the layers need no block-wide barrier; the weights stay in shared memory
+// for the whole (persistent) launch.
+// ---------------------------------------------------------------------------
+constexpr int FT = 128;                 // particles per tile
+constexpr int XS = KP + 8, HS = HID + 8;  // padded row strides (bf16 elements): conflict-free fragments
+
+struct FusedArgs {
+    Geo g;
+    MetView m0, m1;
+    int64_t n;
+    double *lon, *lat, *p;
+    uint8_t* fallback;
+    float w;
+    int window_ok;
+    const __nv_bfloat16 *W1b, *W2b, *W3b;
+    const float *b1, *b2, *b3p, *mu_x, *isd_x, *mu_y, *sd_y;
+    double lon0, pmin, pmax;
+};
+
+constexpr size_t kFusedSmem = (size_t)HID * XS * 2 + (size_t)HID * HS * 2 + (size_t)NOP * HS * 2 +
+                              (size_t)(2 * HID + NOP) * 4 + (size_t)2 * KP * 4 + (size_t)FT * XS * 2 +
+                              (size_t)FT * HS * 2 + (size_t)FT * NOP * 4 + FT * 4;
+
+// nearest node (float64, the definition) and the offsets from it
+__device__ __forceinline__ void nearest_node(const Geo& g, double lon, double lat, double p, int& i0, int& j0,
+                                             int& k0, double& ox, double& oy, double& oz) {
+    double r = fmod(lon - g.lon0_d, 360.0);
+    if (r < 0.0) r += 360.0;
+    const double x = r / g.dlon_d;
+    const double xr = floor(x + 0.5);
+    long long ii = (long long)xr % g.nx;
+    if (ii < 0) ii += g.nx;
+    const double y = (lat - g.lat0_d) / g.dlat_d;
+    long long jj = (long long)floor(y + 0.5);
+    jj = jj < 1 ? 1 : (jj > g.ny - 2 ? g.ny - 2 : jj);
+    const double pc = fmin(fmax(p, g.pmin_d), g.pmax_d);
+    int lo = 0, hi = g.nz;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (g.plev_d[mid] >= pc) lo = mid + 1; else hi = mid;
+    }
+    int k = lo - 1;
+    k = k < 0 ? 0 : (k > g.nz - 2 ? g.nz - 2 : k);
+    double fz = (g.plev_d[k] - pc) / (g.plev_d[k] - g.plev_d[k + 1]);
+    fz = fmin(fmax(fz, 0.0), 1.0);
+    const double z = k + fz;
+    long long kk = (long long)floor(z + 0.5);
+    kk = kk < 1 ? 1 : (kk > g.nz - 2 ? g.nz - 2 : kk);
+    i0 = (int)ii;
+    j0 = (int)jj;
+    k0 = (int)kk;
+    ox = x - xr;
+    oy = y - (double)jj;
+    oz = z - (double)kk;
+}
+
+template <int ST>
+__global__ void __launch_bounds__(256, 1) k_surr_fused(const FusedArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __nv_bfloat16* W1T = reinterpret_cast<__nv_bfloat16*>(smem);            // [HID][XS]
+    __nv_bfloat16* W2T = W1T + HID * XS;                                      // [HID][HS]
+    __nv_bfloat16* W3T = W2T + HID * HS;                                      // [NOP][HS]
+    float* bias = reinterpret_cast<float*>(W3T + NOP * HS);                   // b1 | b2 | b3
+    float* mu = bias + 2 * HID + NOP;                                         // [KP]
+    float* isd = mu + KP;                                                     // [KP]
+    __nv_bfloat16* Xs = reinterpret_cast<__nv_bfloat16*>(isd + KP);          // [FT][XS]
+    __nv_bfloat16* Hs = Xs + FT * XS;                                         // [FT][HS]
+    float* Ys = reinterpret_cast<float*>(Hs + FT * HS);                       // [FT][NOP]
+    int* env = reinterpret_cast<int*>(Ys + FT * NOP);                         // [FT]
+    const int tid = threadIdx.x;
+    for (int e = tid; e < KP * HID; e += blockDim.x) {
+        const int k = e / HID, nn = e % HID;
+        W1T[nn * XS + k] = a.W1b[e];
+    }
+    for (int e = tid; e < HID * HID; e += blockDim.x) {
+        const int k = e / HID, nn = e % HID;
+        W2T[nn * HS + k] = a.W2b[e];
+    }
+    for (int e = tid; e < HID * NOP; e += blockDim.x) {
+        const int k = e / NOP, nn = e % NOP;
+        W3T[nn * HS + k] = a.W3b[e];
+    }
+    for (int e = tid; e < HID; e += blockDim.x) {
+        bias[e] = a.b1[e];
+        bias[HID + e] = a.b2[e];
+    }
+    if (tid < NOP) bias[2 * HID + tid] = a.b3p[tid];
+    for (int e = tid; e < KP; e += blockDim.x) {
+        mu[e] = a.mu_x[e];
+        isd[e] = a.isd_x[e];
+    }
+    __syncthreads();
+    const Geo& g = a.g;
+    using R = typename RecT<ST>::T;
+    const int lane = tid & 31, warp = tid >> 5, gq = lane >> 2, tq = lane & 3;
+    const int64_t ntiles = (a.n + FT - 1) / FT;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        // ---- gather and standardise: thread = (particle pl, snapshot sn) ----
+        {
+            const int pl = tid >> 1, sn = tid & 1;
+            const int64_t q = tile * FT + pl;
+            __nv_bfloat16* xr = Xs + pl * XS;
+            float mx = 0.f;
+            if (q < a.n) {
+                int i0, j0, k0;
+                double ox, oy, oz;
+                const double lat = a.lat[q];
+                nearest_node(g, a.lon[q], lat, a.p[q], i0, j0, k0, ox, oy, oz);
+                const R* rec = static_cast<const R*>(sn ? a.m1.rec : a.m0.rec);
+                const float* sc = sn ? a.m1.scales : a.m0.scales;
+                int col = 0;
+                for (int dk = -1; dk <= 1; ++dk) {
+                    const int kk = k0 + dk;
+                    for (int dj = -1; dj <= 1; ++dj) {
+                        const int jj = j0 + dj;
+#pragma unroll
+                        for (int di = -1; di <= 1; ++di) {
+                            int ii = i0 + di;
+                            ii = ii < 0 ? ii + g.nx : (ii >= g.nx ? ii - g.nx : ii);
+                            float4 v = decode<ST>(__ldg(rec + ((int64_t)jj * g.nx + ii) * g.nz + kk));
+                            if (ST != MPTRAC_FP32) {
+                                v.x *= sc[kk];
+                                v.y *= sc[g.nz + kk];
+                                v.z *= sc[2 * g.nz + kk];
+                            }
+                            const int c0 = sn * 81 + col;
+                            const float xu = (v.x - mu[c0]) * isd[c0];
+                            const float xv = (v.y - mu[c0 + 27]) * isd[c0 + 27];
+                            const float xw = (v.z - mu[c0 + 54]) * isd[c0 + 54];
+                            mx = fmaxf(mx, fmaxf(fabsf(xu), fmaxf(fabsf(xv), fabsf(xw))));
+                            xr[c0] = __float2bfloat16_rn(xu);
+                            xr[c0 + 27] = __float2bfloat16_rn(xv);
+                            xr[c0 + 54] = __float2bfloat16_rn(xw);
+                            ++col;
+                        }
+                    }
+                }
+                if (sn == 0) {
+                    double snl, csl;
+                    sincos(lat * (kPi / 180.0), &snl, &csl);
+                    const float ex[6] = {(float)ox, (float)oy, (float)oz, a.w, (float)snl, (float)csl};
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        const float xe = (ex[c] - mu[162 + c]) * isd[162 + c];
+                        mx = fmaxf(mx, fabsf(xe));
+                        xr[162 + c] = __float2bfloat16_rn(xe);
+                    }
+#pragma unroll
+                    for (int c = NF; c < KP; ++c) xr[c] = __float2bfloat16(0.f);
+                }
+            } else {
+                for (int c = sn; c < KP; c += 2) xr[c] = __float2bfloat16(0.f);
+                mx = 1e30f;
+            }
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+            if (sn == 0) env[pl] = (mx <= 4.f) ? 1 : 0;
+        }
+        __syncthreads();
+        // ---- MLP: warp owns rows r0 .. r0+15 ----
+        const int r0 = warp * 16;
+        {
+            float acc[16][4];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < KP; kk += 16) {
+                uint32_t af[4];
+                af[0] = *reinterpret_cast<const uint32_t*>(&Xs[(r0 + gq) * XS + kk + 2 * tq]);
+                af[1] = *reinterpret_cast<const uint32_t*>(&Xs[(r0 + gq + 8) * XS + kk + 2 * tq]);
+                af[2] = *reinterpret_cast<const uint32_t*>(&Xs[(r0 + gq) * XS + kk + 2 * tq + 8]);
+                af[3] = *reinterpret_cast<const uint32_t*>(&Xs[(r0 + gq + 8) * XS + kk + 2 * tq + 8]);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    uint32_t bf[2];
+                    bf[0] = *reinterpret_cast<const uint32_t*>(&W1T[(8 * j + gq) * XS + kk + 2 * tq]);
+                    bf[1] = *reinterpret_cast<const uint32_t*>(&W1T[(8 * j + gq) * XS + kk + 2 * tq + 8]);
+                    mma_bf16(acc[j], af, bf);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int row = r0 + gq + (c >> 1) * 8, col = 8 * j + 2 * tq + (c & 1);
+                    Hs[row * HS + col] = __float2bfloat16_rn(gelu(acc[j][c] + bias[col]));
+                }
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < HID; kk += 16) {
+                uint32_t af[4];
+                af[0] = *reinterpret_cast<const uint32_t*>(&Hs[(r0 + gq) * HS + kk + 2 * tq]);
+                af[1] = *reinterpret_cast<const uint32_t*>(&Hs[(r0 + gq + 8) * HS + kk + 2 * tq]);
+                af[2] = *reinterpret_cast<const uint32_t*>(&Hs[(r0 + gq) * HS + kk + 2 * tq + 8]);
+                af[3] = *reinterpret_cast<const uint32_t*>(&Hs[(r0 + gq + 8) * HS + kk + 2 * tq + 8]);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    uint32_t bf[2];
+                    bf[0] = *reinterpret_cast<const uint32_t*>(&W2T[(8 * j + gq) * HS + kk + 2 * tq]);
+                    bf[1] = *reinterpret_cast<const uint32_t*>(&W2T[(8 * j + gq) * HS + kk + 2 * tq + 8]);
+                    mma_bf16(acc[j], af, bf);
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int row = r0 + gq + (c >> 1) * 8, col = 8 * j + 2 * tq + (c & 1);
+                    Hs[row * HS + col] = __float2bfloat16_rn(gelu(acc[j][c] + bias[HID + col]));
+                }
+            __syncwarp();
+            float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kk = 0; kk < HID; kk += 16) {
+                uint32_t af[4], bf[2];
+                af[0] = *reinterpret_cast<const uint32_t*>(&Hs[(r0 + gq) * HS + kk + 2 * tq]);
+                af[1] = *reinterpret_cast<const uint32_t*>(&Hs[(r0 + gq + 8) * HS + kk + 2 * tq]);
+                af[2] = *reinterpret_cast<const uint32_t*>(&Hs[(r0 + gq) * HS + kk + 2 * tq + 8]);
+                af[3] = *reinterpret_cast<const uint32_t*>(&Hs[(r0 + gq + 8) * HS + kk + 2 * tq + 8]);
+                bf[0] = *reinterpret_cast<const uint32_t*>(&W3T[gq * HS + kk + 2 * tq]);
+                bf[1] = *reinterpret_cast<const uint32_t*>(&W3T[gq * HS + kk + 2 * tq + 8]);
+                mma_bf16(o, af, bf);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int row = r0 + gq + (c >> 1) * 8, col = 2 * tq + (c & 1);
+                Ys[row * NOP + col] = o[c] + bias[2 * HID + col];
+            }
+        }
+        __syncthreads();
+        // ---- apply the displacement (or flag the particle for the fallback) ----
+        if (tid < FT) {
+            const int64_t q = tile * FT + tid;
+            if (q < a.n) {
+                const double la = a.lat[q];
+                const bool ok = a.window_ok && env[tid] && fabs(la) <= 80.0;
+                a.fallback[q] = ok ? 0 : 1;
+                if (ok) {
+                    const double dx = (double)(Ys[tid * NOP + 0] * a.sd_y[0] + a.mu_y[0]);
+                    const double dy = (double)(Ys[tid * NOP + 1] * a.sd_y[1] + a.mu_y[1]);
+                    const double dz = (double)(Ys[tid * NOP + 2] * a.sd_y[2] + a.mu_y[2]);
+                    double lo = a.lon[q] + dx / (kR * cos(la * (kPi / 180.0))) * (180.0 / kPi);
+                    double lt = la + dy / kR * (180.0 / kPi);
+                    const double pp = a.p[q] * exp(dz);
+                    if (lt > 90.0) { lt = 180.0 - lt; lo += 180.0; }
+                    else if (lt < -90.0) { lt = -180.0 - lt; lo += 180.0; }
+                    double r = fmod(lo - a.lon0, 360.0);
+                    if (r < 0.0) r += 360.0;
+                    if (r >= 360.0) r -= 360.0;
+                    a.lon[q] = a.lon0 + r;
+                    a.lat[q] = lt;
+                    a.p[q] = fmin(fmax(pp, a.pmin), a.pmax);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 int grid1(int64_t n, int block) {
     int64_t b = (n + block - 1) / block;
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, 1 << 20));
@@ -543,6 +809,39 @@ cudaError_t launch_colstats(const float* D, int64_t n, int ncol, double* sum, do
     const int rpb = 2048;
     note_launches(1);
     k_colstats<<<grid1(n, rpb), 256, 0, s>>>(D, n, ncol, rpb, sum, sumsq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_surr_fused(int storage, Surrogate& S, const Geo& g, MetView m0, MetView m1, int64_t n,
+                              double* lon, double* lat, double* p, float w, int window_ok, uint8_t* fallback,
+                              double lon0, cudaStream_t s) {
+    FusedArgs a{g, m0, m1, n, lon, lat, p, fallback, w, window_ok, S.W1b, S.W2b, S.W3b,
+                S.theta + OB1, S.theta + OB2, S.b3p, S.mu_x, S.isd_x, S.mu_y, S.sd_y,
+                lon0, g.pmin_d, g.pmax_d};
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t ntiles = (n + FT - 1) / FT;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, sms));
+    note_launches(1);
+    cudaError_t e;
+    switch (storage) {
+        case MPTRAC_FP32:
+            e = cudaFuncSetAttribute(k_surr_fused<MPTRAC_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
+            if (e != cudaSuccess) return e;
+            k_surr_fused<MPTRAC_FP32><<<grid, 256, kFusedSmem, s>>>(a);
+            break;
+        case MPTRAC_BF16:
+            e = cudaFuncSetAttribute(k_surr_fused<MPTRAC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
+            if (e != cudaSuccess) return e;
+            k_surr_fused<MPTRAC_BF16><<<grid, 256, kFusedSmem, s>>>(a);
+            break;
+        default:
+            e = cudaFuncSetAttribute(k_surr_fused<MPTRAC_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
+            if (e != cudaSuccess) return e;
+            k_surr_fused<MPTRAC_FP16><<<grid, 256, kFusedSmem, s>>>(a);
+            break;
+    }
     return cudaGetLastError();
 }
 
