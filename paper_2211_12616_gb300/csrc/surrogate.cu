@@ -415,7 +415,7 @@ struct FusedArgs {
 
 constexpr size_t kFusedSmem = (size_t)HID * XS * 2 + (size_t)HID * HS * 2 + (size_t)NOP * HS * 2 +
                               (size_t)(2 * HID + NOP) * 4 + (size_t)2 * KP * 4 + (size_t)FT * XS * 2 +
-                              (size_t)FT * HS * 2 + (size_t)FT * NOP * 4 + FT * 4;
+                              (size_t)FT * HS * 2 + (size_t)FT * NOP * 4 + FT * 4 + (size_t)kMaxNZ * 4;
 
 // nearest node (float64, the definition) and the offsets from it
 __device__ __forceinline__ void nearest_node(const Geo& g, double lon, double lat, double p, int& i0, int& j0,
@@ -450,6 +450,44 @@ __device__ __forceinline__ void nearest_node(const Geo& g, double lon, double la
     oz = z - (double)kk;
 }
 
+// Nearest node in float32 (latitude in float-float): used by the fused
+// inference, where a different choice within ~1e-6 cells of a half-cell
+// boundary only swaps one valid stencil for its neighbour.  Level search from
+// the float level table.
+__device__ __forceinline__ void nearest_node_f32(const Geo& g, const float* plev, double lon, double lat,
+                                                 double p, int& i0, int& j0, int& k0, float& ox, float& oy,
+                                                 float& oz) {
+    float lf = (float)(lon - (double)g.lon0);
+    if (lf < 0.f) lf += 360.f;
+    if (lf >= 360.f) lf -= 360.f;
+    const float x = lf * g.inv_dlon;
+    const float xr = floorf(x + 0.5f);
+    int ii = (int)xr;
+    if (ii >= g.nx) ii -= g.nx;
+    ii = min(max(ii, 0), g.nx - 1);
+    const float lat_hi = (float)lat, lat_lo = (float)(lat - (double)lat_hi);
+    const float y = ((lat_hi - g.lat0) + lat_lo) * g.inv_dlat;
+    int jj = (int)floorf(y + 0.5f);
+    jj = min(max(jj, 1), g.ny - 2);
+    const float pc = fminf(fmaxf((float)p, g.pmin), g.pmax);
+    int lo = 0, hi = g.nz;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (plev[mid] >= pc) lo = mid + 1; else hi = mid;
+    }
+    int k = min(max(lo - 1, 0), g.nz - 2);
+    const float fz = fminf(fmaxf((plev[k] - pc) / (plev[k] - plev[k + 1]), 0.f), 1.f);
+    const float z = (float)k + fz;
+    int kk = (int)floorf(z + 0.5f);
+    kk = min(max(kk, 1), g.nz - 2);
+    i0 = ii;
+    j0 = jj;
+    k0 = kk;
+    ox = x - xr;
+    oy = y - (float)jj;
+    oz = z - (float)kk;
+}
+
 template <int ST>
 __global__ void __launch_bounds__(256, 1) k_surr_fused(const FusedArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -463,7 +501,9 @@ __global__ void __launch_bounds__(256, 1) k_surr_fused(const FusedArgs a) {
     __nv_bfloat16* Hs = Xs + FT * XS;                                         // [FT][HS]
     float* Ys = reinterpret_cast<float*>(Hs + FT * HS);                       // [FT][NOP]
     int* env = reinterpret_cast<int*>(Ys + FT * NOP);                         // [FT]
+    float* plevs = reinterpret_cast<float*>(env + FT);                        // [nz]
     const int tid = threadIdx.x;
+    for (int e = tid; e < a.g.nz; e += blockDim.x) plevs[e] = a.g.plev[e];
     for (int e = tid; e < KP * HID; e += blockDim.x) {
         const int k = e / HID, nn = e % HID;
         W1T[nn * XS + k] = a.W1b[e];
@@ -499,42 +539,43 @@ __global__ void __launch_bounds__(256, 1) k_surr_fused(const FusedArgs a) {
             float mx = 0.f;
             if (q < a.n) {
                 int i0, j0, k0;
-                double ox, oy, oz;
+                float ox, oy, oz;
                 const double lat = a.lat[q];
-                nearest_node(g, a.lon[q], lat, a.p[q], i0, j0, k0, ox, oy, oz);
+                nearest_node_f32(g, plevs, a.lon[q], lat, a.p[q], i0, j0, k0, ox, oy, oz);
                 const R* rec = static_cast<const R*>(sn ? a.m1.rec : a.m0.rec);
                 const float* sc = sn ? a.m1.scales : a.m0.scales;
-                int col = 0;
-                for (int dk = -1; dk <= 1; ++dk) {
-                    const int kk = k0 + dk;
-                    for (int dj = -1; dj <= 1; ++dj) {
-                        const int jj = j0 + dj;
+                int im = i0 - 1, ip = i0 + 1;
+                if (im < 0) im += g.nx;
+                if (ip >= g.nx) ip -= g.nx;
+                const int icol[3] = {im, i0, ip};
+                R r[27];
 #pragma unroll
-                        for (int di = -1; di <= 1; ++di) {
-                            int ii = i0 + di;
-                            ii = ii < 0 ? ii + g.nx : (ii >= g.nx ? ii - g.nx : ii);
-                            float4 v = decode<ST>(__ldg(rec + ((int64_t)jj * g.nx + ii) * g.nz + kk));
-                            if (ST != MPTRAC_FP32) {
-                                v.x *= sc[kk];
-                                v.y *= sc[g.nz + kk];
-                                v.z *= sc[2 * g.nz + kk];
-                            }
-                            const int c0 = sn * 81 + col;
-                            const float xu = (v.x - mu[c0]) * isd[c0];
-                            const float xv = (v.y - mu[c0 + 27]) * isd[c0 + 27];
-                            const float xw = (v.z - mu[c0 + 54]) * isd[c0 + 54];
-                            mx = fmaxf(mx, fmaxf(fabsf(xu), fmaxf(fabsf(xv), fabsf(xw))));
-                            xr[c0] = __float2bfloat16_rn(xu);
-                            xr[c0 + 27] = __float2bfloat16_rn(xv);
-                            xr[c0 + 54] = __float2bfloat16_rn(xw);
-                            ++col;
-                        }
+                for (int c = 0; c < 27; ++c) {
+                    const int dk = c / 9 - 1, dj = (c / 3) % 3 - 1, di = c % 3;
+                    r[c] = __ldg(rec + ((int64_t)(j0 + dj) * g.nx + icol[di]) * g.nz + (k0 + dk));
+                }
+#pragma unroll
+                for (int c = 0; c < 27; ++c) {
+                    float4 v = decode<ST>(r[c]);
+                    if (ST != MPTRAC_FP32) {
+                        const int kk = k0 + c / 9 - 1;
+                        v.x *= sc[kk];
+                        v.y *= sc[g.nz + kk];
+                        v.z *= sc[2 * g.nz + kk];
                     }
+                    const int c0 = sn * 81 + c;
+                    const float xu = (v.x - mu[c0]) * isd[c0];
+                    const float xv = (v.y - mu[c0 + 27]) * isd[c0 + 27];
+                    const float xw = (v.z - mu[c0 + 54]) * isd[c0 + 54];
+                    mx = fmaxf(mx, fmaxf(fabsf(xu), fmaxf(fabsf(xv), fabsf(xw))));
+                    xr[c0] = __float2bfloat16_rn(xu);
+                    xr[c0 + 27] = __float2bfloat16_rn(xv);
+                    xr[c0 + 54] = __float2bfloat16_rn(xw);
                 }
                 if (sn == 0) {
-                    double snl, csl;
-                    sincos(lat * (kPi / 180.0), &snl, &csl);
-                    const float ex[6] = {(float)ox, (float)oy, (float)oz, a.w, (float)snl, (float)csl};
+                    float snl, csl;
+                    sincospif((float)lat * (1.0f / 180.0f), &snl, &csl);
+                    const float ex[6] = {ox, oy, oz, a.w, snl, csl};
 #pragma unroll
                     for (int c = 0; c < 6; ++c) {
                         const float xe = (ex[c] - mu[162 + c]) * isd[162 + c];
@@ -634,18 +675,18 @@ __global__ void __launch_bounds__(256, 1) k_surr_fused(const FusedArgs a) {
                 const bool ok = a.window_ok && env[tid] && fabs(la) <= 80.0;
                 a.fallback[q] = ok ? 0 : 1;
                 if (ok) {
-                    const double dx = (double)(Ys[tid * NOP + 0] * a.sd_y[0] + a.mu_y[0]);
-                    const double dy = (double)(Ys[tid * NOP + 1] * a.sd_y[1] + a.mu_y[1]);
-                    const double dz = (double)(Ys[tid * NOP + 2] * a.sd_y[2] + a.mu_y[2]);
-                    double lo = a.lon[q] + dx / (kR * cos(la * (kPi / 180.0))) * (180.0 / kPi);
-                    double lt = la + dy / kR * (180.0 / kPi);
-                    const double pp = a.p[q] * exp(dz);
+                    const float dx = Ys[tid * NOP + 0] * a.sd_y[0] + a.mu_y[0];
+                    const float dy = Ys[tid * NOP + 1] * a.sd_y[1] + a.mu_y[1];
+                    const float dz = Ys[tid * NOP + 2] * a.sd_y[2] + a.mu_y[2];
+                    const float cl = cospif((float)la * (1.0f / 180.0f));
+                    double lo = a.lon[q] + (double)(dx / ((float)kR * cl) * (float)(180.0 / kPi));
+                    double lt = la + (double)(dy * (float)(180.0 / (kPi * kR)));
+                    const double pp = a.p[q] * (double)expf(dz);
                     if (lt > 90.0) { lt = 180.0 - lt; lo += 180.0; }
                     else if (lt < -90.0) { lt = -180.0 - lt; lo += 180.0; }
-                    double r = fmod(lo - a.lon0, 360.0);
-                    if (r < 0.0) r += 360.0;
-                    if (r >= 360.0) r -= 360.0;
-                    a.lon[q] = a.lon0 + r;
+                    if (lo >= a.lon0 + 360.0) lo -= 360.0;
+                    if (lo < a.lon0) lo += 360.0;
+                    a.lon[q] = lo;
                     a.lat[q] = lt;
                     a.p[q] = fmin(fmax(pp, a.pmin), a.pmax);
                 }
