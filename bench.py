@@ -566,11 +566,16 @@ def run_surrogate_bench(args, rank, world):
     sur_p = init.clone()
     ms_sur, fb = timed(lambda P: learn.run_surrogate(ctx, sur, P, at, DT_MET, 0.0, SURR_T_END, stream=stream),
                        sur_p)
-    ref = plain.to_numpy()
+    def by_id(parts):
+        d = parts.to_numpy()
+        o = np.argsort(d["id"])
+        return {k: v[o] for k, v in d.items()}
+
+    ref = by_id(plain)
     substeps = n * int(round(SURR_T_END / DT))
     for name, parts, ms in (("plain_dt180", plain, ms_plain), ("midpoint_dt1800", coarse, ms_coarse),
                             ("surrogate", sur_p, ms_sur)):
-        got = parts.to_numpy()
+        got = by_id(parts)
         km = great_circle_km(got["lon"], got["lat"], ref["lon"], ref["lat"])
         dp = np.abs(got["p"] - ref["p"]) / ref["p"]
         runs[name] = {"ms_per_48h": ms, "substep_equivalents_per_s": substeps / (ms / 1000.0),

@@ -109,15 +109,22 @@ def evaluate(surr: Surrogate, X: torch.Tensor, Y: torch.Tensor, batch: int = 819
 
 
 def run_surrogate(ctx: Context, surr: Surrogate, parts: Particles, snapshot_at, dt_met: float, t_start: float,
-                  t_end: float, stream=None):
-    """Surrogate segments with the plain fallback; returns the fraction of fallback particle-segments."""
+                  t_end: float, stream=None, workspace=None):
+    """Surrogate segments with the plain fallback; returns the fraction of fallback particle-segments.
+
+    Particles are sorted by met cell at the start of every met interval, which also groups the
+    fallback particles (poles, rare wind patterns) into whole warps of the masked plain kernel.
+    """
     fallback = torch.zeros(parts.n, dtype=torch.uint8, device=parts.lon.device)
+    if workspace is None:
+        workspace = torch.empty(ctx.sort_workspace_bytes(parts.n), dtype=torch.uint8, device=parts.lon.device)
     segs_per_iv = int(round(dt_met / DT_SEG))
     n_iv = int(round((t_end - t_start) / dt_met))
     fb = torch.zeros((), dtype=torch.float64, device=parts.lon.device)
     for iv in range(n_iv):
         ta = t_start + iv * dt_met
         _load_interval(ctx, snapshot_at, ta, ta + dt_met, stream)
+        ctx.sort(parts, workspace, stream=stream)
         for sg in range(segs_per_iv):
             t = ta + sg * DT_SEG
             surr.advance(ctx, parts, t, DT_SEG, fallback, stream=stream)
@@ -127,11 +134,15 @@ def run_surrogate(ctx: Context, surr: Surrogate, parts: Particles, snapshot_at, 
 
 
 def run_plain(ctx: Context, parts: Particles, snapshot_at, dt_met: float, t_start: float, t_end: float,
-              dt: float = DT, stream=None):
-    """Plain midpoint advection over [t_start, t_end] with step dt (the judge at dt = 180 s)."""
+              dt: float = DT, stream=None, workspace=None):
+    """Plain midpoint advection over [t_start, t_end] with step dt (the judge at dt = 180 s);
+    particles sorted by met cell at the start of every met interval, like ``run_surrogate``."""
+    if workspace is None:
+        workspace = torch.empty(ctx.sort_workspace_bytes(parts.n), dtype=torch.uint8, device=parts.lon.device)
     n_iv = int(round((t_end - t_start) / dt_met))
     steps = int(round(dt_met / dt))
     for iv in range(n_iv):
         ta = t_start + iv * dt_met
         _load_interval(ctx, snapshot_at, ta, ta + dt_met, stream)
+        ctx.sort(parts, workspace, stream=stream)
         ctx.advect(parts, ta, dt, steps, stream=stream)

@@ -167,9 +167,14 @@ def test_advance_applies_prediction_and_flags_fallback(M, field):
     y = yh[:, :3] * sd_y.astype(np.float32) + mu_y.astype(np.float32)     # float32, as in the kernel
     lon1, lat1, p1 = S.apply_displacement(st["lon"], st["lat"], st["p"], y.astype(np.float64))
     lon1, lat1, p1 = tr.position_bc(lon1, lat1, p1, 0.0, grid.plev[-1], grid.plev[0])
-    np.testing.assert_allclose(got["lat"][inside], lat1[inside], atol=1e-6)
-    np.testing.assert_allclose(np.mod(got["lon"][inside] - lon1[inside] + 180, 360) - 180, 0, atol=1e-6)
-    np.testing.assert_allclose(got["p"][inside], p1[inside], rtol=1e-6)
+    # the fused kernel forms its own (float32) features, whose bf16 rounding may differ from the
+    # float64 features used here by one bf16 unit: displacements agree to 1e-2 of their size
+    from oracle.errors import great_circle_km
+    d_ref = great_circle_km(st["lon"], st["lat"], lon1, lat1)[inside]
+    d_err = great_circle_km(got["lon"], got["lat"], lon1, lat1)[inside]
+    assert np.all(d_err <= 1e-2 * d_ref + 1e-3), np.max(d_err / (d_ref + 1e-9))
+    assert np.median(d_err / (d_ref + 1e-9)) < 1e-3
+    np.testing.assert_allclose(got["p"][inside], p1[inside], rtol=2e-3)
     np.testing.assert_array_equal(got["lon"][fbn == 1], st["lon"][fbn == 1])
     # the window must fit inside the loaded interval, else everything falls back
     sur.advance(ctx, parts, T6H - 900.0, 1800.0, fb)
