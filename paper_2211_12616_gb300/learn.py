@@ -11,10 +11,10 @@ and moves tensors around.
   and the displacement becomes the target.
 * ``train``: standardises features and targets with their column statistics,
   then runs Adam on shuffled mini-batches with a cosine learning-rate decay.
-* ``run_surrogate`` / ``run_plain`` / ``run_coarse``: 30-minute segments by
-  the network (with the plain fallback), by 10 plain substeps (the judge), or
-  by one plain midpoint step of 30 minutes (the same number of wind
-  evaluations as ... the cheapest plain alternative).
+* ``run_surrogate`` / ``run_plain``: 30-minute segments by the network (with
+  the plain fallback), or by the plain integrator -- 10 substeps of 180 s (the
+  judge), or one midpoint step of 30 minutes (``dt=DT_SEG``, the cheapest plain
+  alternative: two wind evaluations per segment).
 """
 from __future__ import annotations
 
