@@ -194,7 +194,8 @@ def run_ours(args, rank, world):
     grid = grid_1deg_60lev()
     modes = fourier_modes(SEED_FIELD)
     snaps = [fourier_snapshot(grid, modes, h * DT_MET, device=dev, as_numpy=False) for h in range(4)]
-    st0 = uniform_particles(n, grid.plev, SEED_PART + 1000 * rank, id0=rank * n)
+    from paper_2211_12616_gb300.replicas import aggregate_rate, id_offset, max_over_ranks
+    st0 = uniform_particles(n, grid.plev, SEED_PART + 1000 * rank, id0=id_offset(rank, n))
     init = M.Particles.from_numpy(st0, device=dev)
     work = init.clone()
     ctx = M.Context(grid, M.MPTRAC_FP32)
@@ -254,11 +255,8 @@ def run_ours(args, rank, world):
     sim.step_hook = None
     ms = start.elapsed_time(end)
     clk = clocks.stop()
-    ms_t = torch.tensor([ms], dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * psteps_per_pass * args.steps / (ms_max / 1000.0)
+    ms_max = max_over_ranks(ms)
+    value = aggregate_rate(psteps_per_pass * args.steps, world, ms_max)
     step_ms = [a.elapsed_time(b) for a, b in ev_pairs]
     step_avg_ms = sum(step_ms) / len(step_ms)
     psteps_per_launch = n * SORT_EVERY
@@ -291,8 +289,8 @@ def run_ours(args, rank, world):
             e2e_pass()
         e2.record(stream)
         torch.cuda.synchronize()
-        ms2 = s2.elapsed_time(e2)
-        e2e = {"value": world * psteps_per_pass * k2 / (ms2 / 1000.0), "unit": "particle-steps/s",
+        ms2 = max_over_ranks(s2.elapsed_time(e2))
+        e2e = {"value": aggregate_rate(psteps_per_pass * k2, world, ms2), "unit": "particle-steps/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     if rank != 0:

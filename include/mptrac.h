@@ -194,6 +194,20 @@ size_t mptrac_sort_workspace_bytes(const mptrac_ctx* ctx, int64_t n);
 int mptrac_sort(mptrac_ctx* ctx, const mptrac_particles* parts, void* workspace,
                 size_t ws_bytes, uintptr_t stream);
 
+/* module_meteo (Section 3.2): u, v, omega and T (0 when nvars == 3) at every
+ * particle position at time t, by the 4D linear interpolation of the
+ * advection (float32 arithmetic), into DEVICE out[4][n] (variable-major).
+ * t must lie within the loaded snapshots (E_TIME_RANGE). */
+int mptrac_sample_met(mptrac_ctx* ctx, const mptrac_particles* parts, double t, float* out,
+                      uintptr_t stream);
+
+/* write_grid (Section 3.3) for particle counts: the number of particles in every
+ * met cell, indexed by the cell key of mptrac_sort ((j*nx + i)*nz + k), into
+ * DEVICE counts[nx*ny*nz] (overwritten; cells of the last latitude row or the
+ * top level are never used by the cell rule and stay zero). */
+int mptrac_grid_counts(mptrac_ctx* ctx, const mptrac_particles* parts, uint32_t* counts,
+                       uintptr_t stream);
+
 /* Sort for runs with a release table: as mptrac_sort, except that particles
  * whose release is not active at time t (t outside [t_start, t_end) of its
  * release, or a release index outside the table) are keyed after every cell,

@@ -71,6 +71,8 @@ SIGNATURES = {
     "mptrac_sort_at": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_double, C.c_void_p, C.c_size_t,
                                  C.c_void_p]),
     "mptrac_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "mptrac_sample_met": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_double, C.c_void_p, C.c_void_p]),
+    "mptrac_grid_counts": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_void_p, C.c_void_p]),
     "mptrac_advect_masked": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_void_p, C.c_double, C.c_double,
                                        C.c_int, C.c_void_p]),
     "mptrac_surr_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int64]),
@@ -270,6 +272,17 @@ class Context:
         check(load().mptrac_sort_at(self.h, C.byref(parts.desc()), float(t), _ptr(workspace), workspace.numel(),
                                     _stream(stream)), self.h)
         return workspace
+
+    def sample_met(self, parts: Particles, t, stream=None) -> torch.Tensor:
+        out = torch.empty(4, parts.n, dtype=torch.float32, device=parts.lon.device)
+        check(load().mptrac_sample_met(self.h, C.byref(parts.desc()), float(t), _ptr(out), _stream(stream)), self.h)
+        return out
+
+    def grid_counts(self, parts: Particles, stream=None) -> torch.Tensor:
+        g = self.grid
+        out = torch.empty(g.nx * g.ny * g.nz, dtype=torch.int32, device=parts.lon.device)
+        check(load().mptrac_grid_counts(self.h, C.byref(parts.desc()), _ptr(out), _stream(stream)), self.h)
+        return out
 
     def set_launch(self, variant: int = 0, persistent: bool = False):
         check(load().mptrac_set_launch(self.h, int(variant), int(persistent)), self.h)

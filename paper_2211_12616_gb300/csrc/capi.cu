@@ -528,6 +528,34 @@ int mptrac_met_slot_copy(const mptrac_ctx* c, int slot, void* rec_out, float* sc
     return ok();
 }
 
+int mptrac_sample_met(mptrac_ctx* c, const mptrac_particles* P, double t, float* out, uintptr_t stream) {
+    if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    int rc = check_particles(P, false);
+    if (rc) return rc;
+    int s0, s1;
+    if ((rc = ordered_slots(c, s0, s1))) return rc;
+    const double t0 = c->t_slot[s0], t1 = c->t_slot[s1];
+    if (!(t >= t0 && t <= t1)) return fail(MPTRAC_E_TIME_RANGE, "t = %g outside [%g, %g]", t, t0, t1);
+    if (P->n == 0) return ok();
+    if (!device_accessible(out)) return fail(MPTRAC_E_INVALID_ARG, "out must be device memory");
+    MPTRAC_CUDA(launch_sample(c->storage, c->geo, MetView{c->d_met[s0], c->d_scales[s0]},
+                              MetView{c->d_met[s1], c->d_scales[s1]}, (float)((t - t0) / (t1 - t0)), P->n,
+                              P->lon, P->lat, P->p, out, reinterpret_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
+int mptrac_grid_counts(mptrac_ctx* c, const mptrac_particles* P, uint32_t* counts, uintptr_t stream) {
+    if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    int rc = check_particles(P, false);
+    if (rc) return rc;
+    if (!device_accessible(counts)) return fail(MPTRAC_E_INVALID_ARG, "counts must be device memory");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    MPTRAC_CUDA(cudaMemsetAsync(counts, 0, (size_t)c->nx * c->ny * c->nz * sizeof(uint32_t), st));
+    if (P->n == 0) return ok();
+    MPTRAC_CUDA(launch_grid_counts(c->geo, P->n, P->lon, P->lat, P->p, counts, st));
+    return ok();
+}
+
 int mptrac_advect_masked(mptrac_ctx* c, const mptrac_particles* P, const uint8_t* mask, double t,
                          double dt, int nsteps, uintptr_t stream) {
     if (P && P->n > 0 && !device_accessible(mask))

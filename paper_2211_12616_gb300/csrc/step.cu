@@ -545,6 +545,54 @@ __global__ void __launch_bounds__(kBlock) k_interp(Geo g, MetView m0, MetView m1
     }
 }
 
+// module_meteo: u, v, omega, T at the particle positions (4D linear, float32)
+template <int ST>
+__global__ void __launch_bounds__(kBlock) k_sample(Geo g, MetView m0, MetView m1, float w, int64_t n,
+                                                   const double* lon, const double* lat, const double* p,
+                                                   float* out) {
+    __shared__ Smem s;
+    load_tables(s, g, m0, m1, false);
+    using R = typename RecT<ST>::T;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
+        const Cell c = locate(ff_make(lon[idx]).hi, ff_make(lat[idx]), ff_make(p[idx]).hi, g, s, -1);
+        const int i1 = (c.i + 1 == g.nx) ? 0 : c.i + 1;
+        const int col[4] = {c.j * g.nx + c.i, c.j * g.nx + i1, (c.j + 1) * g.nx + c.i, (c.j + 1) * g.nx + i1};
+        float res[2][4];
+        for (int t = 0; t < 2; ++t) {
+            const R* rec = static_cast<const R*>(t ? m1.rec : m0.rec);
+            const float* sc = t ? m1.scales : m0.scales;
+            float4 v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                v[q] = decode<ST>(__ldg(rec + col[q & 3] * g.nz + c.k + (q >> 2)));
+                if (ST != MPTRAC_FP32) {
+                    const int k = c.k + (q >> 2);
+                    v[q].x *= sc[k];
+                    v[q].y *= sc[g.nz + k];
+                    v[q].z *= sc[2 * g.nz + k];
+                    v[q].w *= sc[3 * g.nz + k];
+                }
+            }
+#define MPTRAC_TRI4(comp, dst)                                                             \
+    {                                                                                      \
+        const float e0 = fmaf(v[1].comp, c.fx, v[0].comp * c.gx);                          \
+        const float e1 = fmaf(v[3].comp, c.fx, v[2].comp * c.gx);                          \
+        const float e2 = fmaf(v[5].comp, c.fx, v[4].comp * c.gx);                          \
+        const float e3 = fmaf(v[7].comp, c.fx, v[6].comp * c.gx);                          \
+        dst = fmaf(fmaf(e3, c.fy, e2 * c.gy), c.fz, fmaf(e1, c.fy, e0 * c.gy) * c.gz);    \
+    }
+            MPTRAC_TRI4(x, res[t][0])
+            MPTRAC_TRI4(y, res[t][1])
+            MPTRAC_TRI4(z, res[t][2])
+            MPTRAC_TRI4(w, res[t][3])
+#undef MPTRAC_TRI4
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) out[v * n + idx] = fmaf(w, res[1][v] - res[0][v], res[0][v]);
+    }
+}
+
 __global__ void k_philox(const uint32_t* ctr, int64_t n, uint32_t k0, uint32_t k1,
                          uint32_t* out, float* normals) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -654,6 +702,18 @@ cudaError_t launch_interp(int storage, const Geo& g, MetView m0, MetView m1, flo
         default:
             k_interp<MPTRAC_FP16><<<grid, kBlock, 0, s>>>(g, m0, m1, w, n, lon, lat, p, ou, ov, ow, ovar);
             break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample(int storage, const Geo& g, MetView m0, MetView m1, float w, int64_t n,
+                          const double* lon, const double* lat, const double* p, float* out, cudaStream_t s) {
+    const int grid = grid_for(n);
+    note_launches(1);
+    switch (storage) {
+        case MPTRAC_FP32: k_sample<MPTRAC_FP32><<<grid, kBlock, 0, s>>>(g, m0, m1, w, n, lon, lat, p, out); break;
+        case MPTRAC_BF16: k_sample<MPTRAC_BF16><<<grid, kBlock, 0, s>>>(g, m0, m1, w, n, lon, lat, p, out); break;
+        default: k_sample<MPTRAC_FP16><<<grid, kBlock, 0, s>>>(g, m0, m1, w, n, lon, lat, p, out); break;
     }
     return cudaGetLastError();
 }

@@ -1,0 +1,59 @@
+"""Met sampling along trajectories (module_meteo) and particle counts per met cell (write_grid)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import met as omet
+from oracle import meteo
+from oracle import sort as osort
+from workloads import fourier_modes, fourier_snapshot, grid_global, uniform_particles
+
+from _gpu_common import M, make_ctx  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+T6H = 21600.0
+
+
+@pytest.mark.parametrize("storage", [omet.FP32, omet.BF16, omet.FP16])
+def test_sample_met_matches_oracle(M, storage):
+    grid = grid_global(90, 46, 25)
+    m = fourier_modes(6, with_T=True)
+    f0 = fourier_snapshot(grid, m, 0.0)
+    f1 = fourier_snapshot(grid, m, T6H)
+    ctx = make_ctx(M, grid, [f0, f1], [0.0, T6H], storage=storage, nvars=4)
+    st = uniform_particles(30_001, grid.plev, seed=9)
+    parts = M.Particles.from_numpy(st, meso=False)
+    t = 9000.0
+    out = ctx.sample_met(parts, t).cpu().numpy()
+    ref = meteo.sample(grid, omet.stored_fields(f0, storage), 0.0, omet.stored_fields(f1, storage), T6H, t,
+                       st["lon"], st["lat"], st["p"])
+    for i, (v, scale) in enumerate((("u", 20.0), ("v", 20.0), ("w", 0.5), ("T", 300.0))):
+        err = np.abs(out[i] - ref[v]).max()
+        assert err < 2e-5 * scale * 4, (v, err)
+
+
+def test_sample_met_without_T_is_zero(M):
+    grid = grid_global(36, 19, 10)
+    f = {k: np.ones((10, 19, 36), np.float32) for k in ("u", "v", "w")}
+    ctx = make_ctx(M, grid, [f, f], [0.0, 1.0])
+    parts = M.Particles.from_numpy(uniform_particles(100, grid.plev, seed=1), meso=False)
+    out = ctx.sample_met(parts, 0.5).cpu().numpy()
+    np.testing.assert_allclose(out[:3], 1.0, rtol=1e-6)
+    assert np.all(out[3] == 0)
+
+
+@pytest.mark.parametrize("sort_first", [False, True])
+def test_grid_counts_bit_exact(M, sort_first):
+    grid = grid_global(360, 181, 60, 1e5, 1e3)
+    z = {k: np.zeros((60, 181, 360), np.float32) for k in ("u", "v", "w")}
+    ctx = make_ctx(M, grid, [z, z], [0.0, 1.0])
+    st = uniform_particles(200_003, grid.plev, seed=10)
+    st["lon"][::4], st["lat"][::4], st["p"][::4] = 100.0, 20.0, grid.plev[10]   # one crowded cell
+    st["lon"][1::9] = 359.99999999999994
+    parts = M.Particles.from_numpy(st, meso=False)
+    if sort_first:
+        ctx.sort(parts)
+    counts = ctx.grid_counts(parts).cpu().numpy().view(np.uint32)
+    ref = meteo.grid_counts(grid, st["lon"], st["lat"], st["p"])
+    np.testing.assert_array_equal(counts, ref)
+    assert counts.sum() == 200_003
