@@ -201,6 +201,16 @@ int mptrac_sort(mptrac_ctx* ctx, const mptrac_particles* parts, void* workspace,
 int mptrac_sample_met(mptrac_ctx* ctx, const mptrac_particles* parts, double t, float* out,
                       uintptr_t stream);
 
+/* module_sedi (Section 3.2): nsteps sedimentation steps from time t.  Spherical
+ * particles of radius[i] [m] and density[i] [kg/m^3] (DEVICE float32 arrays of
+ * n) settle at the Stokes velocity with the Cunningham slip correction,
+ * v_s = 2 r^2 (rho_p - rho_air) g C / (9 eta), C = 1 + Kn (1.257 + 0.4 e^(-1.1/Kn)),
+ * Kn = 2 eta / (rho_air vbar r), vbar = sqrt(8 R_d T / pi), eta by Sutherland's
+ * formula, rho_air = p / (R_d T), with T interpolated at the particle; the
+ * fall is dp = rho_air g v_s dt (p clamped).  Needs nvars == 4. */
+int mptrac_sediment(mptrac_ctx* ctx, const mptrac_particles* parts, const float* radius,
+                    const float* density, double t, double dt, int nsteps, uintptr_t stream);
+
 /* write_grid (Section 3.3) for particle counts: the number of particles in every
  * met cell, indexed by the cell key of mptrac_sort ((j*nx + i)*nz + k), into
  * DEVICE counts[nx*ny*nz] (overwritten; cells of the last latitude row or the

@@ -72,6 +72,8 @@ SIGNATURES = {
                                  C.c_void_p]),
     "mptrac_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "mptrac_sample_met": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_double, C.c_void_p, C.c_void_p]),
+    "mptrac_sediment": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_void_p, C.c_void_p, C.c_double,
+                                  C.c_double, C.c_int, C.c_void_p]),
     "mptrac_grid_counts": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_void_p, C.c_void_p]),
     "mptrac_advect_masked": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_void_p, C.c_double, C.c_double,
                                        C.c_int, C.c_void_p]),
@@ -277,6 +279,10 @@ class Context:
         out = torch.empty(4, parts.n, dtype=torch.float32, device=parts.lon.device)
         check(load().mptrac_sample_met(self.h, C.byref(parts.desc()), float(t), _ptr(out), _stream(stream)), self.h)
         return out
+
+    def sediment(self, parts: Particles, radius: torch.Tensor, density: torch.Tensor, t, dt, nsteps, stream=None):
+        check(load().mptrac_sediment(self.h, C.byref(parts.desc()), _ptr(radius), _ptr(density), float(t), float(dt),
+                                     int(nsteps), _stream(stream)), self.h)
 
     def grid_counts(self, parts: Particles, stream=None) -> torch.Tensor:
         g = self.grid

@@ -544,6 +544,28 @@ int mptrac_sample_met(mptrac_ctx* c, const mptrac_particles* P, double t, float*
     return ok();
 }
 
+int mptrac_sediment(mptrac_ctx* c, const mptrac_particles* P, const float* radius, const float* density, double t,
+                    double dt, int nsteps, uintptr_t stream) {
+    if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    if (c->nvars != 4) return fail(MPTRAC_E_INVALID_ARG, "sedimentation needs temperature (nvars == 4)");
+    if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(MPTRAC_E_INVALID_ARG, "bad dt or nsteps");
+    int rc = check_particles(P, false);
+    if (rc) return rc;
+    int s0, s1;
+    if ((rc = ordered_slots(c, s0, s1))) return rc;
+    const double t0 = c->t_slot[s0], t1 = c->t_slot[s1];
+    const double tol = 1e-9 * (t1 - t0);
+    if (t < t0 - tol || t + nsteps * dt > t1 + tol) return fail(MPTRAC_E_TIME_RANGE, "sedimentation steps leave the loaded snapshots");
+    if (P->n == 0 || nsteps == 0) return ok();
+    if (!device_accessible(radius) || !device_accessible(density))
+        return fail(MPTRAC_E_INVALID_ARG, "radius and density must be device memory");
+    MPTRAC_CUDA(launch_sedi(c->storage, c->geo, MetView{c->d_met[s0], c->d_scales[s0]},
+                            MetView{c->d_met[s1], c->d_scales[s1]}, P->n, P->lon, P->lat, P->p, radius, density,
+                            nsteps, (float)dt, (float)((t - t0) / (t1 - t0)), (float)(dt / (t1 - t0)),
+                            reinterpret_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
 int mptrac_grid_counts(mptrac_ctx* c, const mptrac_particles* P, uint32_t* counts, uintptr_t stream) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
     int rc = check_particles(P, false);

@@ -79,6 +79,9 @@ cudaError_t launch_interp(int storage, const Geo& g, MetView m0, MetView m1, flo
                           float* ov, float* ow, float* ovar, cudaStream_t s);
 cudaError_t launch_sample(int storage, const Geo& g, MetView m0, MetView m1, float w, int64_t n,
                           const double* lon, const double* lat, const double* p, float* out, cudaStream_t s);
+cudaError_t launch_sedi(int storage, const Geo& g, MetView m0, MetView m1, int64_t n, const double* lon,
+                        const double* lat, double* p, const float* radius, const float* rho_p, int nsteps,
+                        float dt, float w0, float dw, cudaStream_t s);
 cudaError_t launch_grid_counts(const Geo& g, int64_t n, const double* lon, const double* lat,
                                const double* p, uint32_t* counts, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, int64_t n, uint32_t k0, uint32_t k1, uint32_t* out,

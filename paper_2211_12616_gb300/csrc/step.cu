@@ -593,6 +593,79 @@ __global__ void __launch_bounds__(kBlock) k_sample(Geo g, MetView m0, MetView m1
     }
 }
 
+// module_sedi: Stokes settling with the Cunningham slip correction, T from the
+// met snapshots (4D linear), dp = rho_air g v_s dt per step, p clamped.
+struct SediArgs {
+    Geo g;
+    MetView m0, m1;
+    int64_t n;
+    const double *lon, *lat;
+    double* p;
+    const float *radius, *rho_p;
+    int nsteps;
+    float dt, w0, dw;
+};
+
+template <int ST>
+__global__ void __launch_bounds__(kBlock) k_sedi(const SediArgs a) {
+    __shared__ Smem s;
+    load_tables(s, a.g, a.m0, a.m1, false);
+    const Geo& g = a.g;
+    using R = typename RecT<ST>::T;
+    constexpr float Rd = 287.058f, G = 9.80665f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < a.n; idx += stride) {
+        const float lonf = ff_make(a.lon[idx]).hi;
+        const ff lat = ff_make(a.lat[idx]);
+        ff p = ff_make(a.p[idx]);
+        const float r = a.radius[idx], rp = a.rho_p[idx];
+        int ccol = -1, ck = -1;
+        float T0[8], T1[8];
+        for (int n = 0; n < a.nsteps; ++n) {
+            const Cell c = locate(lonf, lat, p.hi, g, s, ck);
+            const int col = c.j * g.nx + c.i;
+            if (col != ccol || c.k != ck) {
+                const int i1 = (c.i + 1 == g.nx) ? 0 : c.i + 1;
+                const int cols[4] = {col, col - c.i + i1, col + g.nx, col + g.nx - c.i + i1};
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int k = c.k + (q >> 2);
+                    const int64_t o = (int64_t)cols[q & 3] * g.nz + k;
+                    T0[q] = decode<ST>(__ldg(static_cast<const R*>(a.m0.rec) + o)).w;
+                    T1[q] = decode<ST>(__ldg(static_cast<const R*>(a.m1.rec) + o)).w;
+                    if (ST != MPTRAC_FP32) {
+                        T0[q] *= a.m0.scales[3 * g.nz + k];
+                        T1[q] *= a.m1.scales[3 * g.nz + k];
+                    }
+                }
+                ccol = col;
+                ck = c.k;
+            }
+            float tr[2];
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const float* v = t ? T1 : T0;
+                const float e0 = fmaf(v[1], c.fx, v[0] * c.gx), e1 = fmaf(v[3], c.fx, v[2] * c.gx);
+                const float e2 = fmaf(v[5], c.fx, v[4] * c.gx), e3 = fmaf(v[7], c.fx, v[6] * c.gx);
+                tr[t] = fmaf(fmaf(e3, c.fy, e2 * c.gy), c.fz, fmaf(e1, c.fy, e0 * c.gy) * c.gz);
+            }
+            const float w = a.w0 + (float)n * a.dw;
+            const float T = fmaf(w, tr[1] - tr[0], tr[0]);
+            const float rho = p.hi / (Rd * T);
+            const float tt = T * (1.0f / 296.16f);
+            const float eta = 1.8325e-5f * (416.16f / (T + 120.0f)) * tt * sqrtf(tt);
+            const float vbar = sqrtf(8.0f * Rd * T * 0.31830988618379067f);
+            const float kn = 2.0f * eta / (rho * vbar) / r;
+            const float cc = 1.0f + kn * (1.257f + 0.4f * expf(-1.1f / kn));
+            const float vs = 2.0f * r * r * (rp - rho) * G * cc / (9.0f * eta);
+            p = ff_add(p, rho * G * vs * a.dt);
+            if (ff_less(p, g.pmin, g.pmin_lo)) { p.hi = g.pmin; p.lo = g.pmin_lo; }
+            if (ff_greater(p, g.pmax, g.pmax_lo)) { p.hi = g.pmax; p.lo = g.pmax_lo; }
+        }
+        a.p[idx] = ff_val(p);
+    }
+}
+
 __global__ void k_philox(const uint32_t* ctr, int64_t n, uint32_t k0, uint32_t k1,
                          uint32_t* out, float* normals) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -714,6 +787,20 @@ cudaError_t launch_sample(int storage, const Geo& g, MetView m0, MetView m1, flo
         case MPTRAC_FP32: k_sample<MPTRAC_FP32><<<grid, kBlock, 0, s>>>(g, m0, m1, w, n, lon, lat, p, out); break;
         case MPTRAC_BF16: k_sample<MPTRAC_BF16><<<grid, kBlock, 0, s>>>(g, m0, m1, w, n, lon, lat, p, out); break;
         default: k_sample<MPTRAC_FP16><<<grid, kBlock, 0, s>>>(g, m0, m1, w, n, lon, lat, p, out); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sedi(int storage, const Geo& g, MetView m0, MetView m1, int64_t n, const double* lon,
+                        const double* lat, double* p, const float* radius, const float* rho_p, int nsteps,
+                        float dt, float w0, float dw, cudaStream_t s) {
+    SediArgs a{g, m0, m1, n, lon, lat, p, radius, rho_p, nsteps, dt, w0, dw};
+    const int grid = grid_for(n);
+    note_launches(1);
+    switch (storage) {
+        case MPTRAC_FP32: k_sedi<MPTRAC_FP32><<<grid, kBlock, 0, s>>>(a); break;
+        case MPTRAC_BF16: k_sedi<MPTRAC_BF16><<<grid, kBlock, 0, s>>>(a); break;
+        default: k_sedi<MPTRAC_FP16><<<grid, kBlock, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }

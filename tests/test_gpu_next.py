@@ -57,3 +57,41 @@ def test_grid_counts_bit_exact(M, sort_first):
     ref = meteo.grid_counts(grid, st["lon"], st["lat"], st["p"])
     np.testing.assert_array_equal(counts, ref)
     assert counts.sum() == 200_003
+
+
+@pytest.mark.parametrize("storage", [omet.FP32, omet.BF16])
+def test_sedimentation_matches_oracle(M, storage):
+    from oracle import sedi
+    grid = grid_global(90, 46, 25)
+    m = fourier_modes(7, with_T=True)
+    f0 = fourier_snapshot(grid, m, 0.0)
+    f1 = fourier_snapshot(grid, m, T6H)
+    ctx = make_ctx(M, grid, [f0, f1], [0.0, T6H], storage=storage, nvars=4)
+    st = uniform_particles(20_000, grid.plev, seed=11)
+    rng = np.random.default_rng(2)
+    r = np.exp(rng.uniform(np.log(1e-7), np.log(2e-5), st["lon"].size)).astype(np.float32)
+    rho_p = rng.uniform(800, 3000, st["lon"].size).astype(np.float32)
+    parts = M.Particles.from_numpy(st, meso=False)
+    ctx.sediment(parts, torch.from_numpy(r).cuda(), torch.from_numpy(rho_p).cuda(), 600.0, 60.0, 30)
+    torch.cuda.synchronize()
+    got = parts.to_numpy()
+    T0 = omet.stored_fields(f0, storage)["T"]
+    T1 = omet.stored_fields(f1, storage)["T"]
+    ref = sedi.sediment(grid, T0, 0.0, T1, T6H, st, r.astype(np.float64), rho_p.astype(np.float64), 600.0, 60.0, 30)
+    dp_ref = ref - st["p"]
+    dp_got = got["p"] - st["p"]
+    assert np.all(dp_ref >= 0)
+    # float32 physics: the pressure increments agree to 1e-4 of themselves (or 1e-3 Pa)
+    np.testing.assert_allclose(dp_got, dp_ref, rtol=1e-4, atol=1e-3)
+    np.testing.assert_array_equal(got["lon"], st["lon"])
+
+
+def test_sedimentation_needs_temperature(M):
+    grid = grid_global(36, 19, 10)
+    f = {k: np.ones((10, 19, 36), np.float32) for k in ("u", "v", "w")}
+    ctx = make_ctx(M, grid, [f, f], [0.0, 1.0])
+    parts = M.Particles.from_numpy(uniform_particles(10, grid.plev, seed=1), meso=False)
+    one = torch.ones(10, device="cuda")
+    with pytest.raises(M.MptracError) as e:
+        ctx.sediment(parts, one, one, 0.0, 0.1, 1)
+    assert e.value.code == -1
