@@ -592,6 +592,56 @@ def run_surrogate_bench(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------
+# next rows: met sampling, particle counts per cell, sedimentation
+# --------------------------------------------------------------------------
+def run_next(args, rank, world):
+    import torch
+
+    import paper_2211_12616_gb300 as M
+    from workloads import fourier_modes, fourier_snapshot, grid_1deg_60lev, uniform_particles
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    grid = grid_1deg_60lev()
+    modes = fourier_modes(SEED_FIELD, with_T=True)
+    f0 = fourier_snapshot(grid, modes, 0.0, device=dev, as_numpy=False)
+    f1 = fourier_snapshot(grid, modes, DT_MET, device=dev, as_numpy=False)
+    ctx = M.Context(grid, M.MPTRAC_FP32, nvars=4)
+    ctx.load_met(0, 0.0, f0["u"], f0["v"], f0["w"], f0["T"])
+    ctx.load_met(1, DT_MET, f1["u"], f1["v"], f1["w"], f1["T"])
+    n = args.particles if args.particles != N_PART else 10_000_000
+    st = uniform_particles(n, grid.plev, 8)
+    parts = M.Particles.from_numpy(st, device=dev, meso=False)
+    ctx.sort(parts)
+    rng = np.random.default_rng(8)
+    radius = torch.from_numpy(np.exp(rng.uniform(np.log(1e-7), np.log(2e-5), n)).astype(np.float32)).to(dev)
+    density = torch.full((n,), 1500.0, dtype=torch.float32, device=dev)
+    p_save = parts.p.clone()
+
+    def timeit(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    ms_sample = timeit(lambda: ctx.sample_met(parts, 3600.0))
+    ms_count = timeit(lambda: ctx.grid_counts(parts))
+    ms_sedi = timeit(lambda: (parts.p.copy_(p_save), ctx.sediment(parts, radius, density, 0.0, 180.0, 20)))
+    line = {"workload": f"next rows on the 1deg x 60-level grid (u, v, omega, T), {n} sorted particles",
+            "sample_met": {"ms": ms_sample, "particles_per_s": n / (ms_sample / 1e3),
+                           "bytes_per_particle": 24 + 16 + 2 * 8 * 16},
+            "grid_counts": {"ms": ms_count, "particles_per_s": n / (ms_count / 1e3),
+                            "bytes_per_particle": 24, "cells": grid.npoints},
+            "sediment_20_steps": {"ms": ms_sedi, "particle_steps_per_s": 20 * n / (ms_sedi / 1e3)}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -601,7 +651,7 @@ def main():
     ap.add_argument("--particles", type=int, default=N_PART)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="transport", choices=["transport", "batch", "precision", "surrogate"])
+    ap.add_argument("--workload", default="transport", choices=["transport", "batch", "precision", "surrogate", "next"])
     ap.add_argument("--train-samples", type=int, default=10_000_000)
     ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--count-scale", type=float, default=1.0)
@@ -621,6 +671,8 @@ def main():
             run_batch(args, rank, world)
         elif args.workload == "precision":
             run_precision(args, rank, world)
+        elif args.workload == "next":
+            run_next(args, rank, world)
         elif args.workload == "surrogate":
             if args.particles == N_PART:
                 args.particles = 10_000_000
