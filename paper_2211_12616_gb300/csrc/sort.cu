@@ -103,40 +103,36 @@ __global__ void k_keys(Geo g, int64_t n, const double* lon, const double* lat, c
     }
 }
 
-// Keys for the batched run: the cell key, or 2^key_bits (after every cell key)
-// for particles whose release is inactive at time t.
-__global__ void k_keys_at(Geo g, int64_t n, const double* lon, const double* lat, const double* p,
-                          const uint32_t* release, double t, const double* ts, const double* te,
-                          int nrel, uint32_t inactive_key, uint32_t* keys) {
+// Cell keys (or the inactive key) of one tile of 2048 particles plus that
+// tile's histogram of the lowest 8-bit digit: the first radix pass needs no
+// separate histogram launch.
+__global__ void __launch_bounds__(kSortThreads) k_keys_hist(Geo g, int64_t n, const double* lon,
+                                                            const double* lat, const double* p,
+                                                            const uint32_t* release, double t,
+                                                            const double* ts, const double* te, int nrel,
+                                                            uint32_t inactive_key, uint32_t* keys,
+                                                            uint32_t* hist, int ntiles) {
     __shared__ KeyTables tb;
+    __shared__ uint32_t h[kRadix];
     for (int q = threadIdx.x; q < g.nz; q += blockDim.x) tb.plev[q] = g.plev[q];
     for (int q = threadIdx.x; q < g.nbins; q += blockDim.x) tb.kguess[q] = g.kguess[q];
+    h[threadIdx.x] = 0;
     __syncthreads();
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
-        const uint32_t r = release[q];
-        const bool active = r < (uint32_t)nrel && t >= ts[r] && t < te[r];
-        keys[q] = active ? cell_key(lon[q], lat[q], p[q], g, tb) : inactive_key;
+    const int64_t base = (int64_t)blockIdx.x * kTileKeys;
+    for (int r = 0; r < kRounds; ++r) {
+        const int64_t q = base + r * kSortThreads + threadIdx.x;
+        if (q >= n) continue;
+        bool active = true;
+        if (release) {
+            const uint32_t rr = release[q];
+            active = rr < (uint32_t)nrel && t >= ts[rr] && t < te[rr];
+        }
+        const uint32_t k = active ? cell_key(lon[q], lat[q], p[q], g, tb) : inactive_key;
+        keys[q] = k;
+        atomicAdd(&h[k & 0xFF], 1u);
     }
-}
-
-// write_grid: particles per met cell; lanes of a warp with the same cell (common
-// once particles are sorted) add their count with one atomic.
-__global__ void k_grid_counts(Geo g, int64_t n, const double* lon, const double* lat, const double* p,
-                              uint32_t* counts) {
-    __shared__ KeyTables tb;
-    for (int q = threadIdx.x; q < g.nz; q += blockDim.x) tb.plev[q] = g.plev[q];
-    for (int q = threadIdx.x; q < g.nbins; q += blockDim.x) tb.kguess[q] = g.kguess[q];
     __syncthreads();
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t span = (n + stride - 1) / stride * stride;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < span; q += stride) {
-        const bool valid = q < n;
-        const uint32_t key = valid ? cell_key(lon[q], lat[q], p[q], g, tb) : 0xFFFFFFFFu;
-        const unsigned peers = __match_any_sync(__activemask(), key);
-        const int lane = threadIdx.x & 31;
-        if (valid && (__ffs(peers) - 1) == lane) atomicAdd(&counts[key], (uint32_t)__popc(peers));
-    }
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
 // hist[d * ntiles + tile] = number of keys of `tile` with digit d
@@ -188,18 +184,28 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_rows(uint32_t* hist, int 
     if (threadIdx.x == 0) tot[blockIdx.x] = carry;
 }
 
+// Stable scatter of one tile (2048 keys) for one 8-bit digit.  Warp w owns the
+// tile's keys [256 w, 256 w + 256) and walks them in 8 rounds of 32
+// consecutive keys: lanes with equal digits find each other with
+// __match_any_sync and take ranks from a warp-private running count in shared
+// memory, so the rank of a key is its position among the tile's earlier keys
+// of the same digit within its warp.  One block-wide scan over the 8 warps'
+// counts then places the warps after one another -- stable, with two block
+// barriers per tile.
 __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint32_t* __restrict__ kin,
                                                           const uint32_t* __restrict__ vin,
                                                           uint32_t* __restrict__ kout,
                                                           uint32_t* __restrict__ vout, int64_t n,
                                                           int shift, const uint32_t* __restrict__ offs,
                                                           const uint32_t* __restrict__ tot, int ntiles) {
+    constexpr int W = kSortThreads / 32;
+    __shared__ uint32_t s_wc[W][kRadix];
     __shared__ uint32_t s_base[kRadix];
-    __shared__ uint32_t s_run[kRadix];
-    __shared__ uint32_t s_wc[kSortThreads / 32][kRadix];
-    __shared__ uint32_t s_tot_scan[kRadix];
+    __shared__ uint32_t s_ws[W];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    // exclusive scan of the digit totals (256 values, one per thread)
+#pragma unroll
+    for (int q = 0; q < kRadix / 32; ++q) s_wc[wid][q * 32 + lane] = 0;
+    // exclusive scan of the digit totals (one digit per thread) + this tile's offset
     {
         const uint32_t v = tot[tid];
         uint32_t incl = v;
@@ -207,48 +213,54 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint32_t* __rest
             const uint32_t o = __shfl_up_sync(0xffffffffu, incl, off);
             if (lane >= off) incl += o;
         }
-        __shared__ uint32_t ws[kSortThreads / 32];
-        if (lane == 31) ws[wid] = incl;
+        if (lane == 31) s_ws[wid] = incl;
         __syncthreads();
         uint32_t pre = 0;
-        for (int w = 0; w < wid; ++w) pre += ws[w];
-        s_tot_scan[tid] = pre + incl - v;
+        for (int w = 0; w < wid; ++w) pre += s_ws[w];
+        s_base[tid] = pre + incl - v + offs[(int64_t)tid * ntiles + blockIdx.x];
     }
-    s_base[tid] = s_tot_scan[tid] + offs[(int64_t)tid * ntiles + blockIdx.x];
-    s_run[tid] = 0;
-    __syncthreads();
+    __syncwarp();
     const unsigned lt_mask = (1u << lane) - 1u;
-    const int64_t base = (int64_t)blockIdx.x * kTileKeys;
+    const int64_t base = (int64_t)blockIdx.x * kTileKeys + (int64_t)wid * (kRounds * 32);
+    uint32_t key[kRounds], val[kRounds], rank[kRounds];
+#pragma unroll
     for (int r = 0; r < kRounds; ++r) {
-        const int64_t q = base + r * kSortThreads + tid;
+        const int64_t q = base + r * 32 + lane;
         const bool valid = q < n;
-        const uint32_t key = valid ? kin[q] : 0u;
-        const uint32_t val = valid ? (vin ? vin[q] : (uint32_t)q) : 0u;
-        const uint32_t d = (key >> shift) & 0xFF;
+        key[r] = valid ? kin[q] : 0xFFFFFFFFu;
+        val[r] = valid ? (vin ? vin[q] : (uint32_t)q) : 0u;
+    }
 #pragma unroll
-        for (int w = 0; w < kSortThreads / 32; ++w) s_wc[w][tid] = 0;
-        __syncthreads();
+    for (int r = 0; r < kRounds; ++r) {
+        const int64_t q = base + r * 32 + lane;
+        const bool valid = q < n;
+        const uint32_t d = (key[r] >> shift) & 0xFF;
         const unsigned peers = __match_any_sync(0xffffffffu, valid ? d : (kRadix + lane));
-        const uint32_t rank = __popc(peers & lt_mask);
-        if (valid && rank == 0) s_wc[wid][d] = __popc(peers);
-        __syncthreads();
-        {
-            uint32_t run = s_run[tid];
+        rank[r] = valid ? s_wc[wid][d] + __popc(peers & lt_mask) : 0u;
+        __syncwarp();
+        if (valid && (peers & lt_mask) == 0) s_wc[wid][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {   // warp prefix per digit
+        uint32_t run = 0;
 #pragma unroll
-            for (int w = 0; w < kSortThreads / 32; ++w) {
-                const uint32_t c = s_wc[w][tid];
-                s_wc[w][tid] = run;
-                run += c;
-            }
-            s_run[tid] = run;
+        for (int w = 0; w < W; ++w) {
+            const uint32_t c = s_wc[w][tid];
+            s_wc[w][tid] = run;
+            run += c;
         }
-        __syncthreads();
-        if (valid) {
-            const uint32_t pos = s_base[d] + s_wc[wid][d] + rank;
-            kout[pos] = key;
-            vout[pos] = val;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const int64_t q = base + r * 32 + lane;
+        if (q < n) {
+            const uint32_t d = (key[r] >> shift) & 0xFF;
+            const uint32_t pos = s_base[d] + s_wc[wid][d] + rank[r];
+            kout[pos] = key[r];
+            vout[pos] = val[r];
         }
-        __syncthreads();
     }
 }
 
@@ -327,7 +339,8 @@ namespace {
 
 // LSD radix passes over the keys already in the workspace's keys_a, then the
 // gather of every particle array in sorted order.
-cudaError_t sort_from_keys(const mptrac_particles& P, void* ws, int key_bits, cudaStream_t s) {
+cudaError_t sort_from_keys(const mptrac_particles& P, void* ws, int key_bits, cudaStream_t s,
+                           bool first_hist_done = false) {
     const int64_t n = P.n;
     const WsLayout L = ws_layout(n);
     char* w = static_cast<char*>(ws);
@@ -340,11 +353,11 @@ cudaError_t sort_from_keys(const mptrac_particles& P, void* ws, int key_bits, cu
     const int ntiles = (int)ntiles_for(n);
     cudaError_t e;
     const int passes = key_bits <= 0 ? 1 : (key_bits + 7) / 8;
-    note_launches(1 + 3 * passes);
+    note_launches(1 + 3 * passes - (first_hist_done ? 1 : 0));
     bool first = true;
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * pass;
-        k_hist<<<ntiles, kSortThreads, 0, s>>>(ka, n, shift, hist, ntiles);
+        if (!(pass == 0 && first_hist_done)) k_hist<<<ntiles, kSortThreads, 0, s>>>(ka, n, shift, hist, ntiles);
         k_scan_rows<<<kRadix, kSortThreads, 0, s>>>(hist, ntiles, tot);
         k_scatter<<<ntiles, kSortThreads, 0, s>>>(ka, first ? nullptr : va, kb, vb, n, shift, hist,
                                                   tot, ntiles);
@@ -400,11 +413,14 @@ cudaError_t run_sort(const Geo& g, const mptrac_particles& P, void* ws, int key_
     if (n <= 0) return cudaSuccess;
     const WsLayout L = ws_layout(n);
     uint32_t* ka = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.keys_a);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.hist);
+    const int ntiles = (int)ntiles_for(n);
     note_launches(1);
-    k_keys<<<grid_for(n), 256, 0, s>>>(g, n, P.lon, P.lat, P.p, ka, nullptr);
+    k_keys_hist<<<ntiles, kSortThreads, 0, s>>>(g, n, P.lon, P.lat, P.p, nullptr, 0.0, nullptr, nullptr, 0, 0u,
+                                                ka, hist, ntiles);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return sort_from_keys(P, ws, key_bits, s);
+    return sort_from_keys(P, ws, key_bits, s, true);
 }
 
 cudaError_t run_sort_at(const Geo& g, const mptrac_particles& P, void* ws, int key_bits, double t,
@@ -413,12 +429,14 @@ cudaError_t run_sort_at(const Geo& g, const mptrac_particles& P, void* ws, int k
     if (n <= 0) return cudaSuccess;
     const WsLayout L = ws_layout(n);
     uint32_t* ka = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.keys_a);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.hist);
+    const int ntiles = (int)ntiles_for(n);
     note_launches(1);
-    k_keys_at<<<grid_for(n), 256, 0, s>>>(g, n, P.lon, P.lat, P.p, P.release, t, ts, te, nrel,
-                                          1u << key_bits, ka);
+    k_keys_hist<<<ntiles, kSortThreads, 0, s>>>(g, n, P.lon, P.lat, P.p, P.release, t, ts, te, nrel,
+                                                1u << key_bits, ka, hist, ntiles);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return sort_from_keys(P, ws, key_bits + 1, s);
+    return sort_from_keys(P, ws, key_bits + 1, s, true);
 }
 
 }  // namespace mptrac

@@ -17,7 +17,9 @@
 //    per snapshot, fetched with 16-byte (float32) or 8-byte (16-bit) loads
 //    through L1/L2; sorting particles by cell makes a warp's stencils overlap;
 //  * random numbers are generated in registers (counter-based Philox): no
-//    random-number arrays are stored or read.
+//    random-number arrays are stored or read;
+//  * the longitude increments divide by cos(lat) with the fast division
+//    (2 ulp): 2e-7 relative on a 0.1-degree step, far inside the tolerance.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -438,7 +440,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
                 else
                     eval_wind<ST, false>(a.m0, a.m1, s, g, c1, w0, cc, V, var);
                 const float cl = coslat(lat);
-                ff lon_s = ff_add(lon, a.half_dt * a.kdeg * V.u / cl);
+                ff lon_s = ff_add(lon, __fdividef(a.half_dt * a.kdeg * V.u, cl));
                 ff lat_s = ff_add(lat, a.half_dt * a.kdeg * V.v);
                 ff p_s = ff_add(p, a.half_dt * V.w);
                 position_bc(lon_s, lat_s, p_s, g);
@@ -446,7 +448,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
                 Wind V2, dummy;
                 eval_wind<ST, false>(a.m0, a.m1, s, g, c2, wm, cc, V2, dummy);
                 const float cl2 = coslat(lat_s);
-                lon = ff_add(lon, a.dt * a.kdeg * V2.u / cl2);
+                lon = ff_add(lon, __fdividef(a.dt * a.kdeg * V2.u, cl2));
                 lat = ff_add(lat, a.dt * a.kdeg * V2.v);
                 p = ff_add(p, a.dt * V2.w);
             } else if (use_meso) {
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
                     dpp += wp * a.dt;
                 }
                 const float c3 = coslat(lat);
-                lon = ff_add(lon, dxm * a.kdeg / c3);
+                lon = ff_add(lon, __fdividef(dxm * a.kdeg, c3));
                 lat = ff_add(lat, dym * a.kdeg);
                 p = ff_add(p, dpp);
             }
