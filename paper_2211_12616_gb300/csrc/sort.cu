@@ -103,6 +103,25 @@ __global__ void k_keys(Geo g, int64_t n, const double* lon, const double* lat, c
     }
 }
 
+// write_grid: particles per met cell; lanes of a warp with the same cell (common
+// once particles are sorted) add their count with one atomic.
+__global__ void k_grid_counts(Geo g, int64_t n, const double* lon, const double* lat, const double* p,
+                              uint32_t* counts) {
+    __shared__ KeyTables tb;
+    for (int q = threadIdx.x; q < g.nz; q += blockDim.x) tb.plev[q] = g.plev[q];
+    for (int q = threadIdx.x; q < g.nbins; q += blockDim.x) tb.kguess[q] = g.kguess[q];
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t span = (n + stride - 1) / stride * stride;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < span; q += stride) {
+        const bool valid = q < n;
+        const uint32_t key = valid ? cell_key(lon[q], lat[q], p[q], g, tb) : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(__activemask(), key);
+        const int lane = threadIdx.x & 31;
+        if (valid && (__ffs(peers) - 1) == lane) atomicAdd(&counts[key], (uint32_t)__popc(peers));
+    }
+}
+
 // Cell keys (or the inactive key) of one tile of 2048 particles plus that
 // tile's histogram of the lowest 8-bit digit: the first radix pass needs no
 // separate histogram launch.
