@@ -207,10 +207,10 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_rows(uint32_t* hist, int 
 // tile's keys [256 w, 256 w + 256) and walks them in 8 rounds of 32
 // consecutive keys: lanes with equal digits find each other with
 // __match_any_sync and take ranks from a warp-private running count in shared
-// memory, so the rank of a key is its position among the tile's earlier keys
-// of the same digit within its warp.  One block-wide scan over the 8 warps'
-// counts then places the warps after one another -- stable, with two block
-// barriers per tile.
+// memory.  Scans over warps and over digits then give every key its place in
+// the tile sorted by digit (stable); the tile is staged in that order in
+// shared memory and written out by consecutive threads, so each digit's run
+// of keys lands in consecutive global addresses (coalesced writes).
 __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint32_t* __restrict__ kin,
                                                           const uint32_t* __restrict__ vin,
                                                           uint32_t* __restrict__ kout,
@@ -219,13 +219,15 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint32_t* __rest
                                                           const uint32_t* __restrict__ tot, int ntiles) {
     constexpr int W = kSortThreads / 32;
     __shared__ uint32_t s_wc[W][kRadix];
-    __shared__ uint32_t s_base[kRadix];
+    __shared__ uint32_t s_base[kRadix];   // global start of each digit's run of this tile
+    __shared__ uint32_t s_tp[kRadix];     // start of each digit inside the staged tile
     __shared__ uint32_t s_ws[W];
+    __shared__ uint32_t s_key[kTileKeys];
+    __shared__ uint32_t s_val[kTileKeys];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 #pragma unroll
     for (int q = 0; q < kRadix / 32; ++q) s_wc[wid][q * 32 + lane] = 0;
-    // exclusive scan of the digit totals (one digit per thread) + this tile's offset
-    {
+    {   // exclusive scan of the digit totals + this tile's offset within each digit
         const uint32_t v = tot[tid];
         uint32_t incl = v;
         for (int off = 1; off < 32; off <<= 1) {
@@ -238,9 +240,9 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint32_t* __rest
         for (int w = 0; w < wid; ++w) pre += s_ws[w];
         s_base[tid] = pre + incl - v + offs[(int64_t)tid * ntiles + blockIdx.x];
     }
-    __syncwarp();
     const unsigned lt_mask = (1u << lane) - 1u;
-    const int64_t base = (int64_t)blockIdx.x * kTileKeys + (int64_t)wid * (kRounds * 32);
+    const int64_t tile0 = (int64_t)blockIdx.x * kTileKeys;
+    const int64_t base = tile0 + (int64_t)wid * (kRounds * 32);
     uint32_t key[kRounds], val[kRounds], rank[kRounds];
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
@@ -249,6 +251,7 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint32_t* __rest
         key[r] = valid ? kin[q] : 0xFFFFFFFFu;
         val[r] = valid ? (vin ? vin[q] : (uint32_t)q) : 0u;
     }
+    __syncthreads();   // every warp's counters zeroed, s_ws reusable
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
         const int64_t q = base + r * 32 + lane;
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint32_t* __rest
         __syncwarp();
     }
     __syncthreads();
-    {   // warp prefix per digit
+    {   // thread = digit: prefix over warps, then exclusive scan of the tile's digit counts
         uint32_t run = 0;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
@@ -269,6 +272,16 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint32_t* __rest
             s_wc[w][tid] = run;
             run += c;
         }
+        uint32_t incl = run;
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += o;
+        }
+        if (lane == 31) s_ws[wid] = incl;
+        __syncthreads();
+        uint32_t pre = 0;
+        for (int w = 0; w < wid; ++w) pre += s_ws[w];
+        s_tp[tid] = pre + incl - run;
     }
     __syncthreads();
 #pragma unroll
@@ -276,10 +289,20 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint32_t* __rest
         const int64_t q = base + r * 32 + lane;
         if (q < n) {
             const uint32_t d = (key[r] >> shift) & 0xFF;
-            const uint32_t pos = s_base[d] + s_wc[wid][d] + rank[r];
-            kout[pos] = key[r];
-            vout[pos] = val[r];
+            const uint32_t loc = s_tp[d] + s_wc[wid][d] + rank[r];
+            s_key[loc] = key[r];
+            s_val[loc] = val[r];
         }
+    }
+    __syncthreads();
+    const int64_t left = n - tile0;
+    const int cnt = left < kTileKeys ? (int)left : kTileKeys;
+    for (int e = tid; e < cnt; e += kSortThreads) {
+        const uint32_t k = s_key[e];
+        const uint32_t d = (k >> shift) & 0xFF;
+        const uint32_t pos = s_base[d] + (uint32_t)e - s_tp[d];
+        kout[pos] = k;
+        vout[pos] = s_val[e];
     }
 }
 
