@@ -131,7 +131,6 @@ cudaError_t launch_colstats(const float* D, int64_t n, int ncol, double* sum, do
 cudaError_t launch_surr_fused(int storage, Surrogate& S, const Geo& g, MetView m0, MetView m1, int64_t n,
                               double* lon, double* lat, double* p, float w, int window_ok, uint8_t* fallback,
                               double lon0, cudaStream_t s);
-cudaError_t launch_surr_apply(Surrogate& S, int64_t n, int window_ok, double* lon, double* lat, double* p,
-                              uint8_t* fallback, double lon0, double pmin, double pmax, cudaStream_t s);
+
 
 }  // namespace mptrac

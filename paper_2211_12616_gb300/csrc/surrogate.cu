@@ -360,35 +360,6 @@ __global__ void k_cast_weights(const float* theta, __nv_bfloat16* W1b, __nv_bflo
     if (i < NOP) b3p[i] = i < NO ? theta[OB3 + i] : 0.f;
 }
 
-// Apply predicted displacements to in-envelope particles; flag the others for
-// the plain integrator.  Envelope: |lat| <= 80 deg and every standardised
-// feature within +-4 (env from k_normalise) and the window inside the interval.
-__global__ void k_apply(int64_t n, const float* __restrict__ Yh, const float* mu_y, const float* sd_y,
-                        const uint8_t* env, int window_ok, double* lon, double* lat, double* p,
-                        uint8_t* fallback, double lon0, double pmin, double pmax) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
-        const double la = lat[q];
-        const bool ok = window_ok && env[q] && fabs(la) <= 80.0;
-        fallback[q] = ok ? 0 : 1;
-        if (!ok) continue;
-        const double dx = (double)(Yh[q * NOP + 0] * sd_y[0] + mu_y[0]);
-        const double dy = (double)(Yh[q * NOP + 1] * sd_y[1] + mu_y[1]);
-        const double dz = (double)(Yh[q * NOP + 2] * sd_y[2] + mu_y[2]);
-        double lo = lon[q] + dx / (kR * cos(la * (kPi / 180.0))) * (180.0 / kPi);
-        double lt = la + dy / kR * (180.0 / kPi);
-        double pp = p[q] * exp(dz);
-        if (lt > 90.0) { lt = 180.0 - lt; lo += 180.0; }
-        else if (lt < -90.0) { lt = -180.0 - lt; lo += 180.0; }
-        double r = fmod(lo - lon0, 360.0);
-        if (r < 0.0) r += 360.0;
-        if (r >= 360.0) r -= 360.0;
-        lon[q] = lon0 + r;
-        lat[q] = lt;
-        p[q] = fmin(fmax(pp, pmin), pmax);
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Fused inference: stencil gather -> standardise (shared memory, bf16) ->
 // three tensor-core layers -> displacement, for tiles of 128 particles.
@@ -886,12 +857,6 @@ cudaError_t launch_surr_fused(int storage, Surrogate& S, const Geo& g, MetView m
     return cudaGetLastError();
 }
 
-cudaError_t launch_surr_apply(Surrogate& S, int64_t n, int window_ok, double* lon, double* lat, double* p,
-                              uint8_t* fallback, double lon0, double pmin, double pmax, cudaStream_t s) {
-    note_launches(1);
-    k_apply<<<grid1(n, 256), 256, 0, s>>>(n, S.Yh, S.mu_y, S.sd_y, S.env, window_ok, lon, lat, p, fallback,
-                                          lon0, pmin, pmax);
-    return cudaGetLastError();
-}
+
 
 }  // namespace mptrac
