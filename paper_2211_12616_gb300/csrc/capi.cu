@@ -178,6 +178,12 @@ int run_transport(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
     a.dt = (float)dt;
     a.half_dt = (float)(0.5 * dt);
     a.kdeg = (float)(180.0 / (kPi * kRadius));
+    {
+        // float products, rounded once like the device multiplication they replace
+        volatile float hd = a.half_dt, dd = a.dt, kd = a.kdeg;
+        a.hk = hd * kd;
+        a.dk = dd * kd;
+    }
     a.turb = turb;
     a.meso = meso;
     if (mode != MODE_ADVECT) {
@@ -191,6 +197,10 @@ int run_transport(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
     }
     a.key0 = (uint32_t)(seed & 0xFFFFFFFFull);
     a.key1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {   // Philox4x32 key bumps (Salmon et al., SC'11)
+        a.ks[2 * r] = a.key0 + (uint32_t)r * 0x9E3779B9u;
+        a.ks[2 * r + 1] = a.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
     const int grid = (int)std::min<int64_t>((P->n + kBlock - 1) / kBlock, (int64_t)1 << 20);
     for (int n0 = 0; n0 < nsteps; n0 += kMaxStepsPerLaunch) {
         const int cnt = std::min(kMaxStepsPerLaunch, nsteps - n0);

@@ -56,15 +56,19 @@ struct StepArgs {
     int n_rel;
     int nsteps;
     float dt, half_dt, kdeg;      // kdeg = 180 / (pi R)  [deg per metre]
+    float hk, dk;                 // float products half_dt * kdeg and dt * kdeg
     int turb, meso;
     float sh, sv, inv_H;          // sqrt(2 Dx dt), sqrt(2 Dz dt), 1/H
     float r_ar, a_ar;             // AR(1) coefficient r and sqrt(1 - r^2) f
     uint32_t key0, key1;          // Philox key = seed
+    uint32_t ks[20];              // Philox key schedule: round r uses (ks[2r], ks[2r+1])
     uint64_t step0;
     float wt[2 * kMaxStepsPerLaunch];   // time weights at t_n and t_n + dt/2
 };
 
-enum Mode { MODE_ADVECT = 0, MODE_DIFFUSE = 1, MODE_STEP = 2 };
+// MODE_STEP_FULL is MODE_STEP with both diffusion parts on, resolved at compile
+// time (the launcher picks it); the C ABI passes only the first three.
+enum Mode { MODE_ADVECT = 0, MODE_DIFFUSE = 1, MODE_STEP = 2, MODE_STEP_FULL = 3 };
 
 // Process-wide count of kernels this library has launched (inspection only).
 void note_launches(int n);

@@ -32,7 +32,6 @@ namespace mptrac {
 namespace {
 
 constexpr float kCosFloor = 1.745329243e-05f;   // cos(89.999 deg)
-constexpr float kTwoPow23Inv = 1.1920928955078125e-07f;
 
 // ---------------------------------------------------------------------------
 // float-float arithmetic (value = hi + lo, |lo| <= ulp(hi)/2)
@@ -132,9 +131,23 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// top 23 bits -> (0, 1), exact in float32
+// top 23 bits m -> (m + 1/2) 2^-23 in (0, 1): the float with exponent 0 and
+// mantissa m is 1 + m 2^-23, and subtracting 1 - 2^-24 from it is exact
+// (the difference (2m + 1) 2^-24 has at most 24 significant bits).
 __device__ __forceinline__ float u23(uint32_t x) {
-    return (__uint2float_rn(x >> 9) + 0.5f) * kTwoPow23Inv;
+    return __fsub_rn(__uint_as_float(0x3F800000u | (x >> 9)), 0.999999940395355224609375f);
+}
+
+// Philox4x32-10 with the key schedule taken from the launch arguments
+// (round r uses ks[2r], ks[2r + 1]).
+__device__ __forceinline__ uint4 philox4x32_10_ks(uint4 c, const uint32_t* ks) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ ks[2 * r], lo1, hi0 ^ c.w ^ ks[2 * r + 1], lo0);
+    }
+    return c;
 }
 
 // Box-Muller pair from two words.  -ln(u) comes from the hardware log2 where
@@ -390,13 +403,67 @@ __device__ __forceinline__ void load_tables(Smem& s, const Geo& g, const MetView
 // ---------------------------------------------------------------------------
 // The particle kernel
 // ---------------------------------------------------------------------------
+// Midpoint position rules in float: latitude reflected over the poles (ff,
+// longitude + 180), longitude wrapped into [lon0, lon0 + 360).  The pressure
+// needs no rule here: `locate` clamps it to the level range.  The midpoint
+// only places the second wind evaluation, so its longitude needs no more
+// than float precision.
+__device__ __forceinline__ void midpoint_bc(float& lon, ff& lat, const Geo& g) {
+    if (ff_greater(lat, 90.f, 0.f)) {
+        lat.hi = __fsub_rn(180.f, lat.hi);
+        lat.lo = -lat.lo;
+        lon += 180.f;
+    } else if (ff_less(lat, -90.f, 0.f)) {
+        lat.hi = __fsub_rn(-180.f, lat.hi);
+        lat.lo = -lat.lo;
+        lon += 180.f;
+    }
+    const float L0 = g.lon0, L1 = g.lon0 + 360.f;
+    if (!(lon < L1) || lon < L0) {
+        const float turns = floorf((lon - L0) * (1.0f / 360.0f));
+        if (isfinite(turns)) {
+            lon = fmaf(-360.f, turns, lon);
+            if (lon >= L1) lon -= 360.f;
+            if (lon < L0) lon += 360.f;
+        }
+    }
+}
+
+// Gaussian draws of one step: turbulence from counter (id, step, 0, release),
+// mesoscale from (id, step, 1, release); three of the four normals of each
+// draw are used.
+struct Normals {
+    float t0, t1, t2;   // turbulence: east, north, vertical
+    float m0, m1, m2;   // mesoscale: u, v, omega
+};
+
+__device__ __forceinline__ void draw_turb(const StepArgs& a, uint32_t pid, uint32_t step, uint32_t rel,
+                                          Normals& z) {
+    const uint4 wd = philox4x32_10_ks(make_uint4(pid, step, 0u, rel), a.ks);
+    float unused;
+    box_muller(wd.x, wd.y, z.t0, z.t1);
+    box_muller(wd.z, wd.w, z.t2, unused);
+}
+__device__ __forceinline__ void draw_meso(const StepArgs& a, uint32_t pid, uint32_t step, uint32_t rel,
+                                          Normals& z) {
+    const uint4 wd = philox4x32_10_ks(make_uint4(pid, step, 1u, rel), a.ks);
+    float unused;
+    box_muller(wd.x, wd.y, z.m0, z.m1);
+    box_muller(wd.z, wd.w, z.m2, unused);
+}
+
+// ---------------------------------------------------------------------------
+// The particle kernel
+// ---------------------------------------------------------------------------
 template <int ST, int MODE, int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant__ StepArgs a) {
     __shared__ Smem s;
     load_tables(s, a.geo, a.m0, a.m1, ST != MPTRAC_FP32);
     const Geo& g = a.geo;
-    const bool use_meso = (MODE != MODE_ADVECT) && a.meso;
-    const bool use_turb = (MODE != MODE_ADVECT) && a.turb;
+    constexpr bool FULL = (MODE == MODE_STEP_FULL);
+    constexpr bool ADVECT = (MODE != MODE_DIFFUSE);
+    const bool use_meso = FULL || ((MODE != MODE_ADVECT) && a.meso);
+    const bool use_turb = FULL || ((MODE != MODE_ADVECT) && a.turb);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < a.n; idx += stride) {
         if (a.mask && !a.mask[idx]) continue;
@@ -429,27 +496,36 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
             wp = a.wp[idx];
         }
         for (int sidx = nlo; sidx < nhi; ++sidx) {
+            const uint32_t step = (uint32_t)(a.step0 + (uint64_t)sidx);
+            Normals z{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            // The draws do not depend on the position: with both diffusion
+            // parts compiled in they are made first, so that their integer
+            // work interleaves with the dependent chain of the advection.
+            if (FULL) {
+                draw_turb(a, pid, step, rel, z);
+                draw_meso(a, pid, step, rel, z);
+            }
             Wind var{0.f, 0.f, 0.f};
-            if (MODE != MODE_DIFFUSE) {
+            if (ADVECT) {
                 // ---- module_advection: explicit midpoint ----
                 const float w0 = a.wt[2 * sidx], wm = a.wt[2 * sidx + 1];
                 const Cell c1 = locate(lon.hi, lat, p.hi, g, s, cc.k);
                 Wind V;
-                if (MODE == MODE_STEP && use_meso)
+                if (MODE != MODE_ADVECT && use_meso)
                     eval_wind<ST, true>(a.m0, a.m1, s, g, c1, w0, cc, V, var);
                 else
                     eval_wind<ST, false>(a.m0, a.m1, s, g, c1, w0, cc, V, var);
                 const float cl = coslat(lat);
-                ff lon_s = ff_add(lon, __fdividef(a.half_dt * a.kdeg * V.u, cl));
-                ff lat_s = ff_add(lat, a.half_dt * a.kdeg * V.v);
-                ff p_s = ff_add(p, a.half_dt * V.w);
-                position_bc(lon_s, lat_s, p_s, g);
-                const Cell c2 = locate(lon_s.hi, lat_s, p_s.hi, g, s, cc.k);
+                float lon_m = lon.hi + __fdividef(a.hk * V.u, cl);
+                ff lat_m = ff_add(lat, a.hk * V.v);
+                const float p_m = p.hi + a.half_dt * V.w;
+                midpoint_bc(lon_m, lat_m, g);
+                const Cell c2 = locate(lon_m, lat_m, p_m, g, s, cc.k);
                 Wind V2, dummy;
                 eval_wind<ST, false>(a.m0, a.m1, s, g, c2, wm, cc, V2, dummy);
-                const float cl2 = coslat(lat_s);
-                lon = ff_add(lon, __fdividef(a.dt * a.kdeg * V2.u, cl2));
-                lat = ff_add(lat, a.dt * a.kdeg * V2.v);
+                const float cl2 = coslat(lat_m);
+                lon = ff_add(lon, __fdividef(a.dk * V2.u, cl2));
+                lat = ff_add(lat, a.dk * V2.v);
                 p = ff_add(p, a.dt * V2.w);
             } else if (use_meso) {
                 const float w0 = a.wt[2 * sidx];
@@ -459,25 +535,18 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
             }
             if (MODE != MODE_ADVECT && (use_turb || use_meso)) {
                 // ---- module_diffusion_turb / module_diffusion_meso ----
-                const uint32_t step = (uint32_t)(a.step0 + (uint64_t)sidx);
+                if (!FULL && use_turb) draw_turb(a, pid, step, rel, z);
+                if (!FULL && use_meso) draw_meso(a, pid, step, rel, z);
                 float dxm = 0.f, dym = 0.f, dpp = 0.f;
                 if (use_turb) {
-                    const uint4 wd = philox4x32_10(make_uint4(pid, step, 0u, rel), a.key0, a.key1);
-                    float z0, z1, z2, z3;
-                    box_muller(wd.x, wd.y, z0, z1);
-                    box_muller(wd.z, wd.w, z2, z3);
-                    dxm = a.sh * z0;
-                    dym = a.sh * z1;
-                    dpp = -p.hi * (a.sv * z2) * a.inv_H;
+                    dxm = a.sh * z.t0;
+                    dym = a.sh * z.t1;
+                    dpp = -p.hi * (a.sv * z.t2) * a.inv_H;
                 }
                 if (use_meso) {
-                    const uint4 wd = philox4x32_10(make_uint4(pid, step, 1u, rel), a.key0, a.key1);
-                    float m0, m1, m2, m3;
-                    box_muller(wd.x, wd.y, m0, m1);
-                    box_muller(wd.z, wd.w, m2, m3);
-                    up = fmaf(a.r_ar, up, a.a_ar * sqrtf(var.u) * m0);
-                    vp = fmaf(a.r_ar, vp, a.a_ar * sqrtf(var.v) * m1);
-                    wp = fmaf(a.r_ar, wp, a.a_ar * sqrtf(var.w) * m2);
+                    up = fmaf(a.r_ar, up, a.a_ar * sqrtf(var.u) * z.m0);
+                    vp = fmaf(a.r_ar, vp, a.a_ar * sqrtf(var.v) * z.m1);
+                    wp = fmaf(a.r_ar, wp, a.a_ar * sqrtf(var.w) * z.m2);
                     dxm += up * a.dt;
                     dym += vp * a.dt;
                     dpp += wp * a.dt;
@@ -700,9 +769,9 @@ int grid_for(int64_t n) {
 // Launch variants of the fused step (threads per block, minimum resident blocks
 // per SM -- which caps the registers): 0 = (256, 2) 128 registers, 1 = (128, 4)
 // 128 registers in finer blocks, 2 = (128, 5) 96 registers, 20 warps per SM.
-template <int ST, int BLOCK, int MINB>
+template <int ST, int MODE, int BLOCK, int MINB>
 cudaError_t launch_step_variant(const StepArgs& a, int grid, bool persistent, cudaStream_t s) {
-    auto kern = k_transport<ST, MODE_STEP, BLOCK, MINB>;
+    auto kern = k_transport<ST, MODE, BLOCK, MINB>;
     if (persistent) {
         static int per_sm = 0;   // resident blocks per SM of this instantiation (same on every GB300)
         if (per_sm <= 0) {
@@ -728,11 +797,18 @@ cudaError_t launch_step_variant(const StepArgs& a, int grid, bool persistent, cu
 template <int ST>
 cudaError_t launch_transport_st(int mode, const StepArgs& a, int grid, int variant, bool persistent,
                                 cudaStream_t s) {
+    if (mode == MODE_STEP && a.turb && a.meso) {
+        switch (variant) {
+            case 1: return launch_step_variant<ST, MODE_STEP_FULL, 128, 4>(a, grid, persistent, s);
+            case 2: return launch_step_variant<ST, MODE_STEP_FULL, 128, 5>(a, grid, persistent, s);
+            default: return launch_step_variant<ST, MODE_STEP_FULL, kBlock, 2>(a, grid, persistent, s);
+        }
+    }
     if (mode == MODE_STEP) {
         switch (variant) {
-            case 1: return launch_step_variant<ST, 128, 4>(a, grid, persistent, s);
-            case 2: return launch_step_variant<ST, 128, 5>(a, grid, persistent, s);
-            default: return launch_step_variant<ST, kBlock, 2>(a, grid, persistent, s);
+            case 1: return launch_step_variant<ST, MODE_STEP, 128, 4>(a, grid, persistent, s);
+            case 2: return launch_step_variant<ST, MODE_STEP, 128, 5>(a, grid, persistent, s);
+            default: return launch_step_variant<ST, MODE_STEP, kBlock, 2>(a, grid, persistent, s);
         }
     }
     switch (mode) {
