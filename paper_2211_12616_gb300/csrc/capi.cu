@@ -318,6 +318,15 @@ int mptrac_init_grid(mptrac_ctx** out, const mptrac_grid_desc* g) {
     G.lat0 = (float)g->lat0;
     G.inv_dlat = (float)(1.0 / g->dlat);
     G.inv_dlat_lo = (float)(1.0 / g->dlat - (double)G.inv_dlat);
+    {
+        volatile float l0 = G.lon0;   // the float sum the kernels compare against
+        G.lon1 = l0 + 360.0f;
+    }
+    G.dn = (float)(90.0 - g->lat0);
+    G.dn_lo = (float)((90.0 - g->lat0) - (double)G.dn);
+    G.ds = (float)(-90.0 - g->lat0);
+    G.ds_lo = (float)((-90.0 - g->lat0) - (double)G.ds);
+    G.dmid = -G.lat0;
     const double pmin = g->plev[nz - 1], pmax = g->plev[0];
     G.pmin = (float)pmin;
     G.pmin_lo = (float)(pmin - (double)G.pmin);

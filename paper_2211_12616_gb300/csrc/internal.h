@@ -20,6 +20,11 @@ constexpr int kBlock = 256;               // threads per block of the particle k
 struct Geo {
     int nx, ny, nz, nbins;
     float lon0, inv_dlon, lat0, inv_dlat, inv_dlat_lo;   // 1/dlat as float-float (hi, lo)
+    float lon1;                   // lon0 + 360 (float sum): longitudes live in [lon0, lon1)
+    // The particle kernels carry latitude as d = lat - lat0.  The poles and the
+    // equator in that coordinate: dn = 90 - lat0, ds = -90 - lat0 as float-float,
+    // dmid = -lat0 (exact).
+    float dn, dn_lo, ds, ds_lo, dmid;
     float pmin, pmax;             // level range (float)
     float pmin_lo, pmax_lo;       // pmin = pmin + pmin_lo exactly as float-float
     float lnp_top, inv_dln;       // ln(p) bin origin and inverse width

@@ -79,29 +79,43 @@ __device__ __forceinline__ float sin_taylor(float x) {
     return x * q;
 }
 
-// |cos(lat)| floored at cos(89.999 deg), as sin of the colatitude so that it
-// keeps its relative precision next to the poles.
-__device__ __forceinline__ float coslat(ff lat) {
-    float colat = (lat.hi >= 0.f) ? __fsub_rn(__fsub_rn(90.f, lat.hi), lat.lo)
-                                  : __fadd_rn(__fadd_rn(90.f, lat.hi), lat.lo);
+// |cos(lat)| floored at cos(89.999 deg), for the latitude d + inc with d =
+// lat - lat0 (float-float) and a float increment inc.  It is the sine of the
+// colatitude, formed from the pole's d so that it keeps its relative
+// precision next to the poles (the difference with the pole's hi part is
+// exact there).
+__device__ __forceinline__ float coslat(ff d, float inc, const Geo& g) {
+    float colat = (__fadd_rn(d.hi, inc) >= g.dmid)
+                      ? __fsub_rn(__fadd_rn(__fsub_rn(g.dn, d.hi), __fsub_rn(g.dn_lo, d.lo)), inc)
+                      : __fadd_rn(__fadd_rn(__fsub_rn(d.hi, g.ds), __fsub_rn(d.lo, g.ds_lo)), inc);
     colat = fminf(fmaxf(colat, -90.f), 90.f);
     const float c = fabsf(sin_taylor(colat * 0.017453292519943295f));
     return fmaxf(c, kCosFloor);
 }
 
-// module_position: reflect over the poles (lon + 180), wrap lon into
-// [lon0, lon0 + 360), clamp p to the level range.
-__device__ __forceinline__ void position_bc(ff& lon, ff& lat, ff& p, const Geo& g) {
-    if (ff_greater(lat, 90.f, 0.f)) {
-        lat.hi = __fsub_rn(180.f, lat.hi);   // exact: lat.hi in [90, 180]
-        lat.lo = -lat.lo;
+// Reflection of d = lat - lat0 over a pole with d = P (float-float):
+// d' = 2 P - d, longitude + 180.  The hi difference is exact (d.hi lies
+// within a factor 2 of 2 P.hi next to the pole), the lo parts are renormalised.
+__device__ __forceinline__ void reflect(ff& d, float ph, float pl) {
+    const float h = __fsub_rn(2.f * ph, d.hi);
+    const float l = __fsub_rn(2.f * pl, d.lo);
+    d.hi = __fadd_rn(h, l);
+    d.lo = __fsub_rn(l, __fsub_rn(d.hi, h));
+}
+
+// module_position on (lon, d = lat - lat0, p): reflect over the poles
+// (lon + 180), wrap lon into [lon0, lon0 + 360), clamp p to the level range.
+// The hi parts decide whether any rule can apply; the exact float-float
+// comparisons run only then.
+__device__ __forceinline__ void position_rules(ff& lon, ff& d, ff& p, const Geo& g) {
+    if (ff_greater(d, g.dn, g.dn_lo)) {
+        reflect(d, g.dn, g.dn_lo);
         lon = ff_add(lon, 180.f);
-    } else if (ff_less(lat, -90.f, 0.f)) {
-        lat.hi = __fsub_rn(-180.f, lat.hi);
-        lat.lo = -lat.lo;
+    } else if (ff_less(d, g.ds, g.ds_lo)) {
+        reflect(d, g.ds, g.ds_lo);
         lon = ff_add(lon, 180.f);
     }
-    const float L0 = g.lon0, L1 = g.lon0 + 360.f;
+    const float L0 = g.lon0, L1 = g.lon1;
     if (!ff_less(lon, L1, 0.f) || ff_less(lon, L0, 0.f)) {
         float turns = floorf((lon.hi - L0) * (1.0f / 360.0f));
         if (isfinite(turns)) {
@@ -112,6 +126,13 @@ __device__ __forceinline__ void position_bc(ff& lon, ff& lat, ff& p, const Geo& 
     }
     if (ff_less(p, g.pmin, g.pmin_lo)) { p.hi = g.pmin; p.lo = g.pmin_lo; }
     if (ff_greater(p, g.pmax, g.pmax_lo)) { p.hi = g.pmax; p.lo = g.pmax_lo; }
+}
+
+__device__ __forceinline__ void position_bc(ff& lon, ff& d, ff& p, const Geo& g) {
+    // NaN fails every comparison and also takes the exact path (which leaves it)
+    if (!(d.hi < g.dn && d.hi > g.ds && lon.hi < g.lon1 && lon.hi > g.lon0 && p.hi > g.pmin &&
+          p.hi < g.pmax))
+        position_rules(lon, d, p, g);
 }
 
 // ---------------------------------------------------------------------------
@@ -195,13 +216,14 @@ struct Cell {
 
 __device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.f), 1.f); }
 
-// The latitude fraction is formed in float-float and both weights are
+// The latitude enters as d = lat - lat0 in float-float.  The latitude
+// fraction is formed in float-float and both weights are
 // computed directly, so that next to a pole the small weight keeps its
 // relative precision (winds there vanish like the distance to the pole while
 // the longitude increment divides by cos(lat)).  The level search starts from
 // `k_hint` (the level of the previous evaluation; < 0: none), else from the
 // ln(p) table, and walks to the bracketing pair.
-__device__ __forceinline__ Cell locate(float lon, ff lat, float p, const Geo& g, const Smem& s,
+__device__ __forceinline__ Cell locate(float lon, ff d, float p, const Geo& g, const Smem& s,
                                        int k_hint) {
     Cell c;
     const float x = (lon - g.lon0) * g.inv_dlon;
@@ -213,8 +235,7 @@ __device__ __forceinline__ Cell locate(float lon, ff lat, float p, const Geo& g,
     c.fx = clamp01(x - xf);
     c.gx = 1.f - c.fx;
 
-    // y = (lat - lat0) / dlat as float-float (yh + ye)
-    const ff d = ff_add(lat, -g.lat0);
+    // y = d / dlat as float-float (yh + ye), d = lat - lat0
     const float yh = d.hi * g.inv_dlat;
     float ye = fmaf(d.hi, g.inv_dlat, -yh);
     ye = fmaf(d.hi, g.inv_dlat_lo, ye);
@@ -318,35 +339,37 @@ __device__ __forceinline__ void fetch_corners(const MetView& m0, const MetView& 
     cc.k = c.k;
 }
 
-// interpolation weights as pairs (same weight for both snapshots)
-struct Weights2 {
-    f2_t fx, gx, fy, gy, fz, gz;
+// The 8 trilinear corner weights, each as a pair (same weight for both
+// snapshots); corner order as in Corners.
+struct Weights8 {
+    f2_t w[8];
 };
 
-__device__ __forceinline__ Weights2 weights2(const Cell& c) {
-    return {f2_pack(c.fx, c.fx), f2_pack(c.gx, c.gx), f2_pack(c.fy, c.fy),
-            f2_pack(c.gy, c.gy), f2_pack(c.fz, c.fz), f2_pack(c.gz, c.gz)};
+__device__ __forceinline__ Weights8 weights8(const Cell& c) {
+    const f2_t gx = f2_pack(c.gx, c.gx), fx = f2_pack(c.fx, c.fx);
+    const f2_t gy = f2_pack(c.gy, c.gy), fy = f2_pack(c.fy, c.fy);
+    const f2_t gz = f2_pack(c.gz, c.gz), fz = f2_pack(c.fz, c.fz);
+    const f2_t a00 = f2_mul(gy, gz), a10 = f2_mul(fy, gz), a01 = f2_mul(gy, fz), a11 = f2_mul(fy, fz);
+    return {{f2_mul(gx, a00), f2_mul(fx, a00), f2_mul(gx, a10), f2_mul(fx, a10),
+             f2_mul(gx, a01), f2_mul(fx, a01), f2_mul(gx, a11), f2_mul(fx, a11)}};
 }
 
-// trilinear interpolation of 8 corner pairs: lon, then lat, then pressure
-__device__ __forceinline__ f2_t trilinear(const f2_t* x, const Weights2& W) {
-    const f2_t e0 = f2_fma(x[1], W.fx, f2_mul(x[0], W.gx));
-    const f2_t e1 = f2_fma(x[3], W.fx, f2_mul(x[2], W.gx));
-    const f2_t e2 = f2_fma(x[5], W.fx, f2_mul(x[4], W.gx));
-    const f2_t e3 = f2_fma(x[7], W.fx, f2_mul(x[6], W.gx));
-    const f2_t s0 = f2_fma(e1, W.fy, f2_mul(e0, W.gy));
-    const f2_t s1 = f2_fma(e3, W.fy, f2_mul(e2, W.gy));
-    return f2_fma(s1, W.fz, f2_mul(s0, W.gz));
+// trilinear interpolation of 8 corner pairs: sum of weight x corner value
+__device__ __forceinline__ f2_t trilinear(const f2_t* x, const Weights8& W) {
+    f2_t acc = f2_mul(W.w[0], x[0]);
+#pragma unroll
+    for (int q = 1; q < 8; ++q) acc = f2_fma(W.w[q], x[q], acc);
+    return acc;
 }
 
 // subgrid variance: spread of the corners about `mean`, weighted by the
-// interpolation weights wt (both snapshots at once)
-__device__ __forceinline__ f2_t weighted_var(const f2_t* x, const f2_t* wt, f2_t mean) {
+// interpolation weights (both snapshots at once)
+__device__ __forceinline__ f2_t weighted_var(const f2_t* x, const Weights8& W, f2_t mean) {
     f2_t acc = f2_pack(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const f2_t d = f2_sub(x[q], mean);
-        acc = f2_fma(f2_mul(wt[q], d), d, acc);
+        acc = f2_fma(f2_mul(W.w[q], d), d, acc);
     }
     return acc;
 }
@@ -365,21 +388,15 @@ __device__ __forceinline__ void eval_wind(const MetView& m0, const MetView& m1, 
                                           Wind& out, Wind& var) {
     const int col = c.j * g.nx + c.i;
     if (col != cc.col || c.k != cc.k) fetch_corners<ST>(m0, m1, s, g, c, col, cc);
-    const Weights2 W = weights2(c);
+    const Weights8 W = weights8(c);
     const f2_t tu = trilinear(cc.u, W), tv = trilinear(cc.v, W), tw = trilinear(cc.w, W);
     out.u = tlerp(tu, w);
     out.v = tlerp(tv, w);
     out.w = tlerp(tw, w);
     if (SIG) {
-        f2_t wt[8];
-        const float a00 = c.gy * c.gz, a10 = c.fy * c.gz, a01 = c.gy * c.fz, a11 = c.fy * c.fz;
-        const float ws[8] = {c.gx * a00, c.fx * a00, c.gx * a10, c.fx * a10,
-                             c.gx * a01, c.fx * a01, c.gx * a11, c.fx * a11};
-#pragma unroll
-        for (int q = 0; q < 8; ++q) wt[q] = f2_pack(ws[q], ws[q]);
-        var.u = tlerp(weighted_var(cc.u, wt, tu), w);
-        var.v = tlerp(weighted_var(cc.v, wt, tv), w);
-        var.w = tlerp(weighted_var(cc.w, wt, tw), w);
+        var.u = tlerp(weighted_var(cc.u, W, tu), w);
+        var.v = tlerp(weighted_var(cc.v, W, tv), w);
+        var.w = tlerp(weighted_var(cc.w, W, tw), w);
     }
 }
 
@@ -403,22 +420,20 @@ __device__ __forceinline__ void load_tables(Smem& s, const Geo& g, const MetView
 // ---------------------------------------------------------------------------
 // The particle kernel
 // ---------------------------------------------------------------------------
-// Midpoint position rules in float: latitude reflected over the poles (ff,
-// longitude + 180), longitude wrapped into [lon0, lon0 + 360).  The pressure
-// needs no rule here: `locate` clamps it to the level range.  The midpoint
-// only places the second wind evaluation, so its longitude needs no more
-// than float precision.
-__device__ __forceinline__ void midpoint_bc(float& lon, ff& lat, const Geo& g) {
-    if (ff_greater(lat, 90.f, 0.f)) {
-        lat.hi = __fsub_rn(180.f, lat.hi);
-        lat.lo = -lat.lo;
+// Midpoint position rules: latitude reflected over the poles (longitude +
+// 180), longitude wrapped into [lon0, lon0 + 360).  The pressure needs no
+// rule here: `locate` clamps it to the level range.  The midpoint only places
+// the second wind evaluation, so its longitude needs no more than float
+// precision.
+__device__ __forceinline__ void midpoint_rules(float& lon, ff& d, const Geo& g) {
+    if (ff_greater(d, g.dn, g.dn_lo)) {
+        reflect(d, g.dn, g.dn_lo);
         lon += 180.f;
-    } else if (ff_less(lat, -90.f, 0.f)) {
-        lat.hi = __fsub_rn(-180.f, lat.hi);
-        lat.lo = -lat.lo;
+    } else if (ff_less(d, g.ds, g.ds_lo)) {
+        reflect(d, g.ds, g.ds_lo);
         lon += 180.f;
     }
-    const float L0 = g.lon0, L1 = g.lon0 + 360.f;
+    const float L0 = g.lon0, L1 = g.lon1;
     if (!(lon < L1) || lon < L0) {
         const float turns = floorf((lon - L0) * (1.0f / 360.0f));
         if (isfinite(turns)) {
@@ -427,6 +442,10 @@ __device__ __forceinline__ void midpoint_bc(float& lon, ff& lat, const Geo& g) {
             if (lon < L0) lon += 360.f;
         }
     }
+}
+
+__device__ __forceinline__ void midpoint_bc(float& lon, ff& d, const Geo& g) {
+    if (!(d.hi < g.dn && d.hi > g.ds && lon < g.lon1 && lon >= g.lon0)) midpoint_rules(lon, d, g);
 }
 
 // Gaussian draws of one step: turbulence from counter (id, step, 0, release),
@@ -483,7 +502,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
         }
         if (nlo >= nhi) continue;
         ff lon = ff_make(a.lon[idx]);
-        ff lat = ff_make(a.lat[idx]);
+        ff d = ff_make(a.lat[idx] - g.lat0_d);   // latitude as d = lat - lat0
         ff p = ff_make(a.p[idx]);
         const uint32_t pid = a.id[idx];
         float up = 0.f, vp = 0.f, wp = 0.f;
@@ -505,43 +524,46 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
                 draw_turb(a, pid, step, rel, z);
                 draw_meso(a, pid, step, rel, z);
             }
+            // increments of this step (lon and lat in degrees, p in Pa)
+            float ilon = 0.f, ilat = 0.f, ip = 0.f;
             Wind var{0.f, 0.f, 0.f};
             if (ADVECT) {
                 // ---- module_advection: explicit midpoint ----
                 const float w0 = a.wt[2 * sidx], wm = a.wt[2 * sidx + 1];
-                const Cell c1 = locate(lon.hi, lat, p.hi, g, s, cc.k);
+                const Cell c1 = locate(lon.hi, d, p.hi, g, s, cc.k);
                 Wind V;
                 if (MODE != MODE_ADVECT && use_meso)
                     eval_wind<ST, true>(a.m0, a.m1, s, g, c1, w0, cc, V, var);
                 else
                     eval_wind<ST, false>(a.m0, a.m1, s, g, c1, w0, cc, V, var);
-                const float cl = coslat(lat);
+                const float cl = coslat(d, 0.f, g);
                 float lon_m = lon.hi + __fdividef(a.hk * V.u, cl);
-                ff lat_m = ff_add(lat, a.hk * V.v);
+                ff d_m = ff_add(d, a.hk * V.v);
                 const float p_m = p.hi + a.half_dt * V.w;
-                midpoint_bc(lon_m, lat_m, g);
-                const Cell c2 = locate(lon_m, lat_m, p_m, g, s, cc.k);
+                midpoint_bc(lon_m, d_m, g);
+                const Cell c2 = locate(lon_m, d_m, p_m, g, s, cc.k);
                 Wind V2, dummy;
                 eval_wind<ST, false>(a.m0, a.m1, s, g, c2, wm, cc, V2, dummy);
-                const float cl2 = coslat(lat_m);
-                lon = ff_add(lon, __fdividef(a.dk * V2.u, cl2));
-                lat = ff_add(lat, a.dk * V2.v);
-                p = ff_add(p, a.dt * V2.w);
+                const float cl2 = coslat(d_m, 0.f, g);
+                ilon = __fdividef(a.dk * V2.u, cl2);
+                ilat = a.dk * V2.v;
+                ip = a.dt * V2.w;
             } else if (use_meso) {
                 const float w0 = a.wt[2 * sidx];
-                const Cell c1 = locate(lon.hi, lat, p.hi, g, s, cc.k);
+                const Cell c1 = locate(lon.hi, d, p.hi, g, s, cc.k);
                 Wind V;
                 eval_wind<ST, true>(a.m0, a.m1, s, g, c1, w0, cc, V, var);
             }
             if (MODE != MODE_ADVECT && (use_turb || use_meso)) {
                 // ---- module_diffusion_turb / module_diffusion_meso ----
+                // at the position after advection: lat + ilat, p + ip
                 if (!FULL && use_turb) draw_turb(a, pid, step, rel, z);
                 if (!FULL && use_meso) draw_meso(a, pid, step, rel, z);
                 float dxm = 0.f, dym = 0.f, dpp = 0.f;
                 if (use_turb) {
                     dxm = a.sh * z.t0;
                     dym = a.sh * z.t1;
-                    dpp = -p.hi * (a.sv * z.t2) * a.inv_H;
+                    dpp = -(p.hi + ip) * (a.sv * z.t2) * a.inv_H;
                 }
                 if (use_meso) {
                     up = fmaf(a.r_ar, up, a.a_ar * sqrtf(var.u) * z.m0);
@@ -551,16 +573,19 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
                     dym += vp * a.dt;
                     dpp += wp * a.dt;
                 }
-                const float c3 = coslat(lat);
-                lon = ff_add(lon, __fdividef(dxm * a.kdeg, c3));
-                lat = ff_add(lat, dym * a.kdeg);
-                p = ff_add(p, dpp);
+                const float c3 = coslat(d, ilat, g);
+                ilon += __fdividef(dxm * a.kdeg, c3);
+                ilat += dym * a.kdeg;
+                ip += dpp;
             }
+            lon = ff_add(lon, ilon);
+            d = ff_add(d, ilat);
+            p = ff_add(p, ip);
             // ---- module_position ----
-            position_bc(lon, lat, p, g);
+            position_bc(lon, d, p, g);
         }
         a.lon[idx] = ff_val(lon);
-        a.lat[idx] = ff_val(lat);
+        a.lat[idx] = ff_val(d) + g.lat0_d;
         a.p[idx] = ff_val(p);
         if (use_meso) {
             a.up[idx] = up;
@@ -599,7 +624,7 @@ __global__ void __launch_bounds__(kBlock) k_interp(Geo g, MetView m0, MetView m1
     load_tables(s, g, m0, m1, ST != MPTRAC_FP32);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
-        const Cell c = locate(ff_make(lon[idx]).hi, ff_make(lat[idx]), ff_make(p[idx]).hi, g, s, -1);
+        const Cell c = locate(ff_make(lon[idx]).hi, ff_make(lat[idx] - g.lat0_d), ff_make(p[idx]).hi, g, s, -1);
         Wind V, var;
         Corners cc;
         cc.col = -1;
@@ -626,7 +651,7 @@ __global__ void __launch_bounds__(kBlock) k_sample(Geo g, MetView m0, MetView m1
     using R = typename RecT<ST>::T;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
-        const Cell c = locate(ff_make(lon[idx]).hi, ff_make(lat[idx]), ff_make(p[idx]).hi, g, s, -1);
+        const Cell c = locate(ff_make(lon[idx]).hi, ff_make(lat[idx] - g.lat0_d), ff_make(p[idx]).hi, g, s, -1);
         const int i1 = (c.i + 1 == g.nx) ? 0 : c.i + 1;
         const int col[4] = {c.j * g.nx + c.i, c.j * g.nx + i1, (c.j + 1) * g.nx + c.i, (c.j + 1) * g.nx + i1};
         float res[2][4];
@@ -687,13 +712,13 @@ __global__ void __launch_bounds__(kBlock) k_sedi(const SediArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < a.n; idx += stride) {
         const float lonf = ff_make(a.lon[idx]).hi;
-        const ff lat = ff_make(a.lat[idx]);
+        const ff d = ff_make(a.lat[idx] - g.lat0_d);
         ff p = ff_make(a.p[idx]);
         const float r = a.radius[idx], rp = a.rho_p[idx];
         int ccol = -1, ck = -1;
         float T0[8], T1[8];
         for (int n = 0; n < a.nsteps; ++n) {
-            const Cell c = locate(lonf, lat, p.hi, g, s, ck);
+            const Cell c = locate(lonf, d, p.hi, g, s, ck);
             const int col = c.j * g.nx + c.i;
             if (col != ccol || c.k != ck) {
                 const int i1 = (c.i + 1 == g.nx) ? 0 : c.i + 1;
