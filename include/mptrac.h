@@ -232,6 +232,9 @@ int mptrac_sort_at(mptrac_ctx* ctx, const mptrac_particles* parts, double t, voi
  *   variant     0: 256 threads per block, >= 2 resident blocks per SM (128 registers)
  *               1: 128 threads per block, >= 4 resident blocks per SM (128 registers)
  *               2: 128 threads per block, >= 5 resident blocks per SM (96 registers)
+ *               3: 128 threads per block, >= 6 resident blocks per SM (80 registers),
+ *                  the per-particle corner cache in shared memory (24.6 KB per block)
+ *               4: as 3 with >= 7 resident blocks per SM (72 registers)
  *   persistent  non-zero: one wave of blocks (SMs x resident blocks per SM) strides
  *               over the particles; zero: one thread per particle.
  * Errors: E_INVALID_ARG for an unknown variant. */

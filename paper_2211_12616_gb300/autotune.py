@@ -16,7 +16,7 @@ import os
 
 import torch
 
-VARIANTS = (0, 1, 2)
+VARIANTS = (0, 1, 2, 3, 4)
 PERSISTENT = (False, True)
 SORT_EVERY = (10, 20, 40, 120)
 

@@ -476,7 +476,7 @@ int mptrac_sort_at(mptrac_ctx* c, const mptrac_particles* P, double t, void* ws,
 
 int mptrac_set_launch(mptrac_ctx* c, int variant, int persistent) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
-    if (variant < 0 || variant > 2) return fail(MPTRAC_E_INVALID_ARG, "launch variant must be 0, 1 or 2 (got %d)", variant);
+    if (variant < 0 || variant > 4) return fail(MPTRAC_E_INVALID_ARG, "launch variant must be 0..4 (got %d)", variant);
     c->launch_variant = variant;
     c->persistent = persistent != 0;
     return ok();

@@ -24,6 +24,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 #include "met_record.cuh"
@@ -198,13 +199,17 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, fl
 // ---------------------------------------------------------------------------
 template <typename T> __device__ __forceinline__ T ldg_rec(const T* p) { return __ldg(p); }
 
-// Shared-memory tables of one block.
-struct Smem {
+// Shared-memory tables of one block.  NSC = kMaxNZ holds the scales of
+// 16-bit storage; float32 storage needs none (NSC = 1, unused).
+template <int NSC>
+struct SmemT {
     float plev[kMaxNZ];
     float inv_dp[kMaxNZ];
     int16_t kguess[kGuessBins];
-    float sc[2][3][kMaxNZ];   // scales of u, v, omega for slot 0 / 1 (16-bit storage)
+    float sc[2][3][NSC];   // scales of u, v, omega for slot 0 / 1
 };
+using Smem = SmemT<kMaxNZ>;
+template <int ST> using SmemFor = SmemT<ST == MPTRAC_FP32 ? 1 : kMaxNZ>;
 
 // Cell of a point: indices (lon i, lat j, lower level k) and the
 // interpolation weights as (f, g = 1 - f) pairs.  All indices are clamped into
@@ -223,7 +228,8 @@ __device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.f), 
 // the longitude increment divides by cos(lat)).  The level search starts from
 // `k_hint` (the level of the previous evaluation; < 0: none), else from the
 // ln(p) table, and walks to the bracketing pair.
-__device__ __forceinline__ Cell locate(float lon, ff d, float p, const Geo& g, const Smem& s,
+template <class S>
+__device__ __forceinline__ Cell locate(float lon, ff d, float p, const Geo& g, const S& s,
                                        int k_hint) {
     Cell c;
     const float x = (lon - g.lon0) * g.inv_dlon;
@@ -296,19 +302,74 @@ __device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
 }
 
 // The 8 corners of one cell on both snapshots, (u, v, omega) decoded and
-// scaled, kept in registers.  A particle moves about 1/60 of a 1-degree cell
+// scaled, kept per particle.  A particle moves about 1/60 of a 1-degree cell
 // per step, so consecutive wind evaluations almost always fall into the cell
-// already held here and need no memory access at all: the gather from L1/L2
-// is paid only when the particle changes cell.
-struct Corners {
+// already held here and need no global memory access at all: the gather from
+// L1/L2 is paid only when the particle changes cell.  Corner order q: bit 0 =
+// i+1, bit 1 = j+1, bit 2 = k+1; each value is a pair (snapshot 0, snapshot 1).
+//
+// RegCache holds the 24 pairs in registers (48 registers per thread).
+struct RegCache {
     int col, k;               // cached cell (record index of column (j, i), lower level); col < 0: empty
-    f2_t u[8], v[8], w[8];    // (snapshot 0, snapshot 1) per corner
+    f2_t u[8], v[8], w[8];
+    static constexpr int kGroups = 1;   // corners fetched in one group of 8
+    __device__ __forceinline__ void init(ulonglong2*) { col = -1; k = -1; }
+    __device__ __forceinline__ void store(int, const f2_t* U, const f2_t* V, const f2_t* W) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            u[q] = U[q];
+            v[q] = V[q];
+            w[q] = W[q];
+        }
+    }
+    __device__ __forceinline__ void get(int var, f2_t* x) const {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x[q] = var == 0 ? u[q] : (var == 1 ? v[q] : w[q]);
+    }
 };
 
-// corner order q: bit 0 = i+1, bit 1 = j+1, bit 2 = k+1
-template <int ST>
-__device__ __forceinline__ void fetch_corners(const MetView& m0, const MetView& m1, const Smem& s,
-                                              const Geo& g, const Cell& c, int col, Corners& cc) {
+// SmemCache holds them in the thread's slice of a block-wide shared array:
+// 12 slots of 16 bytes (two corners of one variable), slot e of thread t at
+// [e * BLOCK + t], so a warp reads 512 contiguous bytes per slot.  It frees
+// the registers for more resident warps at the cost of 12 shared loads per
+// wind evaluation.  It is filled one level (4 corners) at a time, which halves
+// the records in flight during a fetch.
+template <int BLOCK>
+struct SmemCache {
+    static constexpr int kGroups = 2;
+    int col, k;
+    ulonglong2* slot;
+    __device__ __forceinline__ void init(ulonglong2* base) {
+        col = -1;
+        k = -1;
+        slot = base + threadIdx.x;
+    }
+    // corners 4 gi .. 4 gi + 3 (U[0..3] etc.)
+    __device__ __forceinline__ void store(int gi, const f2_t* U, const f2_t* V, const f2_t* W) {
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int h = 2 * gi + hh;
+            slot[(0 * 4 + h) * BLOCK] = make_ulonglong2(U[2 * hh], U[2 * hh + 1]);
+            slot[(1 * 4 + h) * BLOCK] = make_ulonglong2(V[2 * hh], V[2 * hh + 1]);
+            slot[(2 * 4 + h) * BLOCK] = make_ulonglong2(W[2 * hh], W[2 * hh + 1]);
+        }
+    }
+    // The empty asm keeps the compiler from hoisting the loads of all three
+    // variables to the top of an evaluation (48 registers in flight).
+    __device__ __forceinline__ void get(int var, f2_t* x) const {
+        asm volatile("" ::: "memory");
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const ulonglong2 t = slot[(var * 4 + h) * BLOCK];
+            x[2 * h] = t.x;
+            x[2 * h + 1] = t.y;
+        }
+    }
+};
+
+template <int ST, class S, class C>
+__device__ __forceinline__ void fetch_corners(const MetView& m0, const MetView& m1, const S& s,
+                                              const Geo& g, const Cell& c, int col, C& cc) {
     using R = typename RecT<ST>::T;
     const int i1 = (c.i + 1 == g.nx) ? 0 : c.i + 1;
     const int row1 = col - c.i + g.nx;
@@ -316,31 +377,39 @@ __device__ __forceinline__ void fetch_corners(const MetView& m0, const MetView& 
                          (row1 + i1) * g.nz + c.k};
     const R* rec0 = static_cast<const R*>(m0.rec);
     const R* rec1 = static_cast<const R*>(m1.rec);
-    R r[2][8];
+    constexpr int QG = 8 / C::kGroups;   // corners per group
+#pragma unroll 1
+    for (int gi = 0; gi < C::kGroups; ++gi) {
+        R r[2][QG];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        r[0][q] = ldg_rec(rec0 + base[q & 3] + (q >> 2));
-        r[1][q] = ldg_rec(rec1 + base[q & 3] + (q >> 2));
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        float4 a = decode<ST>(r[0][q]);
-        float4 b = decode<ST>(r[1][q]);
-        if (ST != MPTRAC_FP32) {
-            const int k = c.k + (q >> 2);
-            a.x *= s.sc[0][0][k]; a.y *= s.sc[0][1][k]; a.z *= s.sc[0][2][k];
-            b.x *= s.sc[1][0][k]; b.y *= s.sc[1][1][k]; b.z *= s.sc[1][2][k];
+        for (int qq = 0; qq < QG; ++qq) {
+            const int q = gi * QG + qq;
+            r[0][qq] = ldg_rec(rec0 + base[q & 3] + (q >> 2));
+            r[1][qq] = ldg_rec(rec1 + base[q & 3] + (q >> 2));
         }
-        cc.u[q] = f2_pack(a.x, b.x);
-        cc.v[q] = f2_pack(a.y, b.y);
-        cc.w[q] = f2_pack(a.z, b.z);
+        f2_t U[QG], V[QG], W[QG];
+#pragma unroll
+        for (int qq = 0; qq < QG; ++qq) {
+            const int q = gi * QG + qq;
+            float4 a = decode<ST>(r[0][qq]);
+            float4 b = decode<ST>(r[1][qq]);
+            if (ST != MPTRAC_FP32) {
+                const int k = c.k + (q >> 2);
+                a.x *= s.sc[0][0][k]; a.y *= s.sc[0][1][k]; a.z *= s.sc[0][2][k];
+                b.x *= s.sc[1][0][k]; b.y *= s.sc[1][1][k]; b.z *= s.sc[1][2][k];
+            }
+            U[qq] = f2_pack(a.x, b.x);
+            V[qq] = f2_pack(a.y, b.y);
+            W[qq] = f2_pack(a.z, b.z);
+        }
+        cc.store(gi, U, V, W);
     }
     cc.col = col;
     cc.k = c.k;
 }
 
 // The 8 trilinear corner weights, each as a pair (same weight for both
-// snapshots); corner order as in Corners.
+// snapshots); corner order as in the corner caches.
 struct Weights8 {
     f2_t w[8];
 };
@@ -382,32 +451,35 @@ __device__ __forceinline__ float tlerp(f2_t ab, float w) {
 
 // Wind at a located point and time weight w (0 -> m0, 1 -> m1), with the
 // subgrid variances when SIG.
-template <int ST, bool SIG>
-__device__ __forceinline__ void eval_wind(const MetView& m0, const MetView& m1, const Smem& s,
-                                          const Geo& g, const Cell& c, float w, Corners& cc,
+template <int ST, bool SIG, class S, class C>
+__device__ __forceinline__ void eval_wind(const MetView& m0, const MetView& m1, const S& s,
+                                          const Geo& g, const Cell& c, float w, C& cc,
                                           Wind& out, Wind& var) {
     const int col = c.j * g.nx + c.i;
     if (col != cc.col || c.k != cc.k) fetch_corners<ST>(m0, m1, s, g, c, col, cc);
     const Weights8 W = weights8(c);
-    const f2_t tu = trilinear(cc.u, W), tv = trilinear(cc.v, W), tw = trilinear(cc.w, W);
-    out.u = tlerp(tu, w);
-    out.v = tlerp(tv, w);
-    out.w = tlerp(tw, w);
-    if (SIG) {
-        var.u = tlerp(weighted_var(cc.u, W, tu), w);
-        var.v = tlerp(weighted_var(cc.v, W, tv), w);
-        var.w = tlerp(weighted_var(cc.w, W, tw), w);
+    float o[3], sg[3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        f2_t x[8];
+        cc.get(v, x);
+        const f2_t t = trilinear(x, W);
+        o[v] = tlerp(t, w);
+        if (SIG) sg[v] = tlerp(weighted_var(x, W, t), w);
     }
+    out = Wind{o[0], o[1], o[2]};
+    if (SIG) var = Wind{sg[0], sg[1], sg[2]};
 }
 
-__device__ __forceinline__ void load_tables(Smem& s, const Geo& g, const MetView& m0,
+template <int NSC>
+__device__ __forceinline__ void load_tables(SmemT<NSC>& s, const Geo& g, const MetView& m0,
                                             const MetView& m1, bool scales) {
     for (int q = threadIdx.x; q < g.nz; q += blockDim.x) {
         s.plev[q] = g.plev[q];
         s.inv_dp[q] = g.inv_dp[q];
     }
     for (int q = threadIdx.x; q < g.nbins; q += blockDim.x) s.kguess[q] = g.kguess[q];
-    if (scales) {
+    if (NSC > 1 && scales) {
         for (int q = threadIdx.x; q < 3 * g.nz; q += blockDim.x) {
             const int var = q / g.nz, k = q - var * g.nz;
             s.sc[0][var][k] = m0.scales[var * g.nz + k];
@@ -474,13 +546,19 @@ __device__ __forceinline__ void draw_meso(const StepArgs& a, uint32_t pid, uint3
 // ---------------------------------------------------------------------------
 // The particle kernel
 // ---------------------------------------------------------------------------
-template <int ST, int MODE, int BLOCK, int MINB>
+// CACHE: 0 = corner cache in registers, 1 = in shared memory.
+template <int ST, int MODE, int BLOCK, int MINB, int CACHE>
 __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant__ StepArgs a) {
-    __shared__ Smem s;
+    __shared__ SmemFor<ST> s;
+    __shared__ ulonglong2 s_cc[CACHE ? 12 * BLOCK : 1];
+    using Cache = typename std::conditional<CACHE != 0, SmemCache<BLOCK>, RegCache>::type;
     load_tables(s, a.geo, a.m0, a.m1, ST != MPTRAC_FP32);
     const Geo& g = a.geo;
     constexpr bool FULL = (MODE == MODE_STEP_FULL);
     constexpr bool ADVECT = (MODE != MODE_DIFFUSE);
+    // draws made first (see below) only where the registers allow it (the
+    // 128-register variants)
+    constexpr bool EARLY_DRAWS = FULL && CACHE == 0 && MINB * BLOCK <= 512;
     const bool use_meso = FULL || ((MODE != MODE_ADVECT) && a.meso);
     const bool use_turb = FULL || ((MODE != MODE_ADVECT) && a.turb);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -506,9 +584,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
         ff p = ff_make(a.p[idx]);
         const uint32_t pid = a.id[idx];
         float up = 0.f, vp = 0.f, wp = 0.f;
-        Corners cc;
-        cc.col = -1;
-        cc.k = -1;
+        Cache cc;
+        cc.init(s_cc);
         if (use_meso) {
             up = a.up[idx];
             vp = a.vp[idx];
@@ -520,7 +597,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
             // The draws do not depend on the position: with both diffusion
             // parts compiled in they are made first, so that their integer
             // work interleaves with the dependent chain of the advection.
-            if (FULL) {
+            if (EARLY_DRAWS) {
                 draw_turb(a, pid, step, rel, z);
                 draw_meso(a, pid, step, rel, z);
             }
@@ -557,8 +634,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
             if (MODE != MODE_ADVECT && (use_turb || use_meso)) {
                 // ---- module_diffusion_turb / module_diffusion_meso ----
                 // at the position after advection: lat + ilat, p + ip
-                if (!FULL && use_turb) draw_turb(a, pid, step, rel, z);
-                if (!FULL && use_meso) draw_meso(a, pid, step, rel, z);
+                if (!EARLY_DRAWS && use_turb) draw_turb(a, pid, step, rel, z);
+                if (!EARLY_DRAWS && use_meso) draw_meso(a, pid, step, rel, z);
                 float dxm = 0.f, dym = 0.f, dpp = 0.f;
                 if (use_turb) {
                     dxm = a.sh * z.t0;
@@ -626,9 +703,8 @@ __global__ void __launch_bounds__(kBlock) k_interp(Geo g, MetView m0, MetView m1
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
         const Cell c = locate(ff_make(lon[idx]).hi, ff_make(lat[idx] - g.lat0_d), ff_make(p[idx]).hi, g, s, -1);
         Wind V, var;
-        Corners cc;
-        cc.col = -1;
-        cc.k = -1;
+        RegCache cc;
+        cc.init(nullptr);
         eval_wind<ST, true>(m0, m1, s, g, c, w, cc, V, var);
         ou[idx] = V.u;
         ov[idx] = V.v;
@@ -792,11 +868,24 @@ int grid_for(int64_t n) {
 }
 
 // Launch variants of the fused step (threads per block, minimum resident blocks
-// per SM -- which caps the registers): 0 = (256, 2) 128 registers, 1 = (128, 4)
-// 128 registers in finer blocks, 2 = (128, 5) 96 registers, 20 warps per SM.
-template <int ST, int MODE, int BLOCK, int MINB>
+// per SM -- which caps the registers -- and where the corner cache lives):
+// 0 = (256, 2) 128 registers, 1 = (128, 4) 128 registers in finer blocks,
+// 2 = (128, 5) 96 registers, 20 warps per SM; 3 = (128, 6) corner cache in
+// shared memory, 80 registers, 24 warps per SM; 4 = (128, 7) the same with 72
+// registers, 28 warps per SM (24 with 16-bit storage, whose scale tables take
+// shared memory too).
+template <int ST, int MODE, int BLOCK, int MINB, int CACHE>
 cudaError_t launch_step_variant(const StepArgs& a, int grid, bool persistent, cudaStream_t s) {
-    auto kern = k_transport<ST, MODE, BLOCK, MINB>;
+    auto kern = k_transport<ST, MODE, BLOCK, MINB, CACHE>;
+    if (CACHE) {
+        static bool carveout_set = false;   // prefer the largest shared-memory carveout
+        if (!carveout_set) {
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+                (void)cudaGetLastError();
+            carveout_set = true;
+        }
+    }
     if (persistent) {
         static int per_sm = 0;   // resident blocks per SM of this instantiation (same on every GB300)
         if (per_sm <= 0) {
@@ -824,21 +913,25 @@ cudaError_t launch_transport_st(int mode, const StepArgs& a, int grid, int varia
                                 cudaStream_t s) {
     if (mode == MODE_STEP && a.turb && a.meso) {
         switch (variant) {
-            case 1: return launch_step_variant<ST, MODE_STEP_FULL, 128, 4>(a, grid, persistent, s);
-            case 2: return launch_step_variant<ST, MODE_STEP_FULL, 128, 5>(a, grid, persistent, s);
-            default: return launch_step_variant<ST, MODE_STEP_FULL, kBlock, 2>(a, grid, persistent, s);
+            case 1: return launch_step_variant<ST, MODE_STEP_FULL, 128, 4, 0>(a, grid, persistent, s);
+            case 2: return launch_step_variant<ST, MODE_STEP_FULL, 128, 5, 0>(a, grid, persistent, s);
+            case 3: return launch_step_variant<ST, MODE_STEP_FULL, 128, 6, 1>(a, grid, persistent, s);
+            case 4: return launch_step_variant<ST, MODE_STEP_FULL, 128, 7, 1>(a, grid, persistent, s);
+            default: return launch_step_variant<ST, MODE_STEP_FULL, kBlock, 2, 0>(a, grid, persistent, s);
         }
     }
     if (mode == MODE_STEP) {
         switch (variant) {
-            case 1: return launch_step_variant<ST, MODE_STEP, 128, 4>(a, grid, persistent, s);
-            case 2: return launch_step_variant<ST, MODE_STEP, 128, 5>(a, grid, persistent, s);
-            default: return launch_step_variant<ST, MODE_STEP, kBlock, 2>(a, grid, persistent, s);
+            case 1: return launch_step_variant<ST, MODE_STEP, 128, 4, 0>(a, grid, persistent, s);
+            case 2: return launch_step_variant<ST, MODE_STEP, 128, 5, 0>(a, grid, persistent, s);
+            case 3: return launch_step_variant<ST, MODE_STEP, 128, 6, 1>(a, grid, persistent, s);
+            case 4: return launch_step_variant<ST, MODE_STEP, 128, 7, 1>(a, grid, persistent, s);
+            default: return launch_step_variant<ST, MODE_STEP, kBlock, 2, 0>(a, grid, persistent, s);
         }
     }
     switch (mode) {
-        case MODE_ADVECT: k_transport<ST, MODE_ADVECT, kBlock, 2><<<grid, kBlock, 0, s>>>(a); break;
-        default: k_transport<ST, MODE_DIFFUSE, kBlock, 2><<<grid, kBlock, 0, s>>>(a); break;
+        case MODE_ADVECT: k_transport<ST, MODE_ADVECT, kBlock, 2, 0><<<grid, kBlock, 0, s>>>(a); break;
+        default: k_transport<ST, MODE_DIFFUSE, kBlock, 2, 0><<<grid, kBlock, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }

@@ -75,6 +75,8 @@ def test_batched_run_parity_and_schedule_invariance(M, case):
     assert ended.any()
     for cfg in ({"variant": 1, "persistent": True, "sort_every": 10},
                 {"variant": 2, "persistent": True, "sort_every": 40},
+                {"variant": 3, "persistent": False, "sort_every": 20},
+                {"variant": 4, "persistent": True, "sort_every": 20},
                 {"variant": 0, "persistent": True, "sort_every": 120}):
         got = _run(M, case, cfg, graphs=True)
         for k in ("lon", "lat", "p", "up", "vp", "wp"):
