@@ -2,7 +2,8 @@
 // Section 6).  key = (j*nx + i)*nz + k of each particle's cell, computed in
 // float64 with the same expressions as the interpolation's cell rule, then a
 // stable least-significant-digit radix sort of (key, index) pairs with 8-bit
-// digits, then one gather of every particle array.
+// digits.  The key kernel also copies every particle array aside, and the
+// last pass gathers them from there into their sorted places.
 //
 // Each pass: (1) per-tile digit histograms, (2) per-digit scan over tiles,
 // (3) stable scatter.  A tile is 2048 keys handled by 256 threads in 8 rounds
@@ -23,13 +24,19 @@ constexpr int kRadix = 256;
 // Cell key from float64 positions, the definition: x = ((lon - lon0) mod 360)
 // / dlon, i = floor(x) mod nx; j = floor((lat - lat0) / dlat) clamped to
 // [0, ny-2]; k = (number of levels >= clamp(p)) - 1 clamped to [0, nz-2].
-__device__ __forceinline__ uint32_t cell_key_f64(double lon, double lat, double p, const Geo& g) {
-    double r = fmod(__dsub_rn(lon, g.lon0_d), 360.0);
-    if (r < 0.0) r = __dadd_rn(r, 360.0);
+// plevd: the float64 levels (a shared-memory copy).  The mod 360 and mod nx
+// are skipped where they are the identity (or one subtraction).
+__device__ __noinline__ uint32_t cell_key_f64(double lon, double lat, double p, const Geo& g,
+                                              const double* plevd) {
+    double r = __dsub_rn(lon, g.lon0_d);
+    if (!(r >= 0.0 && r < 360.0)) {
+        r = fmod(r, 360.0);
+        if (r < 0.0) r = __dadd_rn(r, 360.0);
+    }
     const double x = __ddiv_rn(r, g.dlon_d);
     long long i = (long long)floor(x);
-    i %= g.nx;
-    if (i < 0) i += g.nx;
+    if (i >= g.nx) i = (i - g.nx < g.nx) ? i - g.nx : i % g.nx;
+    if (i < 0) i = 0;   // x >= 0 here; guards a NaN longitude
     const double y = __ddiv_rn(__dsub_rn(lat, g.lat0_d), g.dlat_d);
     long long j = (long long)floor(y);
     j = j < 0 ? 0 : (j > g.ny - 2 ? g.ny - 2 : j);
@@ -37,7 +44,7 @@ __device__ __forceinline__ uint32_t cell_key_f64(double lon, double lat, double 
     int lo = 0, hi = g.nz;   // plev decreasing: length of the prefix with plev >= pc
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (g.plev_d[mid] >= pc) lo = mid + 1; else hi = mid;
+        if (plevd[mid] >= pc) lo = mid + 1; else hi = mid;
     }
     int k = lo - 1;
     k = k < 0 ? 0 : (k > g.nz - 2 ? g.nz - 2 : k);
@@ -45,9 +52,18 @@ __device__ __forceinline__ uint32_t cell_key_f64(double lon, double lat, double 
 }
 
 struct KeyTables {
+    double plev_d[kMaxNZ];
     float plev[kMaxNZ];
     int16_t kguess[kGuessBins];
 };
+
+__device__ __forceinline__ void load_key_tables(KeyTables& t, const Geo& g) {
+    for (int q = threadIdx.x; q < g.nz; q += blockDim.x) {
+        t.plev_d[q] = g.plev_d[q];
+        t.plev[q] = g.plev[q];
+    }
+    for (int q = threadIdx.x; q < g.nbins; q += blockDim.x) t.kguess[q] = g.kguess[q];
+}
 
 // Same key, computed in float32 when that is provably identical: the float32
 // cell coordinates are within key_mx / key_my cells (a bound derived from the
@@ -85,7 +101,7 @@ __device__ __forceinline__ uint32_t cell_key(double lon, double lat, double p, c
         if (k == 0 && !(pc < t.plev[0] - margin)) ok = false;
         if (k == g.nz - 2 && !(pc > t.plev[g.nz - 1] + margin)) ok = false;
     }
-    if (!ok || !(lf == lf) || !(af == af) || !(pf == pf)) return cell_key_f64(lon, lat, p, g);
+    if (!ok || !(lf == lf) || !(af == af) || !(pf == pf)) return cell_key_f64(lon, lat, p, g, t.plev_d);
     const int i = (int)xf;
     return (uint32_t)((j * g.nx + i) * g.nz + k);
 }
@@ -93,8 +109,7 @@ __device__ __forceinline__ uint32_t cell_key(double lon, double lat, double p, c
 __global__ void k_keys(Geo g, int64_t n, const double* lon, const double* lat, const double* p,
                        uint32_t* keys, uint32_t* vals) {
     __shared__ KeyTables t;
-    for (int q = threadIdx.x; q < g.nz; q += blockDim.x) t.plev[q] = g.plev[q];
-    for (int q = threadIdx.x; q < g.nbins; q += blockDim.x) t.kguess[q] = g.kguess[q];
+    load_key_tables(t, g);
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
@@ -108,8 +123,7 @@ __global__ void k_keys(Geo g, int64_t n, const double* lon, const double* lat, c
 __global__ void k_grid_counts(Geo g, int64_t n, const double* lon, const double* lat, const double* p,
                               uint32_t* counts) {
     __shared__ KeyTables tb;
-    for (int q = threadIdx.x; q < g.nz; q += blockDim.x) tb.plev[q] = g.plev[q];
-    for (int q = threadIdx.x; q < g.nbins; q += blockDim.x) tb.kguess[q] = g.kguess[q];
+    load_key_tables(tb, g);
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t span = (n + stride - 1) / stride * stride;
@@ -122,36 +136,61 @@ __global__ void k_grid_counts(Geo g, int64_t n, const double* lon, const double*
     }
 }
 
+// The particle arrays (null entries are absent) and their copies in the
+// workspace: `part` is sorted in place, `copy` holds the unsorted state.
+struct Arrays {
+    double* d[3];      // lon, lat, p
+    uint32_t* u[2];    // id, release
+    float* f[3];       // up, vp, wp
+};
+
+struct KeysArgs {
+    Geo g;
+    int64_t n;
+    Arrays part, copy;
+    double t;                      // time of the activity test (release windows)
+    const double *ts, *te;         // release windows [ts, te), or null: all active
+    int nrel;
+    uint32_t inactive_key;
+    uint32_t* keys;
+    uint32_t* hist;
+    int ntiles;
+};
+
 // Cell keys (or the inactive key) of one tile of 2048 particles plus that
 // tile's histogram of the lowest 8-bit digit: the first radix pass needs no
-// separate histogram launch.
-__global__ void __launch_bounds__(kSortThreads) k_keys_hist(Geo g, int64_t n, const double* lon,
-                                                            const double* lat, const double* p,
-                                                            const uint32_t* release, double t,
-                                                            const double* ts, const double* te, int nrel,
-                                                            uint32_t inactive_key, uint32_t* keys,
-                                                            uint32_t* hist, int ntiles) {
+// separate histogram launch.  Every particle array is copied aside on the way.
+__global__ void __launch_bounds__(kSortThreads) k_keys_hist(const __grid_constant__ KeysArgs a) {
     __shared__ KeyTables tb;
     __shared__ uint32_t h[kRadix];
-    for (int q = threadIdx.x; q < g.nz; q += blockDim.x) tb.plev[q] = g.plev[q];
-    for (int q = threadIdx.x; q < g.nbins; q += blockDim.x) tb.kguess[q] = g.kguess[q];
+    const Geo& g = a.g;
+    load_key_tables(tb, g);
     h[threadIdx.x] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kTileKeys;
     for (int r = 0; r < kRounds; ++r) {
         const int64_t q = base + r * kSortThreads + threadIdx.x;
-        if (q >= n) continue;
+        if (q >= a.n) continue;
+        const double lon = a.part.d[0][q], lat = a.part.d[1][q], p = a.part.d[2][q];
+        a.copy.d[0][q] = lon;
+        a.copy.d[1][q] = lat;
+        a.copy.d[2][q] = p;
         bool active = true;
-        if (release) {
-            const uint32_t rr = release[q];
-            active = rr < (uint32_t)nrel && t >= ts[rr] && t < te[rr];
+        if (a.part.u[1]) {
+            const uint32_t rr = a.part.u[1][q];
+            a.copy.u[1][q] = rr;
+            if (a.ts) active = rr < (uint32_t)a.nrel && a.t >= a.ts[rr] && a.t < a.te[rr];
         }
-        const uint32_t k = active ? cell_key(lon[q], lat[q], p[q], g, tb) : inactive_key;
-        keys[q] = k;
+        if (a.part.u[0]) a.copy.u[0][q] = a.part.u[0][q];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (a.part.f[c]) a.copy.f[c][q] = a.part.f[c][q];
+        const uint32_t k = active ? cell_key(lon, lat, p, g, tb) : a.inactive_key;
+        a.keys[q] = k;
         atomicAdd(&h[k & 0xFF], 1u);
     }
     __syncthreads();
-    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+    a.hist[(int64_t)threadIdx.x * a.ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
 // hist[d * ntiles + tile] = number of keys of `tile` with digit d
@@ -210,13 +249,18 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_rows(uint32_t* hist, int 
 // memory.  Scans over warps and over digits then give every key its place in
 // the tile sorted by digit (stable); the tile is staged in that order in
 // shared memory and written out by consecutive threads, so each digit's run
-// of keys lands in consecutive global addresses (coalesced writes).
+// of keys lands in consecutive global addresses (coalesced writes).  In the
+// last pass (FINAL) the keys and indices are not written: each sorted place
+// receives the particle's values, gathered from the copies.
+template <bool FINAL>
 __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint32_t* __restrict__ kin,
                                                           const uint32_t* __restrict__ vin,
                                                           uint32_t* __restrict__ kout,
                                                           uint32_t* __restrict__ vout, int64_t n,
                                                           int shift, const uint32_t* __restrict__ offs,
-                                                          const uint32_t* __restrict__ tot, int ntiles) {
+                                                          const uint32_t* __restrict__ tot, int ntiles,
+                                                          const __grid_constant__ Arrays part,
+                                                          const __grid_constant__ Arrays copy) {
     constexpr int W = kSortThreads / 32;
     __shared__ uint32_t s_wc[W][kRadix];
     __shared__ uint32_t s_base[kRadix];   // global start of each digit's run of this tile
@@ -301,35 +345,20 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint32_t* __rest
         const uint32_t k = s_key[e];
         const uint32_t d = (k >> shift) & 0xFF;
         const uint32_t pos = s_base[d] + (uint32_t)e - s_tp[d];
-        kout[pos] = k;
-        vout[pos] = s_val[e];
-    }
-}
-
-struct PermArgs {
-    int64_t n;
-    const uint32_t* perm;
-    double* dst_d[3];
-    const double* src_d[3];
-    uint32_t* dst_u[2];
-    const uint32_t* src_u[2];
-    float* dst_f[3];
-    const float* src_f[3];
-};
-
-__global__ void k_permute(const __grid_constant__ PermArgs a) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.n; q += stride) {
-        const uint32_t s = a.perm[q];
+        if (FINAL) {
+            const uint32_t src = s_val[e];
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            if (a.dst_d[c]) a.dst_d[c][q] = a.src_d[c][s];
+            for (int c = 0; c < 3; ++c) part.d[c][pos] = copy.d[c][src];
 #pragma unroll
-        for (int c = 0; c < 2; ++c)
-            if (a.dst_u[c]) a.dst_u[c][q] = a.src_u[c][s];
+            for (int c = 0; c < 2; ++c)
+                if (part.u[c]) part.u[c][pos] = copy.u[c][src];
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            if (a.dst_f[c]) a.dst_f[c][q] = a.src_f[c][s];
+            for (int c = 0; c < 3; ++c)
+                if (part.f[c]) part.f[c][pos] = copy.f[c][src];
+        } else {
+            kout[pos] = k;
+            vout[pos] = s_val[e];
+        }
     }
 }
 
@@ -379,10 +408,50 @@ cudaError_t launch_cell_keys(const Geo& g, int64_t n, const double* lon, const d
 
 namespace {
 
-// LSD radix passes over the keys already in the workspace's keys_a, then the
-// gather of every particle array in sorted order.
-cudaError_t sort_from_keys(const mptrac_particles& P, void* ws, int key_bits, cudaStream_t s,
-                           bool first_hist_done = false) {
+Arrays part_arrays(const mptrac_particles& P) {
+    return Arrays{{P.lon, P.lat, P.p}, {P.id, P.release}, {P.up, P.vp, P.wp}};
+}
+
+// Workspace copies of the arrays present in P (null where P has none).
+Arrays copy_arrays(const mptrac_particles& P, void* ws) {
+    const WsLayout L = ws_layout(P.n);
+    char* w = static_cast<char*>(ws);
+    const size_t n = (size_t)P.n;
+    Arrays c{};
+    for (int q = 0; q < 3; ++q) c.d[q] = reinterpret_cast<double*>(w + L.copy_d + q * align256(n * 8));
+    if (P.id) c.u[0] = reinterpret_cast<uint32_t*>(w + L.copy_u);
+    if (P.release) c.u[1] = reinterpret_cast<uint32_t*>(w + L.copy_u + align256(n * 4));
+    float* fl[3] = {P.up, P.vp, P.wp};
+    for (int q = 0; q < 3; ++q)
+        if (fl[q]) c.f[q] = reinterpret_cast<float*>(w + L.copy_f + q * align256(n * 4));
+    return c;
+}
+
+// Keys, first-digit histograms and copies of the particle arrays (one launch).
+cudaError_t keys_and_copies(const Geo& g, const mptrac_particles& P, void* ws, double t, const double* ts,
+                            const double* te, int nrel, uint32_t inactive_key, cudaStream_t s) {
+    const WsLayout L = ws_layout(P.n);
+    KeysArgs a{};
+    a.g = g;
+    a.n = P.n;
+    a.part = part_arrays(P);
+    a.copy = copy_arrays(P, ws);
+    a.t = t;
+    a.ts = ts;
+    a.te = te;
+    a.nrel = nrel;
+    a.inactive_key = inactive_key;
+    a.keys = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.keys_a);
+    a.hist = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.hist);
+    a.ntiles = (int)ntiles_for(P.n);
+    note_launches(1);
+    k_keys_hist<<<a.ntiles, kSortThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// LSD radix passes over the keys in the workspace's keys_a (first-digit
+// histograms already there); the last pass gathers the particle arrays.
+cudaError_t sort_from_keys(const mptrac_particles& P, void* ws, int key_bits, cudaStream_t s) {
     const int64_t n = P.n;
     const WsLayout L = ws_layout(n);
     char* w = static_cast<char*>(ws);
@@ -393,51 +462,26 @@ cudaError_t sort_from_keys(const mptrac_particles& P, void* ws, int key_bits, cu
     uint32_t* hist = reinterpret_cast<uint32_t*>(w + L.hist);
     uint32_t* tot = reinterpret_cast<uint32_t*>(w + L.tot);
     const int ntiles = (int)ntiles_for(n);
-    cudaError_t e;
+    const Arrays part = part_arrays(P), copy = copy_arrays(P, ws);
     const int passes = key_bits <= 0 ? 1 : (key_bits + 7) / 8;
-    note_launches(1 + 3 * passes - (first_hist_done ? 1 : 0));
-    bool first = true;
+    note_launches(3 * passes - 1);
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * pass;
-        if (!(pass == 0 && first_hist_done)) k_hist<<<ntiles, kSortThreads, 0, s>>>(ka, n, shift, hist, ntiles);
+        if (pass > 0) k_hist<<<ntiles, kSortThreads, 0, s>>>(ka, n, shift, hist, ntiles);
         k_scan_rows<<<kRadix, kSortThreads, 0, s>>>(hist, ntiles, tot);
-        k_scatter<<<ntiles, kSortThreads, 0, s>>>(ka, first ? nullptr : va, kb, vb, n, shift, hist,
-                                                  tot, ntiles);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        first = false;
+        const uint32_t* vin = pass == 0 ? nullptr : va;
+        if (pass + 1 == passes)
+            k_scatter<true><<<ntiles, kSortThreads, 0, s>>>(ka, vin, nullptr, nullptr, n, shift, hist, tot,
+                                                            ntiles, part, copy);
+        else
+            k_scatter<false><<<ntiles, kSortThreads, 0, s>>>(ka, vin, kb, vb, n, shift, hist, tot, ntiles,
+                                                             part, copy);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
         uint32_t* tmp = ka; ka = kb; kb = tmp;
         tmp = va; va = vb; vb = tmp;
     }
-    // copy the arrays aside, then gather them back in sorted order
-    PermArgs pa{};
-    pa.n = n;
-    pa.perm = va;
-    double* dd[3] = {P.lon, P.lat, P.p};
-    uint32_t* uu[2] = {P.id, P.release};
-    float* fl[3] = {P.up, P.vp, P.wp};
-    for (int c = 0; c < 3; ++c) {
-        if (!dd[c]) continue;
-        double* cp = reinterpret_cast<double*>(w + L.copy_d + c * align256((size_t)n * 8));
-        if ((e = cudaMemcpyAsync(cp, dd[c], (size_t)n * 8, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
-        pa.dst_d[c] = dd[c];
-        pa.src_d[c] = cp;
-    }
-    for (int c = 0; c < 2; ++c) {
-        if (!uu[c]) continue;
-        uint32_t* cp = reinterpret_cast<uint32_t*>(w + L.copy_u + c * align256((size_t)n * 4));
-        if ((e = cudaMemcpyAsync(cp, uu[c], (size_t)n * 4, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
-        pa.dst_u[c] = uu[c];
-        pa.src_u[c] = cp;
-    }
-    for (int c = 0; c < 3; ++c) {
-        if (!fl[c]) continue;
-        float* cp = reinterpret_cast<float*>(w + L.copy_f + c * align256((size_t)n * 4));
-        if ((e = cudaMemcpyAsync(cp, fl[c], (size_t)n * 4, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
-        pa.dst_f[c] = fl[c];
-        pa.src_f[c] = cp;
-    }
-    k_permute<<<grid_for(n), 256, 0, s>>>(pa);
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -451,34 +495,19 @@ cudaError_t launch_grid_counts(const Geo& g, int64_t n, const double* lon, const
 
 cudaError_t run_sort(const Geo& g, const mptrac_particles& P, void* ws, int key_bits,
                      cudaStream_t s) {
-    const int64_t n = P.n;
-    if (n <= 0) return cudaSuccess;
-    const WsLayout L = ws_layout(n);
-    uint32_t* ka = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.keys_a);
-    uint32_t* hist = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.hist);
-    const int ntiles = (int)ntiles_for(n);
-    note_launches(1);
-    k_keys_hist<<<ntiles, kSortThreads, 0, s>>>(g, n, P.lon, P.lat, P.p, nullptr, 0.0, nullptr, nullptr, 0, 0u,
-                                                ka, hist, ntiles);
-    cudaError_t e = cudaGetLastError();
+    if (P.n <= 0) return cudaSuccess;
+    cudaError_t e = keys_and_copies(g, P, ws, 0.0, nullptr, nullptr, 0, 0u, s);
     if (e != cudaSuccess) return e;
-    return sort_from_keys(P, ws, key_bits, s, true);
+    return sort_from_keys(P, ws, key_bits, s);
 }
 
 cudaError_t run_sort_at(const Geo& g, const mptrac_particles& P, void* ws, int key_bits, double t,
                         const double* ts, const double* te, int nrel, cudaStream_t s) {
-    const int64_t n = P.n;
-    if (n <= 0) return cudaSuccess;
-    const WsLayout L = ws_layout(n);
-    uint32_t* ka = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.keys_a);
-    uint32_t* hist = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.hist);
-    const int ntiles = (int)ntiles_for(n);
-    note_launches(1);
-    k_keys_hist<<<ntiles, kSortThreads, 0, s>>>(g, n, P.lon, P.lat, P.p, P.release, t, ts, te, nrel,
-                                                1u << key_bits, ka, hist, ntiles);
-    cudaError_t e = cudaGetLastError();
+    if (P.n <= 0) return cudaSuccess;
+    // without a release table every particle is active (ts == null)
+    cudaError_t e = keys_and_copies(g, P, ws, t, P.release ? ts : nullptr, te, nrel, 1u << key_bits, s);
     if (e != cudaSuccess) return e;
-    return sort_from_keys(P, ws, key_bits + 1, s, true);
+    return sort_from_keys(P, ws, key_bits + 1, s);
 }
 
 }  // namespace mptrac
