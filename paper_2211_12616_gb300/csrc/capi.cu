@@ -333,10 +333,11 @@ int mptrac_init_grid(mptrac_ctx** out, const mptrac_grid_desc* g) {
     G.pmax = (float)pmax;
     G.pmax_lo = (float)(pmax - (double)G.pmax);
     G.lnp_top = (float)ln_top;
-    // bound of the float32 cell-coordinate error (rounding of lon/lat to float,
-    // of the subtraction and of the scaled product), times 8 for safety
-    G.key_mx = (float)(8.0 * (std::ldexp(std::fabs(g->lon0) + 720.0, -24) / g->dlon + std::ldexp((double)g->nx, -23)));
-    G.key_my = (float)(8.0 * (std::ldexp(std::fabs(g->lat0) + 360.0, -24) / g->dlat + std::ldexp((double)g->ny, -23)));
+    // bound of the float32 cell-coordinate error: truncation of lon/lat to
+    // float (2^-23 |lon|), rounding of the subtraction (2^-24 |lon - lon0|), of
+    // 1/dlon and of the product (2^-24 |x| each), times 2 for safety
+    G.key_mx = (float)(2.0 * (std::ldexp(2.0 * std::fabs(g->lon0) + 1080.0, -24) / g->dlon + std::ldexp((double)g->nx, -23)));
+    G.key_my = (float)(2.0 * (std::ldexp(2.0 * std::fabs(g->lat0) + 540.0, -24) / g->dlat + std::ldexp((double)g->ny, -23)));
     G.inv_dln = (float)inv_dln;
     G.plev = c->d_plev;
     G.inv_dp = c->d_invdp;

@@ -6,8 +6,8 @@
 // last pass gathers them from there into their sorted places.
 //
 // Each pass: (1) per-tile digit histograms, (2) per-digit scan over tiles,
-// (3) stable scatter.  A tile is 2048 keys handled by 256 threads in 8 rounds
-// of 256 consecutive keys; inside a round, lanes with equal digits find each
+// (3) stable scatter.  A tile is 1024 keys handled by 256 threads in 4 rounds
+// of 256 consecutive keys (about 6 tiles per SM for 1e6 particles); inside a round, lanes with equal digits find each
 // other with __match_any_sync and are ranked by lane, warps are ranked by a
 // shared-memory scan, rounds by a running count -- which keeps equal keys in
 // their input order.
@@ -17,7 +17,7 @@ namespace mptrac {
 namespace {
 
 constexpr int kSortThreads = 256;
-constexpr int kRounds = 8;
+constexpr int kRounds = 4;
 constexpr int kTileKeys = kSortThreads * kRounds;
 constexpr int kRadix = 256;
 
@@ -65,16 +65,31 @@ __device__ __forceinline__ void load_key_tables(KeyTables& t, const Geo& g) {
     for (int q = threadIdx.x; q < g.nbins; q += blockDim.x) t.kguess[q] = g.kguess[q];
 }
 
+// float32 of a float64 by truncating its mantissa, with integer operations
+// only (|error| < 2^-23 |x|), where the result is a normal float32; zero and
+// anything else take the conversion instruction (on the float64 pipe, which
+// is narrow on this GPU).
+__device__ __forceinline__ float f64_to_f32_trunc(double x) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t e = (hi >> 20) & 0x7FFu;   // float64 biased exponent
+    if (e - 897u < 254u) {                     // float32 biased exponent e - 896 in [1, 254]
+        const uint32_t mag = (((hi & 0x7FFFFFFFu) - (896u << 20)) << 3) | (lo >> 29);
+        return __uint_as_float((hi & 0x80000000u) | mag);
+    }
+    return (float)x;
+}
+
 // Same key, computed in float32 when that is provably identical: the float32
-// cell coordinates are within key_mx / key_my cells (a bound derived from the
-// grid on the host, with a factor 8 to spare) and p within ~1e-7 relative of
-// the exact values, so estimates farther than that from every cell face
-// (and p farther than 1e-5 relative from its bracketing levels) have the same
-// floor / level count as the float64 definition.  Anything closer to a face, or outside the regular range, takes
-// the float64 path.
+// cell coordinates are within key_mx / key_my cells of the float64 ones (a
+// bound derived from the grid on the host, with a factor 2 to spare) and the
+// float32 differences p - plev[k] within 1.8e-7 p of the float64 ones, so
+// estimates farther than that from every cell face (and p farther than 1e-6
+// relative from its bracketing levels) have the same floor / level count as
+// the float64 definition.  Anything closer to a face, or outside the regular
+// range, takes the float64 path.
 __device__ __forceinline__ uint32_t cell_key(double lon, double lat, double p, const Geo& g,
                                              const KeyTables& t) {
-    const float lf = (float)lon, af = (float)lat, pf = (float)p;
+    const float lf = f64_to_f32_trunc(lon), af = f64_to_f32_trunc(lat), pf = f64_to_f32_trunc(p);
     const float x = (lf - g.lon0) * g.inv_dlon;
     const float y = (af - g.lat0) * g.inv_dlat;
     const float xf = floorf(x), yf = floorf(y);
@@ -96,7 +111,7 @@ __device__ __forceinline__ uint32_t cell_key(double lon, double lat, double p, c
     const bool below_top = pf > g.pmax * (1.f + 1e-5f);     // clamps to level 0
     const bool above_bot = pf < g.pmin * (1.f - 1e-5f);     // clamps to the top level
     if (!below_top && !above_bot) {
-        const float margin = 1e-5f * pc;
+        const float margin = 1e-6f * pc;
         ok = ok && (t.plev[k] - pc > margin || k == 0) && (pc - t.plev[k + 1] > margin || k == g.nz - 2);
         if (k == 0 && !(pc < t.plev[0] - margin)) ok = false;
         if (k == g.nz - 2 && !(pc > t.plev[g.nz - 1] + margin)) ok = false;
@@ -136,6 +151,15 @@ __global__ void k_grid_counts(Geo g, int64_t n, const double* lon, const double*
     }
 }
 
+// Adds the warp's valid digits to the shared histogram h: lanes with equal
+// digits (most of a warp once the particles are sorted) are counted by one
+// atomic of their lowest lane.  Called by every lane of the warp.
+__device__ __forceinline__ void hist_add(uint32_t* h, bool valid, uint32_t digit) {
+    const unsigned peers = __match_any_sync(0xffffffffu, valid ? digit : 0x100u);
+    const int lane = threadIdx.x & 31;
+    if (valid && (__ffs(peers) - 1) == lane) atomicAdd(&h[digit], (uint32_t)__popc(peers));
+}
+
 // The particle arrays (null entries are absent) and their copies in the
 // workspace: `part` is sorted in place, `copy` holds the unsorted state.
 struct Arrays {
@@ -157,7 +181,7 @@ struct KeysArgs {
     int ntiles;
 };
 
-// Cell keys (or the inactive key) of one tile of 2048 particles plus that
+// Cell keys (or the inactive key) of one tile of particles plus that
 // tile's histogram of the lowest 8-bit digit: the first radix pass needs no
 // separate histogram launch.  Every particle array is copied aside on the way.
 __global__ void __launch_bounds__(kSortThreads) k_keys_hist(const __grid_constant__ KeysArgs a) {
@@ -167,27 +191,51 @@ __global__ void __launch_bounds__(kSortThreads) k_keys_hist(const __grid_constan
     load_key_tables(tb, g);
     h[threadIdx.x] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kTileKeys;
+    const int64_t base = (int64_t)blockIdx.x * kTileKeys + threadIdx.x;
+    // every load of the thread's kRounds particles first (the copies may not be
+    // written before them: the compiler cannot tell the arrays apart)
+    double vd[kRounds][3];
+    uint32_t vu[kRounds][2];
+    float vf[kRounds][3];
+#pragma unroll
     for (int r = 0; r < kRounds; ++r) {
-        const int64_t q = base + r * kSortThreads + threadIdx.x;
+        const int64_t q = base + r * kSortThreads;
         if (q >= a.n) continue;
-        const double lon = a.part.d[0][q], lat = a.part.d[1][q], p = a.part.d[2][q];
-        a.copy.d[0][q] = lon;
-        a.copy.d[1][q] = lat;
-        a.copy.d[2][q] = p;
-        bool active = true;
-        if (a.part.u[1]) {
-            const uint32_t rr = a.part.u[1][q];
-            a.copy.u[1][q] = rr;
-            if (a.ts) active = rr < (uint32_t)a.nrel && a.t >= a.ts[rr] && a.t < a.te[rr];
-        }
-        if (a.part.u[0]) a.copy.u[0][q] = a.part.u[0][q];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) vd[r][c] = a.part.d[c][q];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) vu[r][c] = a.part.u[c] ? a.part.u[c][q] : 0u;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) vf[r][c] = a.part.f[c] ? a.part.f[c][q] : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const int64_t q = base + r * kSortThreads;
+        if (q >= a.n) continue;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) a.copy.d[c][q] = vd[r][c];
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+            if (a.part.u[c]) a.copy.u[c][q] = vu[r][c];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            if (a.part.f[c]) a.copy.f[c][q] = a.part.f[c][q];
-        const uint32_t k = active ? cell_key(lon, lat, p, g, tb) : a.inactive_key;
-        a.keys[q] = k;
-        atomicAdd(&h[k & 0xFF], 1u);
+            if (a.part.f[c]) a.copy.f[c][q] = vf[r][c];
+    }
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const int64_t q = base + r * kSortThreads;
+        const bool valid = q < a.n;
+        uint32_t k = 0;
+        if (valid) {
+            bool active = true;
+            if (a.part.u[1] && a.ts) {
+                const uint32_t rr = vu[r][1];
+                active = rr < (uint32_t)a.nrel && a.t >= a.ts[rr] && a.t < a.te[rr];
+            }
+            k = active ? cell_key(vd[r][0], vd[r][1], vd[r][2], g, tb) : a.inactive_key;
+            a.keys[q] = k;
+        }
+        hist_add(h, valid, k & 0xFF);
     }
     __syncthreads();
     a.hist[(int64_t)threadIdx.x * a.ntiles + blockIdx.x] = h[threadIdx.x];
@@ -203,7 +251,8 @@ __global__ void __launch_bounds__(kSortThreads) k_hist(const uint32_t* __restric
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
         const int64_t q = base + r * kSortThreads + threadIdx.x;
-        if (q < n) atomicAdd(&h[(keys[q] >> shift) & 0xFF], 1u);
+        const bool valid = q < n;
+        hist_add(h, valid, valid ? (keys[q] >> shift) & 0xFF : 0u);
     }
     __syncthreads();
     hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
@@ -242,8 +291,8 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_rows(uint32_t* hist, int 
     if (threadIdx.x == 0) tot[blockIdx.x] = carry;
 }
 
-// Stable scatter of one tile (2048 keys) for one 8-bit digit.  Warp w owns the
-// tile's keys [256 w, 256 w + 256) and walks them in 8 rounds of 32
+// Stable scatter of one tile (kTileKeys keys) for one 8-bit digit.  Warp w owns
+// the tile's keys [32 kRounds w, 32 kRounds (w + 1)) and walks them in kRounds rounds of 32
 // consecutive keys: lanes with equal digits find each other with
 // __match_any_sync and take ranks from a warp-private running count in shared
 // memory.  Scans over warps and over digits then give every key its place in
@@ -341,21 +390,44 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint32_t* __rest
     __syncthreads();
     const int64_t left = n - tile0;
     const int cnt = left < kTileKeys ? (int)left : kTileKeys;
-    for (int e = tid; e < cnt; e += kSortThreads) {
-        const uint32_t k = s_key[e];
-        const uint32_t d = (k >> shift) & 0xFF;
-        const uint32_t pos = s_base[d] + (uint32_t)e - s_tp[d];
-        if (FINAL) {
+    if (FINAL) {
+        // gather every value of the thread's kRounds places first, then store
+        // (the particle arrays and their copies cannot be told apart by the compiler)
+        double vd[kRounds][3];
+        uint32_t vu[kRounds][2];
+        float vf[kRounds][3];
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+            const int e = tid + r * kSortThreads;
+            if (e >= cnt) continue;
             const uint32_t src = s_val[e];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) part.d[c][pos] = copy.d[c][src];
+            for (int c = 0; c < 3; ++c) vd[r][c] = copy.d[c][src];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) vu[r][c] = part.u[c] ? copy.u[c][src] : 0u;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) vf[r][c] = part.f[c] ? copy.f[c][src] : 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+            const int e = tid + r * kSortThreads;
+            if (e >= cnt) continue;
+            const uint32_t d = (s_key[e] >> shift) & 0xFF;
+            const uint32_t pos = s_base[d] + (uint32_t)e - s_tp[d];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) part.d[c][pos] = vd[r][c];
 #pragma unroll
             for (int c = 0; c < 2; ++c)
-                if (part.u[c]) part.u[c][pos] = copy.u[c][src];
+                if (part.u[c]) part.u[c][pos] = vu[r][c];
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                if (part.f[c]) part.f[c][pos] = copy.f[c][src];
-        } else {
+                if (part.f[c]) part.f[c][pos] = vf[r][c];
+        }
+    } else {
+        for (int e = tid; e < cnt; e += kSortThreads) {
+            const uint32_t k = s_key[e];
+            const uint32_t d = (k >> shift) & 0xFF;
+            const uint32_t pos = s_base[d] + (uint32_t)e - s_tp[d];
             kout[pos] = k;
             vout[pos] = s_val[e];
         }
