@@ -39,7 +39,7 @@ SEED_RNG = 2
 # DRAM bytes (read + write) of one fused-step launch of this workload, from an
 # ncu capture of the full-size launch (see profiles/); None when the kernel has
 # changed since the counters were taken.
-TRAFFIC_PER_LAUNCH = 192901376   # 169.1 MB read + 23.8 MB written (ncu, autotuned variant)
+TRAFFIC_PER_LAUNCH = 193503488   # 169.1 MB read + 24.4 MB written (ncu, autotuned variant 2)
 METRIC = "particle-steps/s on 1 GB300 (advect+diffuse) and % gather roofline, surrogate vs plain"
 WORKLOAD = ("1deg 360x181x60 Fourier-mode wind, 4 snapshots 6h apart, 1e6 particles, dt=180s, 24h "
             "(480 fused advect+turb+meso steps), sort by met cell every 20 steps")

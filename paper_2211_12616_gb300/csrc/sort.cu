@@ -152,8 +152,10 @@ __global__ void k_grid_counts(Geo g, int64_t n, const double* lon, const double*
 }
 
 // Adds the warp's valid digits to the shared histogram h: lanes with equal
-// digits (most of a warp once the particles are sorted) are counted by one
-// atomic of their lowest lane.  Called by every lane of the warp.
+// digits (most of a warp of cell keys once the particles are sorted) are
+// counted by one atomic of their lowest lane.  Called by every lane of the
+// warp.  (After the first pass equal digits are rare within a warp, and the
+// plain atomics of k_hist are cheaper.)
 __device__ __forceinline__ void hist_add(uint32_t* h, bool valid, uint32_t digit) {
     const unsigned peers = __match_any_sync(0xffffffffu, valid ? digit : 0x100u);
     const int lane = threadIdx.x & 31;
@@ -251,8 +253,7 @@ __global__ void __launch_bounds__(kSortThreads) k_hist(const uint32_t* __restric
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
         const int64_t q = base + r * kSortThreads + threadIdx.x;
-        const bool valid = q < n;
-        hist_add(h, valid, valid ? (keys[q] >> shift) & 0xFF : 0u);
+        if (q < n) atomicAdd(&h[(keys[q] >> shift) & 0xFF], 1u);
     }
     __syncthreads();
     hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
