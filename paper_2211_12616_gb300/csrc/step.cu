@@ -139,6 +139,15 @@ __device__ __forceinline__ void position_bc(ff& lon, ff& d, ff& p, const Geo& g)
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11) and Box-Muller normals
 // ---------------------------------------------------------------------------
+// 32 x 32 -> 64-bit product as one instruction (both halves of the round's
+// multiplications from a single multiply)
+__device__ __forceinline__ void mul_wide(uint32_t a, uint32_t b, uint32_t& hi, uint32_t& lo) {
+    unsigned long long p;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(b));
+    hi = (uint32_t)(p >> 32);
+    lo = (uint32_t)p;
+}
+
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
@@ -146,8 +155,9 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
             k0 += 0x9E3779B9u;
             k1 += 0xBB67AE85u;
         }
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        uint32_t hi0, lo0, hi1, lo1;
+        mul_wide(0xD2511F53u, c.x, hi0, lo0);
+        mul_wide(0xCD9E8D57u, c.z, hi1, lo1);
         c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
     }
     return c;
@@ -165,8 +175,9 @@ __device__ __forceinline__ float u23(uint32_t x) {
 __device__ __forceinline__ uint4 philox4x32_10_ks(uint4 c, const uint32_t* ks) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        uint32_t hi0, lo0, hi1, lo1;
+        mul_wide(0xD2511F53u, c.x, hi0, lo0);
+        mul_wide(0xCD9E8D57u, c.z, hi1, lo1);
         c = make_uint4(hi1 ^ c.y ^ ks[2 * r], lo1, hi0 ^ c.w ^ ks[2 * r + 1], lo0);
     }
     return c;
