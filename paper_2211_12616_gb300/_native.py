@@ -189,6 +189,10 @@ class Particles:
     def clone(self) -> "Particles":
         return Particles(*[None if getattr(self, k) is None else getattr(self, k).clone() for k in self.FIELDS])
 
+    def view(self, a: int, b: int) -> "Particles":
+        """Particles [a, b) as views of the same device memory."""
+        return Particles(*[None if getattr(self, k) is None else getattr(self, k)[a:b] for k in self.FIELDS])
+
     def copy_(self, other: "Particles"):
         for k in self.FIELDS:
             a, b = getattr(self, k), getattr(other, k)

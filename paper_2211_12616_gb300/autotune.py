@@ -21,9 +21,11 @@ PERSISTENT = (False, True)
 SORT_EVERY = (10, 20, 40, 120)
 
 
-def candidates(variants=VARIANTS, persistent=PERSISTENT, sort_every=SORT_EVERY):
-    return [{"variant": v, "persistent": p, "sort_every": s}
-            for v, p, s in itertools.product(variants, persistent, sort_every)]
+def candidates(variants=VARIANTS, persistent=PERSISTENT, sort_every=SORT_EVERY, groups=(1,)):
+    """Schedules to try; ``groups`` is the number of particle groups on streams of their own
+    (used by runs that support it)."""
+    return [{"variant": v, "persistent": p, "sort_every": s, "groups": g}
+            for v, p, s, g in itertools.product(variants, persistent, sort_every, groups)]
 
 
 def _time(fn, reset, stream, repeats):

@@ -7,7 +7,15 @@ particles then advance in blocks of ``sort_every`` fused steps (advection,
 turbulent and mesoscale diffusion, position rules), and are sorted by met cell
 before every block so that each block starts with cell-ordered particles.
 
-All work is enqueued on one CUDA stream; this module only sequences ABI calls.
+With ``groups`` = G > 1 the particles are split into G contiguous groups, each
+sorted and stepped on a stream of its own: a group's sort and the last,
+partly filled wave of its step kernel then overlap with the other groups'
+steps.  A particle's trajectory does not depend on the other particles or on
+their order (counter-based random numbers keyed by particle id), so the
+results are those of G = 1 up to the order of the particles in memory.
+The groups join before every met load, which overwrites a slot they read.
+
+This module only sequences ABI calls.
 """
 from __future__ import annotations
 
@@ -20,14 +28,27 @@ from ._native import Context, DiffParams, Particles
 
 class Simulation:
     def __init__(self, ctx: Context, snapshot_at, dt_met: float, particles: Particles, dt: float,
-                 prm: DiffParams, seed: int, sort_every: int = 20, sort: bool = True):
+                 prm: DiffParams, seed: int, sort_every: int = 20, sort: bool = True, groups: int = 1):
         """``snapshot_at(t)`` returns (u, v, w) device tensors of the snapshot at time t."""
         self.ctx, self.snapshot_at, self.dt_met = ctx, snapshot_at, float(dt_met)
         self.parts, self.dt, self.prm, self.seed = particles, float(dt), prm, int(seed)
         self.sort_every, self.do_sort = int(sort_every), bool(sort)
-        self.workspace = torch.empty(ctx.sort_workspace_bytes(particles.n), dtype=torch.uint8,
-                                     device=particles.lon.device) if sort else None
+        n, g = particles.n, max(1, min(int(groups), max(particles.n, 1)))
+        bounds = [round(q * n / g) for q in range(g + 1)]
+        self.groups = [particles.view(bounds[q], bounds[q + 1]) for q in range(g)] if g > 1 else [particles]
+        dev = particles.lon.device
+        self.workspaces = [torch.empty(ctx.sort_workspace_bytes(v.n), dtype=torch.uint8, device=dev)
+                           for v in self.groups] if sort else [None] * g
+        self.workspace = self.workspaces[0]
+        self._streams = None
         self.step_hook = None     # called around every mptrac_step: hook(stage, stream)
+
+    def _group_streams(self, main):
+        if len(self.groups) == 1:
+            return [main]
+        if self._streams is None:
+            self._streams = [torch.cuda.Stream(device=self.parts.lon.device) for _ in self.groups]
+        return self._streams
 
     def run(self, t_start: float, t_end: float, stream=None) -> int:
         """Advances from t_start to t_end; returns the number of steps taken.
@@ -40,30 +61,42 @@ class Simulation:
             raise ValueError("the met interval must be a whole number of steps")
         n_iv = int(round((t_end - t_start) / self.dt_met))
         ctx, slots = self.ctx, {}
+        main = stream if stream is not None else torch.cuda.current_stream(self.parts.lon.device)
+        gstreams = self._group_streams(main)
         step = 0
         for iv in range(n_iv):
             ta = t_start + iv * self.dt_met
             tb = ta + self.dt_met
+            for gs in gstreams:          # the groups finish with the slots before they change
+                if gs is not main:
+                    main.wait_stream(gs)
             for t, keep in ((ta, tb), (tb, ta)):
                 if t in slots.values():
                     continue
                 free = [q for q in (0, 1) if q not in slots]
                 slot = free[0] if free else (0 if slots[0] != keep else 1)
-                ctx.load_met(slot, t, *self.snapshot_at(t), stream=stream)
+                ctx.load_met(slot, t, *self.snapshot_at(t), stream=main)
                 slots[slot] = t
+            for gs in gstreams:
+                if gs is not main:
+                    gs.wait_stream(main)
             done = 0
             while done < steps_per_iv:
                 cnt = min(self.sort_every, steps_per_iv - done)
-                if self.do_sort:
-                    ctx.sort(self.parts, self.workspace, stream=stream)
                 t = ta + done * self.dt
-                if self.step_hook:
-                    self.step_hook("begin", stream)
-                ctx.step(self.parts, t, self.dt, self.prm, self.seed, step, cnt, stream=stream)
-                if self.step_hook:
-                    self.step_hook("end", stream)
+                for parts, ws, gs in zip(self.groups, self.workspaces, gstreams):
+                    if self.do_sort:
+                        ctx.sort(parts, ws, stream=gs)
+                    if self.step_hook:
+                        self.step_hook("begin", gs)
+                    ctx.step(parts, t, self.dt, self.prm, self.seed, step, cnt, stream=gs)
+                    if self.step_hook:
+                        self.step_hook("end", gs)
                 done += cnt
                 step += cnt
+        for gs in gstreams:
+            if gs is not main:
+                main.wait_stream(gs)
         return step
 
 
