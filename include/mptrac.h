@@ -122,7 +122,9 @@ typedef struct {
     int turb, meso;
 } mptrac_diff_params;
 
-/* Creates a context for grid `g`: allocates two device met slots and the
+/* Creates a context for grid `g`: allocates two device met slots, their
+ * interleaved copy (both slots' values of a grid point in one record, the
+ * layout the particle kernels gather from; as large as the two slots) and the
  * level tables on the current CUDA device.  On success *out owns them until
  * mptrac_destroy.  Errors: E_INVALID_ARG (bad grid), E_OOM, E_CUDA. */
 int mptrac_init_grid(mptrac_ctx** out, const mptrac_grid_desc* g);
@@ -141,7 +143,8 @@ const char* mptrac_last_error(const mptrac_ctx* ctx);
  * stay valid until the stream has passed this call).  The slot is rewritten
  * as records [lat][lon][level] x (u, v, omega, T) in the grid's storage
  * precision; reduced precision uses per-(level, variable) power-of-two scales
- * 2^(E-15), maxabs = m 2^E, m in [0.5, 1).  The two loaded slots must have
+ * 2^(E-15), maxabs = m 2^E, m in [0.5, 1).  The same values are written to
+ * this slot's lane of the interleaved copy.  The two loaded slots must have
  * different times; the earlier one is the interval start.
  * Errors: E_INVALID_ARG, E_NOT_INIT, E_CUDA. */
 int mptrac_load_met(mptrac_ctx* ctx, int slot, double t,

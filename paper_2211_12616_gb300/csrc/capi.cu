@@ -26,6 +26,7 @@ struct mptrac_ctx {
     int16_t* d_kguess = nullptr;
     double* d_plev_d = nullptr;
     void* d_met[2] = {nullptr, nullptr};
+    void* d_pair = nullptr;            // both slots interleaved (lane = slot), read by the particle kernels
     float* d_scales[2] = {nullptr, nullptr};
     double t_slot[2] = {0.0, 0.0};
     bool loaded[2] = {false, false};
@@ -86,7 +87,7 @@ constexpr double kPi = 3.14159265358979323846;
 
 void free_ctx(mptrac_ctx* c) {
     void* ptrs[] = {c->d_plev, c->d_invdp, c->d_kguess, c->d_plev_d, c->d_met[0], c->d_met[1],
-                    c->d_scales[0], c->d_scales[1], c->d_staging, c->d_rel_ts, c->d_rel_te,
+                    c->d_pair, c->d_scales[0], c->d_scales[1], c->d_staging, c->d_rel_ts, c->d_rel_te,
                     c->d_win};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -126,6 +127,14 @@ int ordered_slots(const mptrac_ctx* c, int& a, int& b) {
     return MPTRAC_OK;
 }
 
+// Time weights of the pair lanes (slot 0, slot 1) for the time fraction w
+// between the earlier snapshot (slot s_early) and the later one.
+void lane_weights(int s_early, double w, float& lane0, float& lane1) {
+    const float early = (float)(1.0 - w), late = (float)w;
+    lane0 = s_early == 0 ? early : late;
+    lane1 = s_early == 0 ? late : early;
+}
+
 int run_transport(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
                   const mptrac_diff_params* prm, uint64_t seed, uint64_t step0, int nsteps,
                   uintptr_t stream, int mode, const uint8_t* mask = nullptr) {
@@ -160,8 +169,7 @@ int run_transport(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
     StepArgs a;
     memset(&a, 0, sizeof(a));
     a.geo = c->geo;
-    a.m0 = MetView{c->d_met[s0], c->d_scales[s0]};
-    a.m1 = MetView{c->d_met[s1], c->d_scales[s1]};
+    a.mp = MetPair{c->d_pair, {c->d_scales[0], c->d_scales[1]}};
     a.n = P->n;
     a.lon = P->lon;
     a.lat = P->lat;
@@ -208,8 +216,8 @@ int run_transport(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
         a.step0 = step0 + (uint64_t)n0;
         for (int q = 0; q < cnt; ++q) {
             const double tn = t + (double)(n0 + q) * dt;
-            a.wt[2 * q] = (float)((tn - t0) / (t1 - t0));
-            a.wt[2 * q + 1] = (float)((tn + 0.5 * dt - t0) / (t1 - t0));
+            lane_weights(s0, (tn - t0) / (t1 - t0), a.wt[4 * q], a.wt[4 * q + 1]);
+            lane_weights(s0, (tn + 0.5 * dt - t0) / (t1 - t0), a.wt[4 * q + 2], a.wt[4 * q + 3]);
         }
         if (use_win) MPTRAC_CUDA(launch_windows(c->d_rel_ts, c->d_rel_te, c->n_rel, t, dt, n0, cnt, c->d_win, st));
         MPTRAC_CUDA(launch_transport(c->storage, mode, a, grid, c->launch_variant, c->persistent, st));
@@ -298,6 +306,7 @@ int mptrac_init_grid(mptrac_ctx** out, const mptrac_grid_desc* g) {
         rc = alloc(&c->d_met[s], c->rec_bytes);
         if (!rc) rc = alloc((void**)&c->d_scales[s], 4 * nz * sizeof(float));
     }
+    if (!rc) rc = alloc(&c->d_pair, 2 * c->rec_bytes);
     if (rc) {
         free_ctx(c);
         return rc;
@@ -392,7 +401,7 @@ int mptrac_load_met(mptrac_ctx* c, int slot, double t, const float* u, const flo
         }
     }
     MPTRAC_CUDA(launch_pack(c->storage, c->nvars, src[0], src[1], src[2], src[3], c->nx, c->ny, c->nz,
-                            c->d_met[slot], c->d_scales[slot], st));
+                            c->d_met[slot], c->d_scales[slot], c->d_pair, slot, st));
     c->t_slot[slot] = t;
     c->loaded[slot] = true;
     return ok();
@@ -506,10 +515,10 @@ int mptrac_interp(mptrac_ctx* c, int64_t n, const double* lon, const double* lat
     if (ovar && !device_accessible(ovar)) return fail(MPTRAC_E_INVALID_ARG, "out_var is not device memory");
     const double t0 = c->t_slot[s0], t1 = c->t_slot[s1];
     if (!(t >= t0 && t <= t1)) return fail(MPTRAC_E_TIME_RANGE, "t = %g outside [%g, %g]", t, t0, t1);
-    const float w = (float)((t - t0) / (t1 - t0));
-    MPTRAC_CUDA(launch_interp(c->storage, c->geo, MetView{c->d_met[s0], c->d_scales[s0]},
-                              MetView{c->d_met[s1], c->d_scales[s1]}, w, n, lon, lat, p, ou, ov, ow,
-                              ovar, reinterpret_cast<cudaStream_t>(stream)));
+    float wl0, wl1;
+    lane_weights(s0, (t - t0) / (t1 - t0), wl0, wl1);
+    MPTRAC_CUDA(launch_interp(c->storage, c->geo, MetPair{c->d_pair, {c->d_scales[0], c->d_scales[1]}}, wl0,
+                              wl1, n, lon, lat, p, ou, ov, ow, ovar, reinterpret_cast<cudaStream_t>(stream)));
     return ok();
 }
 

@@ -43,10 +43,20 @@ struct MetView {
     const float* scales;
 };
 
+// Both slots interleaved, the layout the particle kernels gather from: per grid
+// point ([lat][lon][level]) the pairs (slot 0, slot 1) of u, v, omega, T --
+// 8 float32 (32 B) or 8 16-bit codes (16 B) -- so that one load brings a
+// corner's values on both snapshots, already paired.  Lane s is written when
+// slot s is loaded; scales[s] are slot s's scales (16-bit storage).
+struct MetPair {
+    const void* rec;
+    const float* scales[2];
+};
+
 // Arguments of the particle kernels (advect / diffuse / step).
 struct StepArgs {
     Geo geo;
-    MetView m0, m1;               // m0 = earlier snapshot
+    MetPair mp;                   // both snapshots, interleaved (lane = slot)
     int64_t n;
     double* lon;
     double* lat;
@@ -68,7 +78,9 @@ struct StepArgs {
     uint32_t key0, key1;          // Philox key = seed
     uint32_t ks[20];              // Philox key schedule: round r uses (ks[2r], ks[2r+1])
     uint64_t step0;
-    float wt[2 * kMaxStepsPerLaunch];   // time weights at t_n and t_n + dt/2
+    // time weights of lanes (slot 0, slot 1) at t_n and at t_n + dt/2: step q uses
+    // wt[4q], wt[4q + 1] and wt[4q + 2], wt[4q + 3]
+    float wt[4 * kMaxStepsPerLaunch];
 };
 
 // MODE_STEP_FULL is MODE_STEP with both diffusion parts on, resolved at compile
@@ -83,7 +95,7 @@ cudaError_t launch_transport(int storage, int mode, const StepArgs& a, int grid,
                              bool persistent, cudaStream_t s);
 cudaError_t launch_windows(const double* ts, const double* te, int nrel, double t, double dt,
                            int n_begin, int nsteps, int2* out, cudaStream_t s);
-cudaError_t launch_interp(int storage, const Geo& g, MetView m0, MetView m1, float w, int64_t n,
+cudaError_t launch_interp(int storage, const Geo& g, MetPair mp, float w_lane0, float w_lane1, int64_t n,
                           const double* lon, const double* lat, const double* p, float* ou,
                           float* ov, float* ow, float* ovar, cudaStream_t s);
 cudaError_t launch_sample(int storage, const Geo& g, MetView m0, MetView m1, float w, int64_t n,
@@ -96,9 +108,11 @@ cudaError_t launch_grid_counts(const Geo& g, int64_t n, const double* lon, const
 cudaError_t launch_philox(const uint32_t* ctr, int64_t n, uint32_t k0, uint32_t k1, uint32_t* out,
                           float* normals, cudaStream_t s);
 
+// Packs one snapshot into slot records `rec` (+ scales) and into lane `slot`
+// of the interleaved pair records `pairs`.
 cudaError_t launch_pack(int storage, int nvars, const float* u, const float* v, const float* w,
-                        const float* T, int nx, int ny, int nz, void* rec, float* scales,
-                        cudaStream_t s);
+                        const float* T, int nx, int ny, int nz, void* rec, float* scales, void* pairs,
+                        int slot, cudaStream_t s);
 
 size_t sort_workspace_bytes(int64_t n);
 cudaError_t launch_cell_keys(const Geo& g, int64_t n, const double* lon, const double* lat,

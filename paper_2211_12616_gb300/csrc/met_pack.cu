@@ -9,7 +9,8 @@
 //
 // The transpose goes through shared memory in tiles of 32 longitudes x 32
 // levels: reads are 128-byte rows of one level, writes are runs of 32
-// consecutive records.
+// consecutive records.  The same values go to lane `slot` of the interleaved
+// pair records that the particle kernels read (both slots per grid point).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -61,7 +62,7 @@ template <int ST>
 __global__ void __launch_bounds__(256) k_pack(const float* __restrict__ u, const float* __restrict__ v,
                                               const float* __restrict__ w, const float* __restrict__ T,
                                               int nx, int ny, int nz, void* recv,
-                                              const float* __restrict__ scales) {
+                                              const float* __restrict__ scales, void* pairs, int slot) {
     __shared__ float tile[4][kTile][kTile + 1];   // [var][level][lon]
     const int i0 = blockIdx.x * kTile, j = blockIdx.y, k0 = blockIdx.z * kTile;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -91,10 +92,17 @@ __global__ void __launch_bounds__(256) k_pack(const float* __restrict__ u, const
         if (ST == MPTRAC_FP32) {
             static_cast<float4*>(recv)[r] =
                 make_float4(tile[0][kl][il], tile[1][kl][il], tile[2][kl][il], tile[3][kl][il]);
+            float* pr = static_cast<float*>(pairs) + r * 8 + slot;
+#pragma unroll
+            for (int var = 0; var < 4; ++var) pr[2 * var] = tile[var][kl][il];
         } else {
-            const uint32_t a = code16(tile[0][kl][il], ST) | (code16(tile[1][kl][il], ST) << 16);
-            const uint32_t b = code16(tile[2][kl][il], ST) | (code16(tile[3][kl][il], ST) << 16);
-            static_cast<uint2*>(recv)[r] = make_uint2(a, b);
+            uint32_t c[4];
+#pragma unroll
+            for (int var = 0; var < 4; ++var) c[var] = code16(tile[var][kl][il], ST);
+            static_cast<uint2*>(recv)[r] = make_uint2(c[0] | (c[1] << 16), c[2] | (c[3] << 16));
+            unsigned short* pr = static_cast<unsigned short*>(pairs) + r * 8 + slot;
+#pragma unroll
+            for (int var = 0; var < 4; ++var) pr[2 * var] = (unsigned short)c[var];
         }
     }
 }
@@ -107,8 +115,8 @@ __global__ void k_fill(float* p, int n, float v) {
 }  // namespace
 
 cudaError_t launch_pack(int storage, int nvars, const float* u, const float* v, const float* w,
-                        const float* T, int nx, int ny, int nz, void* rec, float* scales,
-                        cudaStream_t s) {
+                        const float* T, int nx, int ny, int nz, void* rec, float* scales, void* pairs,
+                        int slot, cudaStream_t s) {
     if (nvars < 4) T = nullptr;
     const int64_t plane = (int64_t)nx * ny;
     note_launches(2);
@@ -121,9 +129,9 @@ cudaError_t launch_pack(int storage, int nvars, const float* u, const float* v, 
     if (e != cudaSuccess) return e;
     const dim3 grid((nx + kTile - 1) / kTile, ny, (nz + kTile - 1) / kTile), block(kTile, 8);
     switch (storage) {
-        case MPTRAC_FP32: k_pack<MPTRAC_FP32><<<grid, block, 0, s>>>(u, v, w, T, nx, ny, nz, rec, scales); break;
-        case MPTRAC_BF16: k_pack<MPTRAC_BF16><<<grid, block, 0, s>>>(u, v, w, T, nx, ny, nz, rec, scales); break;
-        default: k_pack<MPTRAC_FP16><<<grid, block, 0, s>>>(u, v, w, T, nx, ny, nz, rec, scales); break;
+        case MPTRAC_FP32: k_pack<MPTRAC_FP32><<<grid, block, 0, s>>>(u, v, w, T, nx, ny, nz, rec, scales, pairs, slot); break;
+        case MPTRAC_BF16: k_pack<MPTRAC_BF16><<<grid, block, 0, s>>>(u, v, w, T, nx, ny, nz, rec, scales, pairs, slot); break;
+        default: k_pack<MPTRAC_FP16><<<grid, block, 0, s>>>(u, v, w, T, nx, ny, nz, rec, scales, pairs, slot); break;
     }
     return cudaGetLastError();
 }

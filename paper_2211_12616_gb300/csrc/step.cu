@@ -217,7 +217,7 @@ struct SmemT {
     float plev[kMaxNZ];
     float inv_dp[kMaxNZ];
     int16_t kguess[kGuessBins];
-    float sc[2][3][NSC];   // scales of u, v, omega for slot 0 / 1
+    float2 sc[3][NSC];     // scales of u, v, omega per level as pairs (slot 0, slot 1)
 };
 using Smem = SmemT<kMaxNZ>;
 template <int ST> using SmemFor = SmemT<ST == MPTRAC_FP32 ? 1 : kMaxNZ>;
@@ -378,40 +378,59 @@ struct SmemCache {
     }
 };
 
+// One interleaved pair record: (u, v, omega, T) x (slot 0, slot 1).
+template <int ST> struct PairRecT;
+template <> struct PairRecT<MPTRAC_FP32> { static constexpr int kBytes = 32; };
+template <> struct PairRecT<MPTRAC_BF16> { static constexpr int kBytes = 16; };
+template <> struct PairRecT<MPTRAC_FP16> { static constexpr int kBytes = 16; };
+
+// float32 pair record -> u, v, omega pairs, straight from one 32-byte load
+__device__ __forceinline__ void load_pair32(const void* p, f2_t& u, f2_t& v, f2_t& w) {
+    f2_t t;
+    asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];" : "=l"(u), "=l"(v), "=l"(w), "=l"(t) : "l"(p));
+}
+
+// a word of two 16-bit codes (slot 0 low, slot 1 high) -> pair of floats
+template <int ST>
+__device__ __forceinline__ f2_t decode_pair16(uint32_t x) {
+    if (ST == MPTRAC_BF16) return f2_pack(__uint_as_float(x << 16), __uint_as_float(x & 0xFFFF0000u));
+    return f2_pack(__half2float(__ushort_as_half((unsigned short)(x & 0xFFFFu))),
+                   __half2float(__ushort_as_half((unsigned short)(x >> 16))));
+}
+
 template <int ST, class S, class C>
-__device__ __forceinline__ void fetch_corners(const MetView& m0, const MetView& m1, const S& s,
-                                              const Geo& g, const Cell& c, int col, C& cc) {
-    using R = typename RecT<ST>::T;
+__device__ __forceinline__ void fetch_corners(const MetPair& mp, const S& s, const Geo& g, const Cell& c,
+                                              int col, C& cc) {
     const int i1 = (c.i + 1 == g.nx) ? 0 : c.i + 1;
     const int row1 = col - c.i + g.nx;
     const int base[4] = {col * g.nz + c.k, (col - c.i + i1) * g.nz + c.k, (row1 + c.i) * g.nz + c.k,
                          (row1 + i1) * g.nz + c.k};
-    const R* rec0 = static_cast<const R*>(m0.rec);
-    const R* rec1 = static_cast<const R*>(m1.rec);
+    const char* rec = static_cast<const char*>(mp.rec);
+    constexpr int RB = PairRecT<ST>::kBytes;
     constexpr int QG = 8 / C::kGroups;   // corners per group
 #pragma unroll 1
     for (int gi = 0; gi < C::kGroups; ++gi) {
-        R r[2][QG];
-#pragma unroll
-        for (int qq = 0; qq < QG; ++qq) {
-            const int q = gi * QG + qq;
-            r[0][qq] = ldg_rec(rec0 + base[q & 3] + (q >> 2));
-            r[1][qq] = ldg_rec(rec1 + base[q & 3] + (q >> 2));
-        }
         f2_t U[QG], V[QG], W[QG];
+        if (ST == MPTRAC_FP32) {
 #pragma unroll
-        for (int qq = 0; qq < QG; ++qq) {
-            const int q = gi * QG + qq;
-            float4 a = decode<ST>(r[0][qq]);
-            float4 b = decode<ST>(r[1][qq]);
-            if (ST != MPTRAC_FP32) {
-                const int k = c.k + (q >> 2);
-                a.x *= s.sc[0][0][k]; a.y *= s.sc[0][1][k]; a.z *= s.sc[0][2][k];
-                b.x *= s.sc[1][0][k]; b.y *= s.sc[1][1][k]; b.z *= s.sc[1][2][k];
+            for (int qq = 0; qq < QG; ++qq) {
+                const int q = gi * QG + qq;
+                load_pair32(rec + (size_t)(base[q & 3] + (q >> 2)) * RB, U[qq], V[qq], W[qq]);
             }
-            U[qq] = f2_pack(a.x, b.x);
-            V[qq] = f2_pack(a.y, b.y);
-            W[qq] = f2_pack(a.z, b.z);
+        } else {
+            uint4 r[QG];
+#pragma unroll
+            for (int qq = 0; qq < QG; ++qq) {
+                const int q = gi * QG + qq;
+                r[qq] = __ldg(reinterpret_cast<const uint4*>(rec + (size_t)(base[q & 3] + (q >> 2)) * RB));
+            }
+#pragma unroll
+            for (int qq = 0; qq < QG; ++qq) {
+                const int k = c.k + ((gi * QG + qq) >> 2);
+                U[qq] = f2_mul(decode_pair16<ST>(r[qq].x), *reinterpret_cast<const f2_t*>(&s.sc[0][k]));
+                V[qq] = f2_mul(decode_pair16<ST>(r[qq].y), *reinterpret_cast<const f2_t*>(&s.sc[1][k]));
+                W[qq] = f2_mul(decode_pair16<ST>(r[qq].z), *reinterpret_cast<const f2_t*>(&s.sc[2][k]));
+            }
         }
         cc.store(gi, U, V, W);
     }
@@ -454,20 +473,21 @@ __device__ __forceinline__ f2_t weighted_var(const f2_t* x, const Weights8& W, f
     return acc;
 }
 
-__device__ __forceinline__ float tlerp(f2_t ab, float w) {
+// linear interpolation in time of a (slot 0, slot 1) pair with the lane
+// weights (wl, wh): 1 - w for the earlier snapshot's lane, w for the later's
+__device__ __forceinline__ float tlerp(f2_t ab, float wl, float wh) {
     float a, b;
     f2_split(ab, a, b);
-    return fmaf(w, b - a, a);
+    return fmaf(wh, b, wl * a);
 }
 
-// Wind at a located point and time weight w (0 -> m0, 1 -> m1), with the
-// subgrid variances when SIG.
+// Wind at a located point and lane time weights (wl, wh), with the subgrid
+// variances when SIG.
 template <int ST, bool SIG, class S, class C>
-__device__ __forceinline__ void eval_wind(const MetView& m0, const MetView& m1, const S& s,
-                                          const Geo& g, const Cell& c, float w, C& cc,
-                                          Wind& out, Wind& var) {
+__device__ __forceinline__ void eval_wind(const MetPair& mp, const S& s, const Geo& g, const Cell& c,
+                                          float wl, float wh, C& cc, Wind& out, Wind& var) {
     const int col = c.j * g.nx + c.i;
-    if (col != cc.col || c.k != cc.k) fetch_corners<ST>(m0, m1, s, g, c, col, cc);
+    if (col != cc.col || c.k != cc.k) fetch_corners<ST>(mp, s, g, c, col, cc);
     const Weights8 W = weights8(c);
     float o[3], sg[3];
 #pragma unroll
@@ -475,16 +495,17 @@ __device__ __forceinline__ void eval_wind(const MetView& m0, const MetView& m1, 
         f2_t x[8];
         cc.get(v, x);
         const f2_t t = trilinear(x, W);
-        o[v] = tlerp(t, w);
-        if (SIG) sg[v] = tlerp(weighted_var(x, W, t), w);
+        o[v] = tlerp(t, wl, wh);
+        if (SIG) sg[v] = tlerp(weighted_var(x, W, t), wl, wh);
     }
     out = Wind{o[0], o[1], o[2]};
     if (SIG) var = Wind{sg[0], sg[1], sg[2]};
 }
 
+// sc0 / sc1: scales of slot 0 / 1 (read only when `scales`)
 template <int NSC>
-__device__ __forceinline__ void load_tables(SmemT<NSC>& s, const Geo& g, const MetView& m0,
-                                            const MetView& m1, bool scales) {
+__device__ __forceinline__ void load_tables(SmemT<NSC>& s, const Geo& g, const float* sc0, const float* sc1,
+                                            bool scales) {
     for (int q = threadIdx.x; q < g.nz; q += blockDim.x) {
         s.plev[q] = g.plev[q];
         s.inv_dp[q] = g.inv_dp[q];
@@ -493,8 +514,7 @@ __device__ __forceinline__ void load_tables(SmemT<NSC>& s, const Geo& g, const M
     if (NSC > 1 && scales) {
         for (int q = threadIdx.x; q < 3 * g.nz; q += blockDim.x) {
             const int var = q / g.nz, k = q - var * g.nz;
-            s.sc[0][var][k] = m0.scales[var * g.nz + k];
-            s.sc[1][var][k] = m1.scales[var * g.nz + k];
+            s.sc[var][k] = make_float2(sc0[var * g.nz + k], sc1[var * g.nz + k]);
         }
     }
     __syncthreads();
@@ -563,7 +583,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
     __shared__ SmemFor<ST> s;
     __shared__ ulonglong2 s_cc[CACHE ? 12 * BLOCK : 1];
     using Cache = typename std::conditional<CACHE != 0, SmemCache<BLOCK>, RegCache>::type;
-    load_tables(s, a.geo, a.m0, a.m1, ST != MPTRAC_FP32);
+    load_tables(s, a.geo, a.mp.scales[0], a.mp.scales[1], ST != MPTRAC_FP32);
     const Geo& g = a.geo;
     constexpr bool FULL = (MODE == MODE_STEP_FULL);
     constexpr bool ADVECT = (MODE != MODE_DIFFUSE);
@@ -617,13 +637,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
             Wind var{0.f, 0.f, 0.f};
             if (ADVECT) {
                 // ---- module_advection: explicit midpoint ----
-                const float w0 = a.wt[2 * sidx], wm = a.wt[2 * sidx + 1];
+                const float wl0 = a.wt[4 * sidx], wh0 = a.wt[4 * sidx + 1];
+                const float wlm = a.wt[4 * sidx + 2], whm = a.wt[4 * sidx + 3];
                 const Cell c1 = locate(lon.hi, d, p.hi, g, s, cc.k);
                 Wind V;
                 if (MODE != MODE_ADVECT && use_meso)
-                    eval_wind<ST, true>(a.m0, a.m1, s, g, c1, w0, cc, V, var);
+                    eval_wind<ST, true>(a.mp, s, g, c1, wl0, wh0, cc, V, var);
                 else
-                    eval_wind<ST, false>(a.m0, a.m1, s, g, c1, w0, cc, V, var);
+                    eval_wind<ST, false>(a.mp, s, g, c1, wl0, wh0, cc, V, var);
                 const float cl = coslat(d, 0.f, g);
                 float lon_m = lon.hi + __fdividef(a.hk * V.u, cl);
                 ff d_m = ff_add(d, a.hk * V.v);
@@ -631,16 +652,15 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
                 midpoint_bc(lon_m, d_m, g);
                 const Cell c2 = locate(lon_m, d_m, p_m, g, s, cc.k);
                 Wind V2, dummy;
-                eval_wind<ST, false>(a.m0, a.m1, s, g, c2, wm, cc, V2, dummy);
+                eval_wind<ST, false>(a.mp, s, g, c2, wlm, whm, cc, V2, dummy);
                 const float cl2 = coslat(d_m, 0.f, g);
                 ilon = __fdividef(a.dk * V2.u, cl2);
                 ilat = a.dk * V2.v;
                 ip = a.dt * V2.w;
             } else if (use_meso) {
-                const float w0 = a.wt[2 * sidx];
                 const Cell c1 = locate(lon.hi, d, p.hi, g, s, cc.k);
                 Wind V;
-                eval_wind<ST, true>(a.m0, a.m1, s, g, c1, w0, cc, V, var);
+                eval_wind<ST, true>(a.mp, s, g, c1, a.wt[4 * sidx], a.wt[4 * sidx + 1], cc, V, var);
             }
             if (MODE != MODE_ADVECT && (use_turb || use_meso)) {
                 // ---- module_diffusion_turb / module_diffusion_meso ----
@@ -703,20 +723,20 @@ __global__ void k_windows(const double* ts, const double* te, int nrel, double t
 }
 
 template <int ST>
-__global__ void __launch_bounds__(kBlock) k_interp(Geo g, MetView m0, MetView m1, float w,
+__global__ void __launch_bounds__(kBlock) k_interp(Geo g, MetPair mp, float wl, float wh,
                                                    int64_t n, const double* lon,
                                                    const double* lat, const double* p,
                                                    float* ou, float* ov, float* ow,
                                                    float* ovar) {
     __shared__ Smem s;
-    load_tables(s, g, m0, m1, ST != MPTRAC_FP32);
+    load_tables(s, g, mp.scales[0], mp.scales[1], ST != MPTRAC_FP32);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
         const Cell c = locate(ff_make(lon[idx]).hi, ff_make(lat[idx] - g.lat0_d), ff_make(p[idx]).hi, g, s, -1);
         Wind V, var;
         RegCache cc;
         cc.init(nullptr);
-        eval_wind<ST, true>(m0, m1, s, g, c, w, cc, V, var);
+        eval_wind<ST, true>(mp, s, g, c, wl, wh, cc, V, var);
         ou[idx] = V.u;
         ov[idx] = V.v;
         ow[idx] = V.w;
@@ -734,7 +754,7 @@ __global__ void __launch_bounds__(kBlock) k_sample(Geo g, MetView m0, MetView m1
                                                    const double* lon, const double* lat, const double* p,
                                                    float* out) {
     __shared__ Smem s;
-    load_tables(s, g, m0, m1, false);
+    load_tables(s, g, nullptr, nullptr, false);
     using R = typename RecT<ST>::T;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
@@ -792,7 +812,7 @@ struct SediArgs {
 template <int ST>
 __global__ void __launch_bounds__(kBlock) k_sedi(const SediArgs a) {
     __shared__ Smem s;
-    load_tables(s, a.g, a.m0, a.m1, false);
+    load_tables(s, a.g, nullptr, nullptr, false);
     const Geo& g = a.g;
     using R = typename RecT<ST>::T;
     constexpr float Rd = 287.058f, G = 9.80665f;
@@ -967,20 +987,20 @@ cudaError_t launch_windows(const double* ts, const double* te, int nrel, double 
     return cudaGetLastError();
 }
 
-cudaError_t launch_interp(int storage, const Geo& g, MetView m0, MetView m1, float w, int64_t n,
+cudaError_t launch_interp(int storage, const Geo& g, MetPair mp, float w_lane0, float w_lane1, int64_t n,
                           const double* lon, const double* lat, const double* p, float* ou,
                           float* ov, float* ow, float* ovar, cudaStream_t s) {
     const int grid = grid_for(n);
     note_launches(1);
     switch (storage) {
         case MPTRAC_FP32:
-            k_interp<MPTRAC_FP32><<<grid, kBlock, 0, s>>>(g, m0, m1, w, n, lon, lat, p, ou, ov, ow, ovar);
+            k_interp<MPTRAC_FP32><<<grid, kBlock, 0, s>>>(g, mp, w_lane0, w_lane1, n, lon, lat, p, ou, ov, ow, ovar);
             break;
         case MPTRAC_BF16:
-            k_interp<MPTRAC_BF16><<<grid, kBlock, 0, s>>>(g, m0, m1, w, n, lon, lat, p, ou, ov, ow, ovar);
+            k_interp<MPTRAC_BF16><<<grid, kBlock, 0, s>>>(g, mp, w_lane0, w_lane1, n, lon, lat, p, ou, ov, ow, ovar);
             break;
         default:
-            k_interp<MPTRAC_FP16><<<grid, kBlock, 0, s>>>(g, m0, m1, w, n, lon, lat, p, ou, ov, ow, ovar);
+            k_interp<MPTRAC_FP16><<<grid, kBlock, 0, s>>>(g, mp, w_lane0, w_lane1, n, lon, lat, p, ou, ov, ow, ovar);
             break;
     }
     return cudaGetLastError();
