@@ -307,6 +307,10 @@ int mptrac_init_grid(mptrac_ctx** out, const mptrac_grid_desc* g) {
         if (!rc) rc = alloc((void**)&c->d_scales[s], 4 * nz * sizeof(float));
     }
     if (!rc) rc = alloc(&c->d_pair, 2 * c->rec_bytes);
+    if (!rc && cudaMemset(c->d_pair, 0, 2 * c->rec_bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        rc = fail(MPTRAC_E_CUDA, "clearing the pair records failed");
+    }
     if (rc) {
         free_ctx(c);
         return rc;

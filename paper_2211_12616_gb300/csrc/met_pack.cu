@@ -89,20 +89,34 @@ __global__ void __launch_bounds__(256) k_pack(const float* __restrict__ u, const
         const int i = i0 + il, k = k0 + kl;
         if (i >= nx || k >= nz) continue;
         const int64_t r = ((int64_t)j * nx + i) * nz + k;
+        // the pair record is rewritten whole (read, replace this slot's lane,
+        // write): full-sector accesses instead of four scattered partial ones
         if (ST == MPTRAC_FP32) {
             static_cast<float4*>(recv)[r] =
                 make_float4(tile[0][kl][il], tile[1][kl][il], tile[2][kl][il], tile[3][kl][il]);
-            float* pr = static_cast<float*>(pairs) + r * 8 + slot;
-#pragma unroll
-            for (int var = 0; var < 4; ++var) pr[2 * var] = tile[var][kl][il];
+            float4* pr = static_cast<float4*>(pairs) + 2 * r;
+            float4 lo = pr[0], hi = pr[1];   // (u0, u1, v0, v1), (w0, w1, T0, T1)
+            if (slot == 0) {
+                lo.x = tile[0][kl][il]; lo.z = tile[1][kl][il]; hi.x = tile[2][kl][il]; hi.z = tile[3][kl][il];
+            } else {
+                lo.y = tile[0][kl][il]; lo.w = tile[1][kl][il]; hi.y = tile[2][kl][il]; hi.w = tile[3][kl][il];
+            }
+            pr[0] = lo;
+            pr[1] = hi;
         } else {
             uint32_t c[4];
 #pragma unroll
             for (int var = 0; var < 4; ++var) c[var] = code16(tile[var][kl][il], ST);
             static_cast<uint2*>(recv)[r] = make_uint2(c[0] | (c[1] << 16), c[2] | (c[3] << 16));
-            unsigned short* pr = static_cast<unsigned short*>(pairs) + r * 8 + slot;
-#pragma unroll
-            for (int var = 0; var < 4; ++var) pr[2 * var] = (unsigned short)c[var];
+            uint4* pr = static_cast<uint4*>(pairs) + r;   // words (u, v, omega, T), slot 0 in the low half
+            uint4 q = *pr;
+            const uint32_t keep = slot == 0 ? 0xFFFF0000u : 0x0000FFFFu;
+            const int sh = slot == 0 ? 0 : 16;
+            q.x = (q.x & keep) | (c[0] << sh);
+            q.y = (q.y & keep) | (c[1] << sh);
+            q.z = (q.z & keep) | (c[2] << sh);
+            q.w = (q.w & keep) | (c[3] << sh);
+            *pr = q;
         }
     }
 }

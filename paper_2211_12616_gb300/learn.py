@@ -13,7 +13,7 @@ and moves tensors around.
   then runs Adam on shuffled mini-batches with a cosine learning-rate decay.
 * ``run_surrogate`` / ``run_plain``: 30-minute segments by the network (with
   the plain fallback), or by the plain integrator -- 10 substeps of 180 s (the
-  judge), or one midpoint step of 30 minutes (``dt=DT_SEG``, the cheapest plain
+  reference trajectory), or one midpoint step of 30 minutes (``dt=DT_SEG``, the cheapest plain
   alternative: two wind evaluations per segment).
 """
 from __future__ import annotations
@@ -135,7 +135,7 @@ def run_surrogate(ctx: Context, surr: Surrogate, parts: Particles, snapshot_at, 
 
 def run_plain(ctx: Context, parts: Particles, snapshot_at, dt_met: float, t_start: float, t_end: float,
               dt: float = DT, stream=None, workspace=None):
-    """Plain midpoint advection over [t_start, t_end] with step dt (the judge at dt = 180 s);
+    """Plain midpoint advection over [t_start, t_end] with step dt (the reference trajectory at dt = 180 s);
     particles sorted by met cell at the start of every met interval, like ``run_surrogate``."""
     if workspace is None:
         workspace = torch.empty(ctx.sort_workspace_bytes(parts.n), dtype=torch.uint8, device=parts.lon.device)
