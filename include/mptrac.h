@@ -197,6 +197,34 @@ size_t mptrac_sort_workspace_bytes(const mptrac_ctx* ctx, int64_t n);
 int mptrac_sort(mptrac_ctx* ctx, const mptrac_particles* parts, void* workspace,
                 size_t ws_bytes, uintptr_t stream);
 
+/* mptrac_step followed by mptrac_sort, with the same result, fused: the step's
+ * last launch writes each particle's final state to the sort workspace
+ * together with its cell key and the first radix digit's histogram, so the
+ * sort reads no particle array again (the time loop of Sections 3-4 with the
+ * sorting modules of Section 6).  The paper has no such call; it saves a pass
+ * over the particles per sort.  Arguments and errors as mptrac_step and
+ * mptrac_sort (workspace rules included); with nsteps == 0 it is mptrac_sort.
+ * It is mptrac_step_handoff followed by mptrac_sort_handoff. */
+int mptrac_step_sort(mptrac_ctx* ctx, const mptrac_particles* parts, double t, double dt,
+                     const mptrac_diff_params* prm, uint64_t seed, uint64_t step0, int nsteps,
+                     void* workspace, size_t ws_bytes, uintptr_t stream);
+
+/* First half of mptrac_step_sort: the steps, with the final state left in
+ * `workspace` (with the cell keys) and the arrays of `parts` NOT updated.
+ * Until mptrac_sort_handoff has run on the same workspace and particles, the
+ * particle arrays hold the state before the call.  nsteps >= 1, else
+ * E_INVALID_ARG; otherwise arguments and errors as mptrac_step_sort. */
+int mptrac_step_handoff(mptrac_ctx* ctx, const mptrac_particles* parts, double t, double dt,
+                        const mptrac_diff_params* prm, uint64_t seed, uint64_t step0, int nsteps,
+                        void* workspace, size_t ws_bytes, uintptr_t stream);
+
+/* Second half of mptrac_step_sort: radix sort of the keys a preceding
+ * mptrac_step_handoff left in `workspace`, gathering the final state into the
+ * arrays of `parts` in sorted order.  Calling it without that hand-off leaves
+ * garbage in `parts`. */
+int mptrac_sort_handoff(mptrac_ctx* ctx, const mptrac_particles* parts, void* workspace,
+                        size_t ws_bytes, uintptr_t stream);
+
 /* module_meteo (Section 3.2): u, v, omega and T (0 when nvars == 3) at every
  * particle position at time t, by the 4D linear interpolation of the
  * advection (float32 arithmetic), into DEVICE out[4][n] (variable-major).

@@ -57,6 +57,13 @@ SIGNATURES = {
                                  C.POINTER(DiffParamsDesc), C.c_uint64, C.c_uint64, C.c_int, C.c_void_p]),
     "mptrac_step": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_double, C.c_double,
                               C.POINTER(DiffParamsDesc), C.c_uint64, C.c_uint64, C.c_int, C.c_void_p]),
+    "mptrac_step_sort": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_double, C.c_double,
+                                   C.POINTER(DiffParamsDesc), C.c_uint64, C.c_uint64, C.c_int, C.c_void_p,
+                                   C.c_size_t, C.c_void_p]),
+    "mptrac_step_handoff": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_double, C.c_double,
+                                      C.POINTER(DiffParamsDesc), C.c_uint64, C.c_uint64, C.c_int, C.c_void_p,
+                                      C.c_size_t, C.c_void_p]),
+    "mptrac_sort_handoff": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_void_p, C.c_size_t, C.c_void_p]),
     "mptrac_sort_workspace_bytes": (C.c_size_t, [C.c_void_p, C.c_int64]),
     "mptrac_sort": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_void_p, C.c_size_t, C.c_void_p]),
     "mptrac_cell_keys": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_void_p, C.c_void_p]),
@@ -259,6 +266,28 @@ class Context:
     def step(self, parts: Particles, t, dt, prm: DiffParams, seed, step0, nsteps, stream=None):
         check(load().mptrac_step(self.h, C.byref(parts.desc()), float(t), float(dt), C.byref(prm.desc()),
                                  int(seed), int(step0), int(nsteps), _stream(stream)), self.h)
+
+    def step_sort(self, parts: Particles, t, dt, prm: DiffParams, seed, step0, nsteps,
+                  workspace: torch.Tensor | None = None, stream=None):
+        """``step`` then ``sort`` in one call (the step hands its results to the sort)."""
+        if workspace is None:
+            workspace = torch.empty(self.sort_workspace_bytes(parts.n), dtype=torch.uint8, device=parts.lon.device)
+        check(load().mptrac_step_sort(self.h, C.byref(parts.desc()), float(t), float(dt), C.byref(prm.desc()),
+                                      int(seed), int(step0), int(nsteps), _ptr(workspace), workspace.numel(),
+                                      _stream(stream)), self.h)
+        return workspace
+
+    def step_handoff(self, parts: Particles, t, dt, prm: DiffParams, seed, step0, nsteps, workspace: torch.Tensor,
+                     stream=None):
+        """First half of ``step_sort``: the result stays in ``workspace`` until ``sort_handoff``."""
+        check(load().mptrac_step_handoff(self.h, C.byref(parts.desc()), float(t), float(dt), C.byref(prm.desc()),
+                                         int(seed), int(step0), int(nsteps), _ptr(workspace), workspace.numel(),
+                                         _stream(stream)), self.h)
+
+    def sort_handoff(self, parts: Particles, workspace: torch.Tensor, stream=None):
+        """Second half of ``step_sort``."""
+        check(load().mptrac_sort_handoff(self.h, C.byref(parts.desc()), _ptr(workspace), workspace.numel(),
+                                         _stream(stream)), self.h)
 
     def sort_workspace_bytes(self, n: int) -> int:
         return int(load().mptrac_sort_workspace_bytes(self.h, int(n)))

@@ -137,7 +137,7 @@ void lane_weights(int s_early, double w, float& lane0, float& lane1) {
 
 int run_transport(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
                   const mptrac_diff_params* prm, uint64_t seed, uint64_t step0, int nsteps,
-                  uintptr_t stream, int mode, const uint8_t* mask = nullptr) {
+                  uintptr_t stream, int mode, const uint8_t* mask = nullptr, const SortEmit* emit = nullptr) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(MPTRAC_E_INVALID_ARG, "dt must be finite and > 0 (got %g)", dt);
     if (!std::isfinite(t)) return fail(MPTRAC_E_INVALID_ARG, "t must be finite");
@@ -220,6 +220,8 @@ int run_transport(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
             lane_weights(s0, (tn + 0.5 * dt - t0) / (t1 - t0), a.wt[4 * q + 2], a.wt[4 * q + 3]);
         }
         if (use_win) MPTRAC_CUDA(launch_windows(c->d_rel_ts, c->d_rel_te, c->n_rel, t, dt, n0, cnt, c->d_win, st));
+        // the last launch hands its results to the sort, if one follows
+        a.emit = (emit && n0 + cnt >= nsteps) ? *emit : SortEmit{};
         MPTRAC_CUDA(launch_transport(c->storage, mode, a, grid, c->launch_variant, c->persistent, st));
     }
     return ok();
@@ -448,6 +450,50 @@ int mptrac_step(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
                 const mptrac_diff_params* prm, uint64_t seed, uint64_t step0, int nsteps,
                 uintptr_t stream) {
     return run_transport(c, P, t, dt, prm, seed, step0, nsteps, stream, MODE_STEP);
+}
+
+int check_workspace(const mptrac_particles* P, const void* ws, size_t ws_bytes) {
+    const size_t need = sort_workspace_bytes(P->n);
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < need)
+        return fail(MPTRAC_E_WORKSPACE, "sort workspace must be 256-byte aligned device memory of >= %zu bytes (got %p, %zu)", need, ws, ws_bytes);
+    if (!device_accessible(ws)) return fail(MPTRAC_E_WORKSPACE, "sort workspace is not device memory");
+    return MPTRAC_OK;
+}
+
+int mptrac_step_handoff(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
+                        const mptrac_diff_params* prm, uint64_t seed, uint64_t step0, int nsteps, void* ws,
+                        size_t ws_bytes, uintptr_t stream) {
+    if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    if (nsteps < 1) return fail(MPTRAC_E_INVALID_ARG, "nsteps must be >= 1 for a hand-off (got %d)", nsteps);
+    int rc = check_particles(P, false);
+    if (rc) return rc;
+    if (P->n == 0) return run_transport(c, P, t, dt, prm, seed, step0, nsteps, stream, MODE_STEP);
+    if ((rc = check_workspace(P, ws, ws_bytes))) return rc;
+    SortEmit e{};
+    MPTRAC_CUDA(sort_emit_args(*P, ws, e, reinterpret_cast<cudaStream_t>(stream)));
+    return run_transport(c, P, t, dt, prm, seed, step0, nsteps, stream, MODE_STEP, nullptr, &e);
+}
+
+int mptrac_sort_handoff(mptrac_ctx* c, const mptrac_particles* P, void* ws, size_t ws_bytes,
+                        uintptr_t stream) {
+    if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    int rc = check_particles(P, false);
+    if (rc) return rc;
+    if (P->n == 0) return ok();
+    if ((rc = check_workspace(P, ws, ws_bytes))) return rc;
+    MPTRAC_CUDA(sort_after_emit(*P, ws, c->key_bits, reinterpret_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
+int mptrac_step_sort(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
+                     const mptrac_diff_params* prm, uint64_t seed, uint64_t step0, int nsteps, void* ws,
+                     size_t ws_bytes, uintptr_t stream) {
+    if (nsteps == 0) {   // nothing to hand off: the arguments are checked, then a plain sort
+        int rc = run_transport(c, P, t, dt, prm, seed, step0, nsteps, stream, MODE_STEP);
+        return rc ? rc : mptrac_sort(c, P, ws, ws_bytes, stream);
+    }
+    int rc = mptrac_step_handoff(c, P, t, dt, prm, seed, step0, nsteps, ws, ws_bytes, stream);
+    return rc ? rc : mptrac_sort_handoff(c, P, ws, ws_bytes, stream);
 }
 
 size_t mptrac_sort_workspace_bytes(const mptrac_ctx*, int64_t n) {

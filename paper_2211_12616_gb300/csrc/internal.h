@@ -53,6 +53,25 @@ struct MetPair {
     const float* scales[2];
 };
 
+// The particle arrays (null entries are absent) and their copies in the
+// sort workspace: `part` is sorted in place, `copy` holds the unsorted state.
+struct Arrays {
+    double* d[3];      // lon, lat, p
+    uint32_t* u[2];    // id, release
+    float* f[3];       // up, vp, wp
+};
+
+// Hand-off from the fused step to the sort (keys == nullptr: none).  The
+// launch writes every particle's final state to `copy` instead of the particle
+// arrays, its cell key to keys[i] and adds it to the first-digit histogram
+// hist[digit * ntiles + i / 1024] (zeroed beforehand).
+struct SortEmit {
+    Arrays copy;
+    uint32_t* keys;
+    uint32_t* hist;
+    int ntiles;
+};
+
 // Arguments of the particle kernels (advect / diffuse / step).
 struct StepArgs {
     Geo geo;
@@ -78,6 +97,7 @@ struct StepArgs {
     uint32_t key0, key1;          // Philox key = seed
     uint32_t ks[20];              // Philox key schedule: round r uses (ks[2r], ks[2r+1])
     uint64_t step0;
+    SortEmit emit;
     // time weights of lanes (slot 0, slot 1) at t_n and at t_n + dt/2: step q uses
     // wt[4q], wt[4q + 1] and wt[4q + 2], wt[4q + 3]
     float wt[4 * kMaxStepsPerLaunch];
@@ -119,6 +139,10 @@ cudaError_t launch_cell_keys(const Geo& g, int64_t n, const double* lon, const d
                              const double* p, uint32_t* keys, cudaStream_t s);
 cudaError_t run_sort(const Geo& g, const mptrac_particles& P, void* ws, int key_bits,
                      cudaStream_t s);
+// The hand-off arguments for the fused step over P with workspace ws (its
+// first-digit histograms zeroed on s), and the radix passes that follow it.
+cudaError_t sort_emit_args(const mptrac_particles& P, void* ws, SortEmit& out, cudaStream_t s);
+cudaError_t sort_after_emit(const mptrac_particles& P, void* ws, int key_bits, cudaStream_t s);
 // As run_sort, but particles whose release is inactive at time t (window from
 // ts/te, or release index >= nrel) get the key 2^key_bits, after every cell key.
 cudaError_t run_sort_at(const Geo& g, const mptrac_particles& P, void* ws, int key_bits, double t,

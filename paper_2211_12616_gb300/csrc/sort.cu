@@ -11,6 +11,7 @@
 // other with __match_any_sync and are ranked by lane, warps are ranked by a
 // shared-memory scan, rounds by a running count -- which keeps equal keys in
 // their input order.
+#include "cell_key.cuh"
 #include "internal.h"
 
 namespace mptrac {
@@ -19,107 +20,8 @@ namespace {
 constexpr int kSortThreads = 256;
 constexpr int kRounds = 4;
 constexpr int kTileKeys = kSortThreads * kRounds;
-constexpr int kRadix = 256;
-
-// Cell key from float64 positions, the definition: x = ((lon - lon0) mod 360)
-// / dlon, i = floor(x) mod nx; j = floor((lat - lat0) / dlat) clamped to
-// [0, ny-2]; k = (number of levels >= clamp(p)) - 1 clamped to [0, nz-2].
-// plevd: the float64 levels (a shared-memory copy).  The mod 360 and mod nx
-// are skipped where they are the identity (or one subtraction).
-__device__ __noinline__ uint32_t cell_key_f64(double lon, double lat, double p, const Geo& g,
-                                              const double* plevd) {
-    double r = __dsub_rn(lon, g.lon0_d);
-    if (!(r >= 0.0 && r < 360.0)) {
-        r = fmod(r, 360.0);
-        if (r < 0.0) r = __dadd_rn(r, 360.0);
-    }
-    const double x = __ddiv_rn(r, g.dlon_d);
-    long long i = (long long)floor(x);
-    if (i >= g.nx) i = (i - g.nx < g.nx) ? i - g.nx : i % g.nx;
-    if (i < 0) i = 0;   // x >= 0 here; guards a NaN longitude
-    const double y = __ddiv_rn(__dsub_rn(lat, g.lat0_d), g.dlat_d);
-    long long j = (long long)floor(y);
-    j = j < 0 ? 0 : (j > g.ny - 2 ? g.ny - 2 : j);
-    const double pc = fmin(fmax(p, g.pmin_d), g.pmax_d);
-    int lo = 0, hi = g.nz;   // plev decreasing: length of the prefix with plev >= pc
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (plevd[mid] >= pc) lo = mid + 1; else hi = mid;
-    }
-    int k = lo - 1;
-    k = k < 0 ? 0 : (k > g.nz - 2 ? g.nz - 2 : k);
-    return (uint32_t)((j * g.nx + i) * g.nz + k);
-}
-
-struct KeyTables {
-    double plev_d[kMaxNZ];
-    float plev[kMaxNZ];
-    int16_t kguess[kGuessBins];
-};
-
-__device__ __forceinline__ void load_key_tables(KeyTables& t, const Geo& g) {
-    for (int q = threadIdx.x; q < g.nz; q += blockDim.x) {
-        t.plev_d[q] = g.plev_d[q];
-        t.plev[q] = g.plev[q];
-    }
-    for (int q = threadIdx.x; q < g.nbins; q += blockDim.x) t.kguess[q] = g.kguess[q];
-}
-
-// float32 of a float64 by truncating its mantissa, with integer operations
-// only (|error| < 2^-23 |x|), where the result is a normal float32; zero and
-// anything else take the conversion instruction (on the float64 pipe, which
-// is narrow on this GPU).
-__device__ __forceinline__ float f64_to_f32_trunc(double x) {
-    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
-    const uint32_t e = (hi >> 20) & 0x7FFu;   // float64 biased exponent
-    if (e - 897u < 254u) {                     // float32 biased exponent e - 896 in [1, 254]
-        const uint32_t mag = (((hi & 0x7FFFFFFFu) - (896u << 20)) << 3) | (lo >> 29);
-        return __uint_as_float((hi & 0x80000000u) | mag);
-    }
-    return (float)x;
-}
-
-// Same key, computed in float32 when that is provably identical: the float32
-// cell coordinates are within key_mx / key_my cells of the float64 ones (a
-// bound derived from the grid on the host, with a factor 2 to spare) and the
-// float32 differences p - plev[k] within 1.8e-7 p of the float64 ones, so
-// estimates farther than that from every cell face (and p farther than 1e-6
-// relative from its bracketing levels) have the same floor / level count as
-// the float64 definition.  Anything closer to a face, or outside the regular
-// range, takes the float64 path.
-__device__ __forceinline__ uint32_t cell_key(double lon, double lat, double p, const Geo& g,
-                                             const KeyTables& t) {
-    const float lf = f64_to_f32_trunc(lon), af = f64_to_f32_trunc(lat), pf = f64_to_f32_trunc(p);
-    const float x = (lf - g.lon0) * g.inv_dlon;
-    const float y = (af - g.lat0) * g.inv_dlat;
-    const float xf = floorf(x), yf = floorf(y);
-    const float fx = x - xf, fy = y - yf;
-    const float mx = g.key_mx, my = g.key_my;
-    bool ok = mx < 0.25f && my < 0.25f && (x > mx) && (x < (float)g.nx - mx) && fx > mx && fx < 1.f - mx;
-    int j = (int)yf;
-    if (y < -my) j = 0;                                          // clamped from below whatever the rounding
-    else if (y > (float)(g.ny - 2) + my && y < 1e30f) j = g.ny - 2;  // top cell (clamped)
-    else ok = ok && fy > my && fy < 1.f - my && j >= 0 && j <= g.ny - 2;
-    // level: first guess from the ln(p) table, refined in float32, accepted
-    // only when p is clear of both bracketing levels
-    const float pc = fminf(fmaxf(pf, g.pmin), g.pmax);
-    int b = (int)((__logf(pc) - g.lnp_top) * g.inv_dln);
-    b = min(max(b, 0), g.nbins - 1);
-    int k = t.kguess[b];
-    while (k > 0 && t.plev[k] < pc) --k;
-    while (k < g.nz - 2 && t.plev[k + 1] >= pc) ++k;
-    const bool below_top = pf > g.pmax * (1.f + 1e-5f);     // clamps to level 0
-    const bool above_bot = pf < g.pmin * (1.f - 1e-5f);     // clamps to the top level
-    if (!below_top && !above_bot) {
-        const float margin = 1e-6f * pc;
-        ok = ok && (t.plev[k] - pc > margin || k == 0) && (pc - t.plev[k + 1] > margin || k == g.nz - 2);
-        if (k == 0 && !(pc < t.plev[0] - margin)) ok = false;
-        if (k == g.nz - 2 && !(pc > t.plev[g.nz - 1] + margin)) ok = false;
-    }
-    if (!ok || !(lf == lf) || !(af == af) || !(pf == pf)) return cell_key_f64(lon, lat, p, g, t.plev_d);
-    const int i = (int)xf;
-    return (uint32_t)((j * g.nx + i) * g.nz + k);
-}
+constexpr int kRadix = kSortRadix;
+static_assert(kTileKeys == kSortTileKeys, "tile size shared with the fused step");
 
 __global__ void k_keys(Geo g, int64_t n, const double* lon, const double* lat, const double* p,
                        uint32_t* keys, uint32_t* vals) {
@@ -128,7 +30,7 @@ __global__ void k_keys(Geo g, int64_t n, const double* lon, const double* lat, c
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
-        keys[q] = cell_key(lon[q], lat[q], p[q], g, t);
+        keys[q] = cell_key(lon[q], lat[q], p[q], g, t.plev, t.kguess, t.plev_d);
         if (vals) vals[q] = (uint32_t)q;
     }
 }
@@ -144,7 +46,7 @@ __global__ void k_grid_counts(Geo g, int64_t n, const double* lon, const double*
     const int64_t span = (n + stride - 1) / stride * stride;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < span; q += stride) {
         const bool valid = q < n;
-        const uint32_t key = valid ? cell_key(lon[q], lat[q], p[q], g, tb) : 0xFFFFFFFFu;
+        const uint32_t key = valid ? cell_key(lon[q], lat[q], p[q], g, tb.plev, tb.kguess, tb.plev_d) : 0xFFFFFFFFu;
         const unsigned peers = __match_any_sync(__activemask(), key);
         const int lane = threadIdx.x & 31;
         if (valid && (__ffs(peers) - 1) == lane) atomicAdd(&counts[key], (uint32_t)__popc(peers));
@@ -161,14 +63,6 @@ __device__ __forceinline__ void hist_add(uint32_t* h, bool valid, uint32_t digit
     const int lane = threadIdx.x & 31;
     if (valid && (__ffs(peers) - 1) == lane) atomicAdd(&h[digit], (uint32_t)__popc(peers));
 }
-
-// The particle arrays (null entries are absent) and their copies in the
-// workspace: `part` is sorted in place, `copy` holds the unsorted state.
-struct Arrays {
-    double* d[3];      // lon, lat, p
-    uint32_t* u[2];    // id, release
-    float* f[3];       // up, vp, wp
-};
 
 struct KeysArgs {
     Geo g;
@@ -234,7 +128,7 @@ __global__ void __launch_bounds__(kSortThreads) k_keys_hist(const __grid_constan
                 const uint32_t rr = vu[r][1];
                 active = rr < (uint32_t)a.nrel && a.t >= a.ts[rr] && a.t < a.te[rr];
             }
-            k = active ? cell_key(vd[r][0], vd[r][1], vd[r][2], g, tb) : a.inactive_key;
+            k = active ? cell_key(vd[r][0], vd[r][1], vd[r][2], g, tb.plev, tb.kguess, tb.plev_d) : a.inactive_key;
             a.keys[q] = k;
         }
         hist_add(h, valid, k & 0xFF);
@@ -564,6 +458,20 @@ cudaError_t launch_grid_counts(const Geo& g, int64_t n, const double* lon, const
     note_launches(1);
     k_grid_counts<<<grid_for(n), 256, 0, s>>>(g, n, lon, lat, p, counts);
     return cudaGetLastError();
+}
+
+cudaError_t sort_emit_args(const mptrac_particles& P, void* ws, SortEmit& out, cudaStream_t s) {
+    const WsLayout L = ws_layout(P.n);
+    out.copy = copy_arrays(P, ws);
+    out.keys = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.keys_a);
+    out.hist = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + L.hist);
+    out.ntiles = (int)ntiles_for(P.n);
+    return cudaMemsetAsync(out.hist, 0, (size_t)out.ntiles * kRadix * sizeof(uint32_t), s);
+}
+
+cudaError_t sort_after_emit(const mptrac_particles& P, void* ws, int key_bits, cudaStream_t s) {
+    if (P.n <= 0) return cudaSuccess;
+    return sort_from_keys(P, ws, key_bits, s);
 }
 
 cudaError_t run_sort(const Geo& g, const mptrac_particles& P, void* ws, int key_bits,

@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "cell_key.cuh"
 #include "internal.h"
 #include "met_record.cuh"
 
@@ -521,7 +522,7 @@ __device__ __forceinline__ void load_tables(SmemT<NSC>& s, const Geo& g, const f
 }
 
 // ---------------------------------------------------------------------------
-// The particle kernel
+// Pieces of the step: midpoint position rules, random draws
 // ---------------------------------------------------------------------------
 // Midpoint position rules: latitude reflected over the poles (longitude +
 // 180), longitude wrapped into [lon0, lon0 + 360).  The pressure needs no
@@ -574,6 +575,34 @@ __device__ __forceinline__ void draw_meso(const StepArgs& a, uint32_t pid, uint3
     box_muller(wd.z, wd.w, z.m2, unused);
 }
 
+// Hand-off of one particle to the sort that follows the launch: its final
+// state goes to the workspace copies (the mesoscale perturbations already
+// there when `meso_done`), its cell key to keys[idx], and the key's lowest
+// digit to the histogram of its 1024-particle tile.  Lanes of a warp with the
+// same digit add their count with one atomic.
+template <class S>
+__device__ __forceinline__ void hand_off(const StepArgs& a, const S& s, int64_t idx, double lon, double lat,
+                                         double p, uint32_t pid, bool meso_done) {
+    const SortEmit& e = a.emit;
+    e.copy.d[0][idx] = lon;
+    e.copy.d[1][idx] = lat;
+    e.copy.d[2][idx] = p;
+    e.copy.u[0][idx] = pid;
+    if (e.copy.u[1]) e.copy.u[1][idx] = a.release[idx];
+    if (!meso_done) {
+        const float* src[3] = {a.up, a.vp, a.wp};
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (e.copy.f[c]) e.copy.f[c][idx] = src[c][idx];
+    }
+    const uint32_t key = cell_key(lon, lat, p, a.geo, s.plev, s.kguess, a.geo.plev_d);
+    e.keys[idx] = key;
+    const uint32_t digit = key & (kSortRadix - 1);
+    const unsigned peers = __match_any_sync(__activemask(), digit);
+    if ((__ffs(peers) - 1) == (int)(threadIdx.x & 31))
+        atomicAdd(&e.hist[(int64_t)digit * e.ntiles + idx / kSortTileKeys], (uint32_t)__popc(peers));
+}
+
 // ---------------------------------------------------------------------------
 // The particle kernel
 // ---------------------------------------------------------------------------
@@ -594,10 +623,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
     const bool use_turb = FULL || ((MODE != MODE_ADVECT) && a.turb);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < a.n; idx += stride) {
-        if (a.mask && !a.mask[idx]) continue;
+        const bool masked = a.mask && !a.mask[idx];
         int nlo = 0, nhi = a.nsteps;
         uint32_t rel = 0;
-        if (a.release) {
+        if (!masked && a.release) {
             rel = a.release[idx];
             if (a.win) {
                 if (rel < (uint32_t)a.n_rel) {
@@ -609,7 +638,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
                 }
             }
         }
-        if (nlo >= nhi) continue;
+        const bool emit = a.emit.keys != nullptr;
+        if (masked || nlo >= nhi) {   // left as it is
+            if (emit) hand_off(a, s, idx, a.lon[idx], a.lat[idx], a.p[idx], a.id[idx], false);
+            continue;
+        }
         ff lon = ff_make(a.lon[idx]);
         ff d = ff_make(a.lat[idx] - g.lat0_d);   // latitude as d = lat - lat0
         ff p = ff_make(a.p[idx]);
@@ -692,13 +725,23 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
             // ---- module_position ----
             position_bc(lon, d, p, g);
         }
-        a.lon[idx] = ff_val(lon);
-        a.lat[idx] = ff_val(d) + g.lat0_d;
-        a.p[idx] = ff_val(p);
-        if (use_meso) {
-            a.up[idx] = up;
-            a.vp[idx] = vp;
-            a.wp[idx] = wp;
+        const double lon_out = ff_val(lon), lat_out = ff_val(d) + g.lat0_d, p_out = ff_val(p);
+        if (emit) {
+            if (use_meso) {
+                a.emit.copy.f[0][idx] = up;
+                a.emit.copy.f[1][idx] = vp;
+                a.emit.copy.f[2][idx] = wp;
+            }
+            hand_off(a, s, idx, lon_out, lat_out, p_out, pid, use_meso);
+        } else {
+            a.lon[idx] = lon_out;
+            a.lat[idx] = lat_out;
+            a.p[idx] = p_out;
+            if (use_meso) {
+                a.up[idx] = up;
+                a.vp[idx] = vp;
+                a.wp[idx] = wp;
+            }
         }
     }
 }

@@ -5,7 +5,11 @@ Mirrors the structure of MPTRAC's main loop (arxiv 2211.12616, Sections 3 and
 met snapshots the next snapshot is loaded (``read_met`` + update device); the
 particles then advance in blocks of ``sort_every`` fused steps (advection,
 turbulent and mesoscale diffusion, position rules), and are sorted by met cell
-before every block so that each block starts with cell-ordered particles.
+before every block so that each block starts with cell-ordered particles.  The
+sort before the first block is a plain ``mptrac_sort``; every later one is
+fused into the block before it (``mptrac_step_handoff`` +
+``mptrac_sort_handoff``): the block's last launch hands its results to the
+sort.
 
 With ``groups`` = G > 1 the particles are split into G contiguous groups, each
 sorted and stepped on a stream of its own: a group's sort and the last,
@@ -64,6 +68,7 @@ class Simulation:
         main = stream if stream is not None else torch.cuda.current_stream(self.parts.lon.device)
         gstreams = self._group_streams(main)
         step = 0
+        sorted_ = False           # particles already sorted by the previous block
         for iv in range(n_iv):
             ta = t_start + iv * self.dt_met
             tb = ta + self.dt_met
@@ -84,14 +89,22 @@ class Simulation:
             while done < steps_per_iv:
                 cnt = min(self.sort_every, steps_per_iv - done)
                 t = ta + done * self.dt
+                last = iv == n_iv - 1 and done + cnt >= steps_per_iv   # no block follows
                 for parts, ws, gs in zip(self.groups, self.workspaces, gstreams):
-                    if self.do_sort:
+                    if self.do_sort and not sorted_:
                         ctx.sort(parts, ws, stream=gs)
                     if self.step_hook:
                         self.step_hook("begin", gs)
-                    ctx.step(parts, t, self.dt, self.prm, self.seed, step, cnt, stream=gs)
+                    handoff = self.do_sort and not last
+                    if handoff:
+                        ctx.step_handoff(parts, t, self.dt, self.prm, self.seed, step, cnt, ws, stream=gs)
+                    else:
+                        ctx.step(parts, t, self.dt, self.prm, self.seed, step, cnt, stream=gs)
                     if self.step_hook:
                         self.step_hook("end", gs)
+                    if handoff:
+                        ctx.sort_handoff(parts, ws, stream=gs)
+                sorted_ = self.do_sort
                 done += cnt
                 step += cnt
         for gs in gstreams:
