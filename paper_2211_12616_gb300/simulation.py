@@ -19,6 +19,11 @@ their order (counter-based random numbers keyed by particle id), so the
 results are those of G = 1 up to the order of the particles in memory.
 The groups join before every met load, which overwrites a slot they read.
 
+Snapshots that ``snapshot_at`` returns in host memory (pinned, for the copies
+to overlap) are prefetched: right after an interval's loads, the snapshot the
+next interval needs is copied into one of two device buffers on a copy stream
+while the interval computes, and its load then reads the device copy.
+
 This module only sequences ABI calls.
 """
 from __future__ import annotations
@@ -45,7 +50,48 @@ class Simulation:
                            for v in self.groups] if sort else [None] * g
         self.workspace = self.workspaces[0]
         self._streams = None
+        self._pf = None           # host-snapshot prefetch state (copy stream, device buffers, events)
         self.step_hook = None     # called around every mptrac_step: hook(stage, stream)
+
+    def _on_device(self, fields):
+        return all(x is None or (isinstance(x, torch.Tensor) and x.is_cuda) for x in fields)
+
+    def _prefetch(self, t):
+        """Copies the host snapshot at time t into the next device buffer on the copy stream."""
+        f = self.snapshot_at(t)
+        if self._on_device(f) or not all(x is None or isinstance(x, torch.Tensor) for x in f):
+            return
+        dev = self.parts.lon.device
+        if self._pf is None:
+            self._pf = {"stream": torch.cuda.Stream(device=dev), "bufs": [None, None], "used": [None, None],
+                        "ready": {}, "next": 0}
+        pf = self._pf
+        b = pf["next"]
+        pf["next"] = 1 - b
+        if pf["bufs"][b] is None:
+            pf["bufs"][b] = [None if x is None else torch.empty(x.shape, dtype=x.dtype, device=dev) for x in f]
+        cs = pf["stream"]
+        if pf["used"][b] is not None:
+            cs.wait_event(pf["used"][b])      # the load that read this buffer has run
+        with torch.cuda.stream(cs):
+            for dst, src in zip(pf["bufs"][b], f):
+                if dst is not None:
+                    dst.copy_(src, non_blocking=True)
+        ev = torch.cuda.Event()
+        ev.record(cs)
+        pf["ready"][t] = (b, ev)
+
+    def _load(self, slot, t, main):
+        pf = self._pf
+        if pf is not None and t in pf["ready"]:
+            b, ev = pf["ready"].pop(t)
+            main.wait_event(ev)
+            self.ctx.load_met(slot, t, *pf["bufs"][b], stream=main)
+            used = torch.cuda.Event()
+            used.record(main)
+            pf["used"][b] = used
+        else:
+            self.ctx.load_met(slot, t, *self.snapshot_at(t), stream=main)
 
     def _group_streams(self, main):
         if len(self.groups) == 1:
@@ -80,8 +126,10 @@ class Simulation:
                     continue
                 free = [q for q in (0, 1) if q not in slots]
                 slot = free[0] if free else (0 if slots[0] != keep else 1)
-                ctx.load_met(slot, t, *self.snapshot_at(t), stream=main)
+                self._load(slot, t, main)
                 slots[slot] = t
+            if iv + 1 < n_iv:
+                self._prefetch(tb + self.dt_met)   # overlaps with this interval's steps
             for gs in gstreams:
                 if gs is not main:
                     gs.wait_stream(main)
