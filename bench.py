@@ -39,7 +39,7 @@ SEED_RNG = 2
 # DRAM bytes (read + write) of one fused-step launch of this workload, from an
 # ncu capture of the full-size launch (see profiles/); None when the kernel has
 # changed since the counters were taken.
-TRAFFIC_PER_LAUNCH = 193503488   # 169.1 MB read + 24.4 MB written (ncu, autotuned variant 2)
+TRAFFIC_PER_LAUNCH = 203547648   # 169.9 MB read + 33.6 MB written (ncu, variant 2, launch with the hand-off to the sort)
 TRAFFIC_GROUPS = 1                # particle groups of the captured launch
 METRIC = "particle-steps/s on 1 GB300 (advect+diffuse) and % gather roofline, surrogate vs plain"
 WORKLOAD = ("1deg 360x181x60 Fourier-mode wind, 4 snapshots 6h apart, 1e6 particles, dt=180s, 24h "
