@@ -276,7 +276,7 @@ def run_ours(args, rank, world):
     groups_try = (args.groups,) if args.groups else (1, 2, 3)
     if args.variant >= 0:   # fixed schedule (profiling): no autotuner launches before the timed pass
         best = {"variant": args.variant, "persistent": False, "sort_every": SORT_EVERY,
-                "groups": args.groups or 1}
+                "groups": args.groups or 2}
         tune_ms = {}
     else:
         best, tune_ms = autotune(make, lambda: work.copy_(init),
@@ -738,8 +738,9 @@ def main():
     ap.add_argument("--count-scale", type=float, default=1.0)
     ap.add_argument("--variant", type=int, default=-1,
                     help="fixed launch variant of the fused step (-1: autotuned)")
-    ap.add_argument("--groups", type=int, default=1,
-                    help="particle groups on streams of their own (0: the autotuner picks 1, 2 or 3)")
+    ap.add_argument("--groups", type=int, default=0,
+                    help="particle groups on streams of their own (0: the autotuner picks 1, 2 or 3; "
+                         "2 with a fixed --variant)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -94,10 +94,16 @@ class Simulation:
             self.ctx.load_met(slot, t, *self.snapshot_at(t), stream=main)
 
     def _group_streams(self, main):
+        """(step streams, sort streams): one of each per group; with one group both are ``main``.
+        The sorts run at high priority, so that a group's short, latency-bound sort kernels
+        take SM slots as the other groups' step blocks retire."""
         if len(self.groups) == 1:
-            return [main]
+            return [main], [main]
         if self._streams is None:
-            self._streams = [torch.cuda.Stream(device=self.parts.lon.device) for _ in self.groups]
+            dev = self.parts.lon.device
+            lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
+            self._streams = ([torch.cuda.Stream(device=dev) for _ in self.groups],
+                             [torch.cuda.Stream(device=dev, priority=hi) for _ in self.groups])
         return self._streams
 
     def run(self, t_start: float, t_end: float, stream=None) -> int:
@@ -112,7 +118,7 @@ class Simulation:
         n_iv = int(round((t_end - t_start) / self.dt_met))
         ctx, slots = self.ctx, {}
         main = stream if stream is not None else torch.cuda.current_stream(self.parts.lon.device)
-        gstreams = self._group_streams(main)
+        gstreams, sstreams = self._group_streams(main)
         step = 0
         sorted_ = False           # particles already sorted by the previous block
         for iv in range(n_iv):
@@ -138,9 +144,13 @@ class Simulation:
                 cnt = min(self.sort_every, steps_per_iv - done)
                 t = ta + done * self.dt
                 last = iv == n_iv - 1 and done + cnt >= steps_per_iv   # no block follows
-                for parts, ws, gs in zip(self.groups, self.workspaces, gstreams):
+                for parts, ws, gs, ss in zip(self.groups, self.workspaces, gstreams, sstreams):
                     if self.do_sort and not sorted_:
-                        ctx.sort(parts, ws, stream=gs)
+                        if ss is not gs:
+                            ss.wait_stream(gs)
+                        ctx.sort(parts, ws, stream=ss)
+                        if ss is not gs:
+                            gs.wait_stream(ss)
                     if self.step_hook:
                         self.step_hook("begin", gs)
                     handoff = self.do_sort and not last
@@ -151,7 +161,11 @@ class Simulation:
                     if self.step_hook:
                         self.step_hook("end", gs)
                     if handoff:
-                        ctx.sort_handoff(parts, ws, stream=gs)
+                        if ss is not gs:
+                            ss.wait_stream(gs)
+                        ctx.sort_handoff(parts, ws, stream=ss)
+                        if ss is not gs:
+                            gs.wait_stream(ss)
                 sorted_ = self.do_sort
                 done += cnt
                 step += cnt
