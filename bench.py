@@ -36,11 +36,13 @@ SORT_EVERY = 20
 SEED_FIELD = 2
 SEED_PART = 2
 SEED_RNG = 2
-# DRAM bytes (read + write) of one fused-step launch of this workload, from an
-# ncu capture of the full-size launch (see profiles/); None when the kernel has
-# changed since the counters were taken.
-TRAFFIC_PER_LAUNCH = 203547648   # 169.9 MB read + 33.6 MB written (ncu, variant 2, launch with the hand-off to the sort)
-TRAFFIC_GROUPS = 1                # particle groups of the captured launch
+# DRAM bytes (read + write) of one fused-step launch of this workload by the
+# number of particle groups (a launch covers 1/groups of the particles), from ncu
+# captures of full-size launches of variant 2 with the hand-off to the sort (see
+# profiles/).  A schedule without a capture reports None, and so does any launch
+# after the kernel changes, until it is captured again.
+TRAFFIC_PER_LAUNCH = {1: 203547648,   # 169.9 MB read + 33.6 MB written, 1e6 particles
+                      2: 157252352}   # 142.1 MB read + 15.1 MB written, 5e5 particles
 METRIC = "particle-steps/s on 1 GB300 (advect+diffuse) and % gather roofline, surrogate vs plain"
 WORKLOAD = ("1deg 360x181x60 Fourier-mode wind, 4 snapshots 6h apart, 1e6 particles, dt=180s, 24h "
             "(480 fused advect+turb+meso steps), sort by met cell every 20 steps")
@@ -383,7 +385,7 @@ def run_ours(args, rank, world):
         "data": "synthetic", "config": _config(n, {"autotuned": best, "autotune_ms": tune_ms}),
         "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TOP/s",
                      "frac": alu_achieved / alu_peak,
-                     "traffic": TRAFFIC_PER_LAUNCH if n_groups == TRAFFIC_GROUPS else None,
+                     "traffic": TRAFFIC_PER_LAUNCH.get(n_groups) if best["variant"] == 2 else None,
                      "kernel": "k_transport<fp32, step>", "avg_launch_ms": step_avg_ms,
                      "launches_timed": len(step_ms), "particle_steps_per_launch": psteps_per_launch,
                      "timing": "union of the launch intervals (CUDA events on each group's stream) / launches",
