@@ -29,7 +29,9 @@ design notes of the repository):
 * Diffusion displacements (turbulent + mesoscale) are converted at the
   post-advection position: cos(lat) and p of x after advection.
 * Random numbers: ``philox.normals4`` with counter (id, step0 + n, stream,
-  release); turbulent uses z0..z2 of stream 0, mesoscale z0..z2 of stream 1.
+  release).  The normals of stream 0 and then stream 1 are used in order:
+  turbulent takes z0..z2 of stream 0, mesoscale z3 of stream 0 and z0, z1 of
+  stream 1 (z2, z3 of stream 1 are not used).
 * Position boundaries (``module_position``): lat > 90 -> 180 - lat,
   lat < -90 -> -180 - lat, each with lon + 180; lon wrapped into
   [lon0, lon0 + 360); p clamped to [min plev, max plev].
@@ -148,15 +150,17 @@ def _diffusion(met, st, sel, lon, lat, p, s2, step, seed, dt, prm):
     dlon = np.zeros_like(lon)
     dlat = np.zeros_like(lon)
     dp = np.zeros_like(lon)
+    if prm.turb or prm.meso:
+        z0, z1, z2, z3 = philox.normals4(pid, step, philox.STREAM_TURB, rel, seed)
     if prm.turb:
-        z0, z1, z2, _ = philox.normals4(pid, step, philox.STREAM_TURB, rel, seed)
         sh = np.sqrt(2.0 * prm.dx * dt)
         sv = np.sqrt(2.0 * prm.dz * dt)
         dlon += sh * z0
         dlat += sh * z1
         dp += -p * (sv * z2) / prm.scale_height
     if prm.meso:
-        m0, m1, m2, _ = philox.normals4(pid, step, philox.STREAM_MESO, rel, seed)
+        m1, m2, _, _ = philox.normals4(pid, step, philox.STREAM_MESO, rel, seed)
+        m0 = z3
         r = np.clip(1.0 - 2.0 * dt / (met.t1 - met.t0), 0.0, 1.0)
         a = np.sqrt(1.0 - r * r) * prm.meso_f
         up = r * st["up"][sel] + a * np.sqrt(s2[0]) * m0

@@ -552,27 +552,27 @@ __device__ __forceinline__ void midpoint_bc(float& lon, ff& d, const Geo& g) {
     if (!(d.hi < g.dn && d.hi > g.ds && lon < g.lon1 && lon >= g.lon0)) midpoint_rules(lon, d, g);
 }
 
-// Gaussian draws of one step: turbulence from counter (id, step, 0, release),
-// mesoscale from (id, step, 1, release); three of the four normals of each
-// draw are used.
+// Gaussian draws of one step from counters (id, step, 0, release) and
+// (id, step, 1, release): their normals are used in order, turbulence taking
+// the first three of draw 0, mesoscale the fourth of draw 0 and the first two
+// of draw 1 -- three Box-Muller pairs per step.
 struct Normals {
     float t0, t1, t2;   // turbulence: east, north, vertical
     float m0, m1, m2;   // mesoscale: u, v, omega
 };
 
+// draw 0: the turbulent normals and the first mesoscale one
 __device__ __forceinline__ void draw_turb(const StepArgs& a, uint32_t pid, uint32_t step, uint32_t rel,
                                           Normals& z) {
     const uint4 wd = philox4x32_10_ks(make_uint4(pid, step, 0u, rel), a.ks);
-    float unused;
     box_muller(wd.x, wd.y, z.t0, z.t1);
-    box_muller(wd.z, wd.w, z.t2, unused);
+    box_muller(wd.z, wd.w, z.t2, z.m0);
 }
+// draw 1: the other two mesoscale normals
 __device__ __forceinline__ void draw_meso(const StepArgs& a, uint32_t pid, uint32_t step, uint32_t rel,
                                           Normals& z) {
     const uint4 wd = philox4x32_10_ks(make_uint4(pid, step, 1u, rel), a.ks);
-    float unused;
-    box_muller(wd.x, wd.y, z.m0, z.m1);
-    box_muller(wd.z, wd.w, z.m2, unused);
+    box_muller(wd.x, wd.y, z.m1, z.m2);
 }
 
 // Hand-off of one particle to the sort that follows the launch: its final
@@ -698,7 +698,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
             if (MODE != MODE_ADVECT && (use_turb || use_meso)) {
                 // ---- module_diffusion_turb / module_diffusion_meso ----
                 // at the position after advection: lat + ilat, p + ip
-                if (!EARLY_DRAWS && use_turb) draw_turb(a, pid, step, rel, z);
+                if (!EARLY_DRAWS && (use_turb || use_meso)) draw_turb(a, pid, step, rel, z);
                 if (!EARLY_DRAWS && use_meso) draw_meso(a, pid, step, rel, z);
                 float dxm = 0.f, dym = 0.f, dpp = 0.f;
                 if (use_turb) {
