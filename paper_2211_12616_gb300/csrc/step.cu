@@ -11,15 +11,17 @@
 //    stream costs ~60 B per launch, not per step;
 //  * positions are float64 in memory but carried as float-float pairs
 //    (hi + lo) in registers: GB300's float64 rate is a small fraction of its
-//    float32 rate, while a float-float add is six float32 adds;
-//  * met records are [lat][lon][level] x (u, v, omega, T): the two levels of a
-//    cell column are adjacent, so one evaluation touches 4 columns x 2 levels
-//    per snapshot, fetched with 16-byte (float32) or 8-byte (16-bit) loads
-//    through L1/L2; sorting particles by cell makes a warp's stencils overlap;
+//    float32 rate;
+//  * the 8 corners x 2 snapshots of a particle's current cell stay in
+//    registers (or shared memory) as packed float32x2 pairs and are gathered
+//    again only when the particle changes cell -- with one 32-byte load per
+//    corner from the interleaved pair records, [lat][lon][level] x (u, v,
+//    omega, T) x (slot 0, slot 1), whose registers are already the pairs;
 //  * random numbers are generated in registers (counter-based Philox): no
 //    random-number arrays are stored or read;
-//  * the longitude increments divide by cos(lat) with the fast division
-//    (2 ulp): 2e-7 relative on a 0.1-degree step, far inside the tolerance.
+//  * divisions and square roots that only scale increments use the hardware
+//    approximations (__fdividef: 2 ulp, sqrt.approx), far inside the
+//    tolerance.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -244,25 +246,29 @@ template <class S>
 __device__ __forceinline__ Cell locate(float lon, ff d, float p, const Geo& g, const S& s,
                                        int k_hint) {
     Cell c;
-    const float x = (lon - g.lon0) * g.inv_dlon;
+    // The longitude has been wrapped into [lon0, lon0 + 360), so x >= 0 and
+    // x - floor(x) is exact and in [0, 1]; i == nx (x rounded up to nx) wraps
+    // to 0, and the clamp keeps a NaN's index inside the grid.  Explicitly
+    // rounded operations: a multiply-subtract fused by the compiler in some
+    // instantiations only would make results depend on the launch variant.
+    const float x = __fmul_rn(__fsub_rn(lon, g.lon0), g.inv_dlon);
     const float xf = floorf(x);
     int i = (int)xf;
     if (i >= g.nx) i -= g.nx;
-    if (i < 0) i += g.nx;
     c.i = min(max(i, 0), g.nx - 1);
-    c.fx = clamp01(x - xf);
-    c.gx = 1.f - c.fx;
+    c.fx = __fsub_rn(x, xf);
+    c.gx = __fsub_rn(1.f, c.fx);
 
-    // y = d / dlat as float-float (yh + ye), d = lat - lat0
+    // y = d / dlat as float-float (yh + ye), d = lat - lat0; the row index is
+    // clamped as a float (exact small integers), which saves converting it back
     const float yh = d.hi * g.inv_dlat;
     float ye = fmaf(d.hi, g.inv_dlat, -yh);
     ye = fmaf(d.hi, g.inv_dlat_lo, ye);
     ye = fmaf(d.lo, g.inv_dlat, ye);
-    int j = (int)floorf(yh);
-    j = min(max(j, 0), g.ny - 2);
-    c.j = j;
-    c.fy = clamp01(__fadd_rn(__fsub_rn(yh, (float)j), ye));
-    c.gy = clamp01(__fsub_rn(__fsub_rn((float)(j + 1), yh), ye));
+    const float jf = fminf(fmaxf(floorf(yh), 0.f), (float)(g.ny - 2));
+    c.j = (int)jf;
+    c.fy = clamp01(__fadd_rn(__fsub_rn(yh, jf), ye));
+    c.gy = clamp01(__fsub_rn(__fsub_rn(jf + 1.f, yh), ye));
 
     const float pc = fminf(fmaxf(p, g.pmin), g.pmax);
     int k = k_hint;
@@ -285,8 +291,8 @@ struct Wind {
 
 // Pairs of float32 values in one 64-bit register, operated on by Blackwell's
 // packed float32x2 instructions (each lane rounds exactly like the scalar
-// instruction).  Lane 0 holds the earlier snapshot, lane 1 the later one, so
-// one instruction interpolates both snapshots.
+// instruction).  Lane s holds met slot s's snapshot, so one instruction
+// interpolates both snapshots; the time weights come per lane.
 typedef unsigned long long f2_t;
 
 __device__ __forceinline__ f2_t f2_pack(float a, float b) {
@@ -552,6 +558,15 @@ __device__ __forceinline__ void midpoint_bc(float& lon, ff& d, const Geo& g) {
     if (!(d.hi < g.dn && d.hi > g.ds && lon < g.lon1 && lon >= g.lon0)) midpoint_rules(lon, d, g);
 }
 
+// sqrt(x), x >= 0 (a weighted sum of squares), by the approximate square root
+// instruction.  Written as PTX so that every instantiation runs the same
+// instruction: results must not depend on the launch variant.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Gaussian draws of one step from counters (id, step, 0, release) and
 // (id, step, 1, release): their normals are used in order, turbulence taking
 // the first three of draw 0, mesoscale the fourth of draw 0 and the first two
@@ -707,9 +722,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
                     dpp = -(p.hi + ip) * (a.sv * z.t2) * a.inv_H;
                 }
                 if (use_meso) {
-                    up = fmaf(a.r_ar, up, a.a_ar * sqrtf(var.u) * z.m0);
-                    vp = fmaf(a.r_ar, vp, a.a_ar * sqrtf(var.v) * z.m1);
-                    wp = fmaf(a.r_ar, wp, a.a_ar * sqrtf(var.w) * z.m2);
+                    up = fmaf(a.r_ar, up, a.a_ar * sqrt_approx(var.u) * z.m0);
+                    vp = fmaf(a.r_ar, vp, a.a_ar * sqrt_approx(var.v) * z.m1);
+                    wp = fmaf(a.r_ar, wp, a.a_ar * sqrt_approx(var.w) * z.m2);
                     dxm += up * a.dt;
                     dym += vp * a.dt;
                     dpp += wp * a.dt;
