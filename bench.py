@@ -43,6 +43,21 @@ SEED_RNG = 2
 # after the kernel changes, until it is captured again.
 TRAFFIC_PER_LAUNCH = {1: 203547648,   # 169.9 MB read + 33.6 MB written, 1e6 particles
                       2: 157252352}   # 142.1 MB read + 15.1 MB written, 5e5 particles
+# sha256 (first 16 hex digits) of the fused step's sources when the counters
+# were taken; a different hash means the kernel changed and traffic is None
+TRAFFIC_KERNEL_SHA = "unset"
+TRAFFIC_SOURCES = ("paper_2211_12616_gb300/csrc/step.cu", "paper_2211_12616_gb300/csrc/internal.h",
+                   "paper_2211_12616_gb300/csrc/cell_key.cuh", "paper_2211_12616_gb300/csrc/met_record.cuh")
+
+
+def kernel_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    root = os.path.dirname(os.path.abspath(__file__))
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(root, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 METRIC = "particle-steps/s on 1 GB300 (advect+diffuse) and % gather roofline, surrogate vs plain"
 WORKLOAD = ("1deg 360x181x60 Fourier-mode wind, 4 snapshots 6h apart, 1e6 particles, dt=180s, 24h "
             "(480 fused advect+turb+meso steps), sort by met cell every 20 steps")
@@ -385,7 +400,9 @@ def run_ours(args, rank, world):
         "data": "synthetic", "config": _config(n, {"autotuned": best, "autotune_ms": tune_ms}),
         "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TOP/s",
                      "frac": alu_achieved / alu_peak,
-                     "traffic": TRAFFIC_PER_LAUNCH.get(n_groups) if best["variant"] == 2 else None,
+                     "traffic": (TRAFFIC_PER_LAUNCH.get(n_groups)
+                                 if best["variant"] == 2 and kernel_sha() == TRAFFIC_KERNEL_SHA else None),
+                     "kernel_sha": kernel_sha(),
                      "kernel": "k_transport<fp32, step>", "avg_launch_ms": step_avg_ms,
                      "launches_timed": len(step_ms), "particle_steps_per_launch": psteps_per_launch,
                      "timing": "union of the launch intervals (CUDA events on each group's stream) / launches",
