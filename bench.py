@@ -297,7 +297,7 @@ def run_ours(args, rank, world):
         tune_ms = {}
     else:
         best, tune_ms = autotune(make, lambda: work.copy_(init),
-                                 candidates(sort_every=(SORT_EVERY,), groups=groups_try), stream, repeats=1)
+                                 candidates(sort_every=(SORT_EVERY,), groups=groups_try), stream, repeats=3)
     ctx.set_launch(best["variant"], best["persistent"])
     sim = sim_for(best["groups"])
 

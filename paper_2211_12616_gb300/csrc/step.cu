@@ -62,6 +62,20 @@ __device__ __forceinline__ ff ff_add(ff a, float b) {
     lo = __fsub_rn(lo, __fsub_rn(hi, s));
     return {hi, lo};
 }
+
+// a + b for an increment b no larger than the value (|b| <= |a.hi|), the
+// step's case: the error of the hi sum by Fast2Sum (Dekker), exact under that
+// condition, then renormalised.  Where |b| > |a.hi| (a longitude just above
+// lon0, a latitude just above the south pole) the error term is off by at most
+// half an ulp of b, about 1e-9 degrees on a step's increment.
+__device__ __forceinline__ ff ff_add_inc(ff a, float b) {
+    const float s = __fadd_rn(a.hi, b);
+    const float e = __fsub_rn(b, __fsub_rn(s, a.hi));
+    float lo = __fadd_rn(a.lo, e);
+    const float hi = __fadd_rn(s, lo);
+    lo = __fsub_rn(lo, __fsub_rn(hi, s));
+    return {hi, lo};
+}
 __device__ __forceinline__ bool ff_less(ff a, float bh, float bl) {
     return a.hi < bh || (a.hi == bh && a.lo < bl);
 }
@@ -695,7 +709,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
                     eval_wind<ST, false>(a.mp, s, g, c1, wl0, wh0, cc, V, var);
                 const float cl = coslat(d, 0.f, g);
                 float lon_m = lon.hi + __fdividef(a.hk * V.u, cl);
-                ff d_m = ff_add(d, a.hk * V.v);
+                ff d_m = ff_add_inc(d, a.hk * V.v);
                 const float p_m = p.hi + a.half_dt * V.w;
                 midpoint_bc(lon_m, d_m, g);
                 const Cell c2 = locate(lon_m, d_m, p_m, g, s, cc.k);
@@ -734,9 +748,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
                 ilat += dym * a.kdeg;
                 ip += dpp;
             }
-            lon = ff_add(lon, ilon);
-            d = ff_add(d, ilat);
-            p = ff_add(p, ip);
+            lon = ff_add_inc(lon, ilon);
+            d = ff_add_inc(d, ilat);
+            p = ff_add_inc(p, ip);
             // ---- module_position ----
             position_bc(lon, d, p, g);
         }
