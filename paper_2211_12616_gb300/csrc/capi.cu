@@ -94,6 +94,28 @@ void free_ctx(mptrac_ctx* c) {
     delete c;
 }
 
+// Makes `dev` the calling thread's current device for the guard's lifetime and
+// then restores the caller's: an object's memory and kernels live on the
+// device it was created on, whatever device the caller has current.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        int cur = -1;
+        if (cudaGetDevice(&cur) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return;
+        }
+        if (cur == dev) return;
+        if (cudaSetDevice(dev) == cudaSuccess) prev = cur;
+        else (void)cudaGetLastError();
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard&) = delete;
+    DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
 int check_particles(const mptrac_particles* P, bool need_meso) {
     if (!P) return fail(MPTRAC_E_INVALID_ARG, "particles descriptor is NULL");
     if (P->n < 0 || P->n > 0x7FFFFFFF) return fail(MPTRAC_E_INVALID_ARG, "particle count %lld out of range [0, 2^31-1]", (long long)P->n);
@@ -139,6 +161,7 @@ int run_transport(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
                   const mptrac_diff_params* prm, uint64_t seed, uint64_t step0, int nsteps,
                   uintptr_t stream, int mode, const uint8_t* mask = nullptr, const SortEmit* emit = nullptr) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    DeviceGuard device_guard(c->device);
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(MPTRAC_E_INVALID_ARG, "dt must be finite and > 0 (got %g)", dt);
     if (!std::isfinite(t)) return fail(MPTRAC_E_INVALID_ARG, "t must be finite");
     if (nsteps < 0) return fail(MPTRAC_E_INVALID_ARG, "nsteps must be >= 0 (got %d)", nsteps);
@@ -366,6 +389,7 @@ int mptrac_init_grid(mptrac_ctx** out, const mptrac_grid_desc* g) {
 
 int mptrac_destroy(mptrac_ctx* ctx) {
     if (!ctx) return ok();
+    DeviceGuard device_guard(ctx->device);
     cudaError_t e = cudaDeviceSynchronize();
     free_ctx(ctx);
     if (e != cudaSuccess) {
@@ -380,6 +404,7 @@ const char* mptrac_last_error(const mptrac_ctx*) { return g_err; }
 int mptrac_load_met(mptrac_ctx* c, int slot, double t, const float* u, const float* v,
                     const float* omega, const float* T, int src_is_device, uintptr_t stream) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    DeviceGuard device_guard(c->device);
     if (slot != 0 && slot != 1) return fail(MPTRAC_E_INVALID_ARG, "slot must be 0 or 1 (got %d)", slot);
     if (!std::isfinite(t)) return fail(MPTRAC_E_INVALID_ARG, "t must be finite");
     if (!u || !v || !omega) return fail(MPTRAC_E_INVALID_ARG, "u, v and omega must not be NULL");
@@ -415,6 +440,7 @@ int mptrac_load_met(mptrac_ctx* c, int slot, double t, const float* u, const flo
 
 int mptrac_set_releases(mptrac_ctx* c, int n, const double* ts, const double* te) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    DeviceGuard device_guard(c->device);
     if (n < 0 || n > MPTRAC_MAX_RELEASES) return fail(MPTRAC_E_INVALID_ARG, "release count %d out of range", n);
     if (n > 0 && (!ts || !te)) return fail(MPTRAC_E_INVALID_ARG, "release times are NULL");
     for (int r = 0; r < n; ++r)
@@ -464,6 +490,7 @@ int mptrac_step_handoff(mptrac_ctx* c, const mptrac_particles* P, double t, doub
                         const mptrac_diff_params* prm, uint64_t seed, uint64_t step0, int nsteps, void* ws,
                         size_t ws_bytes, uintptr_t stream) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    DeviceGuard device_guard(c->device);
     if (nsteps < 1) return fail(MPTRAC_E_INVALID_ARG, "nsteps must be >= 1 for a hand-off (got %d)", nsteps);
     int rc = check_particles(P, false);
     if (rc) return rc;
@@ -477,6 +504,7 @@ int mptrac_step_handoff(mptrac_ctx* c, const mptrac_particles* P, double t, doub
 int mptrac_sort_handoff(mptrac_ctx* c, const mptrac_particles* P, void* ws, size_t ws_bytes,
                         uintptr_t stream) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    DeviceGuard device_guard(c->device);
     int rc = check_particles(P, false);
     if (rc) return rc;
     if (P->n == 0) return ok();
@@ -488,6 +516,7 @@ int mptrac_sort_handoff(mptrac_ctx* c, const mptrac_particles* P, void* ws, size
 int mptrac_step_sort(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
                      const mptrac_diff_params* prm, uint64_t seed, uint64_t step0, int nsteps, void* ws,
                      size_t ws_bytes, uintptr_t stream) {
+    if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
     if (nsteps == 0) {   // nothing to hand off: the arguments are checked, then a plain sort
         int rc = run_transport(c, P, t, dt, prm, seed, step0, nsteps, stream, MODE_STEP);
         return rc ? rc : mptrac_sort(c, P, ws, ws_bytes, stream);
@@ -503,6 +532,7 @@ size_t mptrac_sort_workspace_bytes(const mptrac_ctx*, int64_t n) {
 int mptrac_sort(mptrac_ctx* c, const mptrac_particles* P, void* ws, size_t ws_bytes,
                 uintptr_t stream) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    DeviceGuard device_guard(c->device);
     int rc = check_particles(P, false);
     if (rc) return rc;
     if (P->n == 0) return ok();
@@ -517,6 +547,7 @@ int mptrac_sort(mptrac_ctx* c, const mptrac_particles* P, void* ws, size_t ws_by
 int mptrac_sort_at(mptrac_ctx* c, const mptrac_particles* P, double t, void* ws, size_t ws_bytes,
                    uintptr_t stream) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    DeviceGuard device_guard(c->device);
     if (!std::isfinite(t)) return fail(MPTRAC_E_INVALID_ARG, "t must be finite");
     int rc = check_particles(P, false);
     if (rc) return rc;
@@ -536,6 +567,7 @@ int mptrac_sort_at(mptrac_ctx* c, const mptrac_particles* P, double t, void* ws,
 
 int mptrac_set_launch(mptrac_ctx* c, int variant, int persistent) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    DeviceGuard device_guard(c->device);
     if (variant < 0 || variant > 4) return fail(MPTRAC_E_INVALID_ARG, "launch variant must be 0..4 (got %d)", variant);
     c->launch_variant = variant;
     c->persistent = persistent != 0;
@@ -544,6 +576,7 @@ int mptrac_set_launch(mptrac_ctx* c, int variant, int persistent) {
 
 int mptrac_cell_keys(mptrac_ctx* c, const mptrac_particles* P, uint32_t* keys, uintptr_t stream) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    DeviceGuard device_guard(c->device);
     int rc = check_particles(P, false);
     if (rc) return rc;
     if (P->n == 0) return ok();
@@ -555,6 +588,7 @@ int mptrac_cell_keys(mptrac_ctx* c, const mptrac_particles* P, uint32_t* keys, u
 int mptrac_interp(mptrac_ctx* c, int64_t n, const double* lon, const double* lat, const double* p,
                   double t, float* ou, float* ov, float* ow, float* ovar, uintptr_t stream) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    DeviceGuard device_guard(c->device);
     if (n < 0 || n > 0x7FFFFFFF) return fail(MPTRAC_E_INVALID_ARG, "n out of range");
     int s0, s1, rc;
     if ((rc = ordered_slots(c, s0, s1))) return rc;
@@ -587,6 +621,7 @@ int mptrac_philox(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_t* out, 
 int mptrac_met_slot_info(const mptrac_ctx* c, int slot, const void** records, const float** scales,
                          double* t, size_t* bytes) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    DeviceGuard device_guard(c->device);
     if (slot != 0 && slot != 1) return fail(MPTRAC_E_INVALID_ARG, "slot must be 0 or 1");
     if (records) *records = c->d_met[slot];
     if (scales) *scales = c->d_scales[slot];
@@ -598,6 +633,7 @@ int mptrac_met_slot_info(const mptrac_ctx* c, int slot, const void** records, co
 int mptrac_met_slot_copy(const mptrac_ctx* c, int slot, void* rec_out, float* sc_out,
                          uintptr_t stream) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    DeviceGuard device_guard(c->device);
     if (slot != 0 && slot != 1) return fail(MPTRAC_E_INVALID_ARG, "slot must be 0 or 1");
     if (rec_out && !device_accessible(rec_out)) return fail(MPTRAC_E_INVALID_ARG, "records_out is not device memory");
     if (sc_out && !device_accessible(sc_out)) return fail(MPTRAC_E_INVALID_ARG, "scales_out is not device memory");
@@ -609,6 +645,7 @@ int mptrac_met_slot_copy(const mptrac_ctx* c, int slot, void* rec_out, float* sc
 
 int mptrac_sample_met(mptrac_ctx* c, const mptrac_particles* P, double t, float* out, uintptr_t stream) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    DeviceGuard device_guard(c->device);
     int rc = check_particles(P, false);
     if (rc) return rc;
     int s0, s1;
@@ -626,6 +663,7 @@ int mptrac_sample_met(mptrac_ctx* c, const mptrac_particles* P, double t, float*
 int mptrac_sediment(mptrac_ctx* c, const mptrac_particles* P, const float* radius, const float* density, double t,
                     double dt, int nsteps, uintptr_t stream) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    DeviceGuard device_guard(c->device);
     if (c->nvars != 4) return fail(MPTRAC_E_INVALID_ARG, "sedimentation needs temperature (nvars == 4)");
     if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(MPTRAC_E_INVALID_ARG, "bad dt or nsteps");
     int rc = check_particles(P, false);
@@ -647,6 +685,7 @@ int mptrac_sediment(mptrac_ctx* c, const mptrac_particles* P, const float* radiu
 
 int mptrac_grid_counts(mptrac_ctx* c, const mptrac_particles* P, uint32_t* counts, uintptr_t stream) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    DeviceGuard device_guard(c->device);
     int rc = check_particles(P, false);
     if (rc) return rc;
     if (!device_accessible(counts)) return fail(MPTRAC_E_INVALID_ARG, "counts must be device memory");
@@ -671,6 +710,7 @@ int mptrac_advect_masked(mptrac_ctx* c, const mptrac_particles* P, const uint8_t
 // ---------------------------------------------------------------------------
 struct mptrac_surr {
     mptrac::Surrogate S;
+    int device = 0;   // the device its buffers live on
 };
 
 extern "C" {
@@ -682,7 +722,8 @@ int mptrac_surr_create(mptrac_surr** out, int64_t max_batch) {
         return fail(MPTRAC_E_INVALID_ARG, "max_batch must be in [64, 4194304] (got %lld)", (long long)max_batch);
     mptrac_surr* s = new (std::nothrow) mptrac_surr();
     if (!s) return fail(MPTRAC_E_OOM, "host allocation failed");
-    cudaError_t e = surr_alloc(s->S, max_batch);
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = surr_alloc(s->S, max_batch);
     if (e == cudaSuccess) {
         // identity normalisation
         std::vector<float> one(MPTRAC_SURR_KPAD, 1.f);
@@ -703,6 +744,7 @@ int mptrac_surr_create(mptrac_surr** out, int64_t max_batch) {
 
 int mptrac_surr_destroy(mptrac_surr* s) {
     if (!s) return ok();
+    DeviceGuard device_guard(s->device);
     cudaDeviceSynchronize();
     surr_free(s->S);
     delete s;
@@ -711,6 +753,7 @@ int mptrac_surr_destroy(mptrac_surr* s) {
 
 int mptrac_surr_set_params(mptrac_surr* s, const float* params) {
     if (!s || !params) return fail(MPTRAC_E_INVALID_ARG, "NULL argument");
+    DeviceGuard device_guard_s(s->device);
     MPTRAC_CUDA(cudaMemcpy(s->S.theta, params, MPTRAC_SURR_NPARAM * 4, cudaMemcpyHostToDevice));
     MPTRAC_CUDA(cudaMemset(s->S.m, 0, MPTRAC_SURR_NPARAM * 4));
     MPTRAC_CUDA(cudaMemset(s->S.v, 0, MPTRAC_SURR_NPARAM * 4));
@@ -721,6 +764,7 @@ int mptrac_surr_set_params(mptrac_surr* s, const float* params) {
 
 int mptrac_surr_get_params(const mptrac_surr* s, float* params) {
     if (!s || !params) return fail(MPTRAC_E_INVALID_ARG, "NULL argument");
+    DeviceGuard device_guard_s(s->device);
     MPTRAC_CUDA(cudaDeviceSynchronize());
     MPTRAC_CUDA(cudaMemcpy(params, s->S.theta, MPTRAC_SURR_NPARAM * 4, cudaMemcpyDeviceToHost));
     return ok();
@@ -728,6 +772,7 @@ int mptrac_surr_get_params(const mptrac_surr* s, float* params) {
 
 int mptrac_surr_get_grads(const mptrac_surr* s, float* grads) {
     if (!s || !grads) return fail(MPTRAC_E_INVALID_ARG, "NULL argument");
+    DeviceGuard device_guard_s(s->device);
     MPTRAC_CUDA(cudaDeviceSynchronize());
     MPTRAC_CUDA(cudaMemcpy(grads, s->S.grad, MPTRAC_SURR_NPARAM * 4, cudaMemcpyDeviceToHost));
     return ok();
@@ -736,6 +781,7 @@ int mptrac_surr_get_grads(const mptrac_surr* s, float* grads) {
 int mptrac_surr_set_norm(mptrac_surr* s, const float* mu_x, const float* sd_x, const float* mu_y,
                          const float* sd_y) {
     if (!s || !mu_x || !sd_x || !mu_y || !sd_y) return fail(MPTRAC_E_INVALID_ARG, "NULL argument");
+    DeviceGuard device_guard_s(s->device);
     float mx[MPTRAC_SURR_KPAD], ix[MPTRAC_SURR_KPAD], my[8] = {0}, iy[8], sy[8];
     for (int c = 0; c < MPTRAC_SURR_KPAD; ++c) {
         const bool used = c < MPTRAC_SURR_NFEAT;
@@ -760,6 +806,7 @@ int mptrac_surr_set_norm(mptrac_surr* s, const float* mu_x, const float* sd_x, c
 
 int mptrac_surr_features(mptrac_ctx* c, const mptrac_particles* P, double t, float* feat, uintptr_t stream) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    DeviceGuard device_guard(c->device);
     int rc = check_particles(P, false);
     if (rc) return rc;
     if (c->nx < 3 || c->ny < 3 || c->nz < 3) return fail(MPTRAC_E_INVALID_ARG, "surrogate features need nx, ny, nz >= 3");
@@ -797,6 +844,7 @@ int mptrac_surr_colstats(const float* data, int64_t n, int ncol, double* sum, do
 
 int mptrac_surr_forward(mptrac_surr* s, const float* x, int64_t n, float* y_hat, uintptr_t stream) {
     if (!s) return fail(MPTRAC_E_NOT_INIT, "surrogate is NULL");
+    DeviceGuard device_guard_s(s->device);
     if (n < 0 || n > s->S.max_batch) return fail(MPTRAC_E_INVALID_ARG, "n must be in [0, max_batch]");
     if (n == 0) return ok();
     if (!device_accessible(x) || (y_hat && !device_accessible(y_hat)))
@@ -809,6 +857,7 @@ int mptrac_surr_forward(mptrac_surr* s, const float* x, int64_t n, float* y_hat,
 
 int mptrac_surr_grads(mptrac_surr* s, const float* x, const float* y, int64_t n, float* loss, uintptr_t stream) {
     if (!s) return fail(MPTRAC_E_NOT_INIT, "surrogate is NULL");
+    DeviceGuard device_guard_s(s->device);
     if (n <= 0 || n > s->S.max_batch) return fail(MPTRAC_E_INVALID_ARG, "n must be in [1, max_batch]");
     if (!device_accessible(x) || !device_accessible(y) || !device_accessible(loss))
         return fail(MPTRAC_E_INVALID_ARG, "x, y and loss must be device memory");
@@ -820,6 +869,8 @@ int mptrac_surr_grads(mptrac_surr* s, const float* x, const float* y, int64_t n,
 
 int mptrac_surr_train_step(mptrac_surr* s, const float* x, const float* y, int64_t n, float lr, int step,
                            float* loss, uintptr_t stream) {
+    if (!s) return fail(MPTRAC_E_NOT_INIT, "surrogate is NULL");
+    DeviceGuard device_guard_s(s->device);
     if (step < 1 || !(lr > 0.f)) return fail(MPTRAC_E_INVALID_ARG, "step must be >= 1 and lr > 0");
     int rc = mptrac_surr_grads(s, x, y, n, loss, stream);
     if (rc) return rc;
@@ -830,7 +881,10 @@ int mptrac_surr_train_step(mptrac_surr* s, const float* x, const float* y, int64
 int mptrac_surr_advance(mptrac_ctx* c, mptrac_surr* s, const mptrac_particles* P, double t, double dt_seg,
                         uint8_t* fallback, uintptr_t stream) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    DeviceGuard device_guard(c->device);
     if (!s) return fail(MPTRAC_E_NOT_INIT, "surrogate is NULL");
+    DeviceGuard device_guard_s(s->device);
+    if (s->device != c->device) return fail(MPTRAC_E_INVALID_ARG, "context and surrogate are on different devices");
     int rc = check_particles(P, false);
     if (rc) return rc;
     if (c->nx < 3 || c->ny < 3 || c->nz < 3) return fail(MPTRAC_E_INVALID_ARG, "surrogate needs nx, ny, nz >= 3");
@@ -908,6 +962,7 @@ int noalloc_scratch(void** out) {
 
 extern "C" int mptrac_sort_noalloc(mptrac_ctx* c, const mptrac_particles* P, uintptr_t stream) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
+    DeviceGuard device_guard(c->device);
     int rc = check_particles(P, false);
     if (rc) return rc;
     if (P->n > MPTRAC_SORT_NOALLOC_MAX_N)

@@ -26,6 +26,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 
 #include "cell_key.cuh"
@@ -36,6 +37,7 @@ namespace mptrac {
 namespace {
 
 constexpr float kCosFloor = 1.745329243e-05f;   // cos(89.999 deg)
+constexpr int kMaxDevices = 64;                  // per-device caches of the launchers
 
 // ---------------------------------------------------------------------------
 // float-float arithmetic (value = hi + lo, |lo| <= ulp(hi)/2)
@@ -980,17 +982,25 @@ int grid_for(int64_t n) {
 template <int ST, int MODE, int BLOCK, int MINB, int CACHE>
 cudaError_t launch_step_variant(const StepArgs& a, int grid, bool persistent, cudaStream_t s) {
     auto kern = k_transport<ST, MODE, BLOCK, MINB, CACHE>;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        (void)cudaGetLastError();
+        dev = 0;
+    }
     if (CACHE) {
-        static bool carveout_set = false;   // prefer the largest shared-memory carveout
-        if (!carveout_set) {
+        // prefer the largest shared-memory carveout (a per-device function attribute)
+        static std::atomic<int> carveout_set[kMaxDevices];
+        if (!carveout_set[dev].load(std::memory_order_relaxed)) {
             if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      cudaSharedmemCarveoutMaxShared) != cudaSuccess)
                 (void)cudaGetLastError();
-            carveout_set = true;
+            carveout_set[dev].store(1, std::memory_order_relaxed);
         }
     }
     if (persistent) {
-        static int per_sm = 0;   // resident blocks per SM of this instantiation (same on every GB300)
+        // resident blocks per SM of this instantiation, per device
+        static std::atomic<int> per_sm_cache[kMaxDevices];
+        int per_sm = per_sm_cache[dev].load(std::memory_order_relaxed);
         if (per_sm <= 0) {
             int v = 0;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, BLOCK, 0) != cudaSuccess) {
@@ -998,9 +1008,9 @@ cudaError_t launch_step_variant(const StepArgs& a, int grid, bool persistent, cu
                 v = MINB;
             }
             per_sm = v;
+            per_sm_cache[dev].store(v, std::memory_order_relaxed);
         }
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
+        int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int64_t need = (a.n + BLOCK - 1) / BLOCK;
         grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(per_sm, 1), need));
