@@ -11,6 +11,7 @@
  *   mptrac_step       ~ the fused chain advection -> turbulent -> mesoscale
  *                       diffusion -> position, as called in the time loop
  *   mptrac_sort       ~ the particle sorting modules                (Section 6)
+ *   mptrac_step_sort  ~ mptrac_step then mptrac_sort, fused through the sort workspace
  * The paper prints no formulas for any of these; the numerics implemented are:
  *   - 4D linear interpolation (lon periodic, lat clamped, linear in p between
  *     levels, linear in time between two snapshots);
@@ -18,10 +19,14 @@
  *     second stage with cos(lat) of the midpoint;
  *   - turbulent diffusion sqrt(2 D dt) xi (horizontal metres; vertical metres
  *     converted as dp = -p dz / H);
- *   - mesoscale AR(1) wind perturbation scaled by the time-weighted population
- *     standard deviation of the 8 cell-corner winds;
+ *   - mesoscale AR(1) wind perturbation scaled by the subgrid standard
+ *     deviation: on each snapshot the spread of the 8 cell-corner winds about
+ *     the interpolated wind, weighted by the interpolation weights, then
+ *     linear in time;
  *   - Philox4x32-10 (Salmon et al., SC'11) with counter
  *     (particle id, step, stream, release), key = seed, Box-Muller normals;
+ *     the normals of stream 0 then stream 1 are used in order (turbulence
+ *     z0..z2 of stream 0, mesoscale z3 of stream 0 and z0, z1 of stream 1);
  *   - lat reflected over the poles (lon + 180), lon wrapped into
  *     [lon0, lon0 + 360), p clamped to the level range.
  *
@@ -39,6 +44,9 @@
  *     device every call that launches work returns MPTRAC_E_CUDA.
  *   - A context is not thread-safe; calls on one context must be serialised
  *     by the caller (they may use different streams).
+ *   - A context (and a surrogate) lives on the device that was current when it
+ *     was created; every call on it makes that device current for its duration
+ *     and restores the caller's.  `stream` must belong to that device.
  */
 #ifndef MPTRAC_H
 #define MPTRAC_H
@@ -57,7 +65,7 @@ extern "C" {
 #define MPTRAC_E_CUDA         -3   /* a CUDA runtime call or launch failed */
 #define MPTRAC_E_TIME_RANGE   -4   /* [t, t + nsteps*dt] leaves the loaded snapshots */
 #define MPTRAC_E_WORKSPACE    -5   /* workspace pointer NULL, misaligned or too small */
-#define MPTRAC_E_TIMEOUT      -6   /* a bounded device-side wait gave up */
+#define MPTRAC_E_TIMEOUT      -6   /* reserved: a bounded device-side wait gave up (no call waits on the device) */
 #define MPTRAC_E_NOT_INIT     -7   /* context NULL, or met snapshots not loaded */
 
 /* ---- met storage precision -------------------------------------------- */
