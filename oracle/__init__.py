@@ -17,8 +17,11 @@ other.  Inputs come from the separate ``workloads`` package.
 Pinning status (what each function is checked against, other than itself):
 
 * ``philox``       -- Triton's Philox4x32 (interpreter mode, a third-party
-                      library) on CPU; cuRAND's device Philox4x32-10 on the GPU;
-                      Box-Muller output checked against the normal distribution.
+                      library) on CPU; counter-bit avalanche; Box-Muller output
+                      checked against the normal distribution.
+* ``meteo``, ``sedi`` -- trilinear fields reproduced exactly, count sums and hand
+                      cells; Sutherland's reference point, the Stokes and slip
+                      limits, textbook settling speeds.
 * ``met``          -- torch's bfloat16/float16 rounding; the half-ulp error bound;
                       hand-computed codes.
 * ``interp``       -- exact reproduction of fields that are trilinear in
