@@ -286,7 +286,7 @@ def run_ours(args, rank, world):
         def go():
             ctx.set_launch(cfg["variant"], cfg["persistent"])
             with torch.cuda.stream(stream):
-                sim_c.run(0.0, DT_MET, stream=stream)
+                sim_c.run(0.0, 2 * DT_MET, stream=stream)   # two intervals: one overlapped met load
         return go
 
     groups_try = (args.groups,) if args.groups else (1, 2, 3)

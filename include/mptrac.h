@@ -63,7 +63,7 @@ extern "C" {
 #define MPTRAC_E_INVALID_ARG  -1   /* a pointer, size or parameter is invalid */
 #define MPTRAC_E_OOM          -2   /* device allocation failed */
 #define MPTRAC_E_CUDA         -3   /* a CUDA runtime call or launch failed */
-#define MPTRAC_E_TIME_RANGE   -4   /* [t, t + nsteps*dt] leaves the loaded snapshots */
+#define MPTRAC_E_TIME_RANGE   -4   /* [t, t + nsteps*dt] lies in no interval of the loaded snapshots */
 #define MPTRAC_E_WORKSPACE    -5   /* workspace pointer NULL, misaligned or too small */
 #define MPTRAC_E_TIMEOUT      -6   /* reserved: a bounded device-side wait gave up (no call waits on the device) */
 #define MPTRAC_E_NOT_INIT     -7   /* context NULL, or met snapshots not loaded */
@@ -74,6 +74,7 @@ extern "C" {
 #define MPTRAC_FP16 2   /* 4 x float16 codes + per-(level,variable) power-of-two scale */
 
 #define MPTRAC_MAX_NZ        256   /* largest supported number of pressure levels */
+#define MPTRAC_NUM_SLOTS       3   /* met slots of a context */
 #define MPTRAC_MAX_RELEASES  65536 /* largest release table */
 
 typedef struct mptrac_ctx mptrac_ctx;   /* opaque: met slots, level tables, release table */
@@ -130,10 +131,12 @@ typedef struct {
     int turb, meso;
 } mptrac_diff_params;
 
-/* Creates a context for grid `g`: allocates two device met slots, their
- * interleaved copy (both slots' values of a grid point in one record, the
- * layout the particle kernels gather from; as large as the two slots) and the
- * level tables on the current CUDA device.  On success *out owns them until
+/* Creates a context for grid `g`: allocates MPTRAC_NUM_SLOTS (3) device met
+ * slots, their interleaved copies (for every pair of slots, both slots' values
+ * of a grid point in one record, the layout the particle kernels gather from;
+ * each as large as two slots) and the level tables on the current CUDA device.
+ * Two slots hold a met interval; the third lets the next snapshot be loaded
+ * while the current interval is being used.  On success *out owns them until
  * mptrac_destroy.  Errors: E_INVALID_ARG (bad grid), E_OOM, E_CUDA. */
 int mptrac_init_grid(mptrac_ctx** out, const mptrac_grid_desc* g);
 
@@ -143,7 +146,7 @@ int mptrac_destroy(mptrac_ctx* ctx);
 /* Message of the calling thread's most recent error ("" if none). `ctx` may be NULL. */
 const char* mptrac_last_error(const mptrac_ctx* ctx);
 
-/* Loads snapshot time `t` [s] into met slot `slot` (0 or 1)  -- read_met +
+/* Loads snapshot time `t` [s] into met slot `slot` (0, 1 or 2)  -- read_met +
  * update device (Sections 3.1, 4.1).  u, v, omega (and T when nvars == 4,
  * otherwise ignored) are float32 arrays of nz*ny*nx values in layout
  * [level][lat][lon], on the DEVICE if src_is_device != 0, else on the HOST (copied
@@ -152,8 +155,12 @@ const char* mptrac_last_error(const mptrac_ctx* ctx);
  * as records [lat][lon][level] x (u, v, omega, T) in the grid's storage
  * precision; reduced precision uses per-(level, variable) power-of-two scales
  * 2^(E-15), maxabs = m 2^E, m in [0.5, 1).  The same values are written to
- * this slot's lane of the interleaved copy.  The two loaded slots must have
- * different times; the earlier one is the interval start.
+ * this slot's lane of the interleaved copies it belongs to (never the copy of
+ * the other two slots, so a load does not disturb work in flight on them).
+ * Every call that interpolates in time uses the two loaded slots that are
+ * consecutive in time and whose interval contains its time range (the earlier
+ * one is the interval start): E_NOT_INIT if fewer than two slots with
+ * different times are loaded, E_TIME_RANGE if no such interval contains it.
  * Errors: E_INVALID_ARG, E_NOT_INIT, E_CUDA. */
 int mptrac_load_met(mptrac_ctx* ctx, int slot, double t,
                     const float* u, const float* v, const float* omega, const float* T,

@@ -216,7 +216,7 @@ class Particles:
 
 
 class Context:
-    """One grid + two met slots (``mptrac_init_grid``)."""
+    """One grid + three met slots (``mptrac_init_grid``)."""
 
     def __init__(self, grid, storage: int = MPTRAC_FP32, nvars: int = 3):
         lib = load()

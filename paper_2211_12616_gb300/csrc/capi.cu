@@ -15,6 +15,9 @@
 
 using namespace mptrac;
 
+constexpr int kSlots = MPTRAC_NUM_SLOTS;
+static_assert(kSlots == 3, "the pair buffers are indexed by a + b - 1");
+
 struct mptrac_ctx {
     int device = 0;
     int num_sms = 0;
@@ -25,11 +28,12 @@ struct mptrac_ctx {
     float* d_invdp = nullptr;
     int16_t* d_kguess = nullptr;
     double* d_plev_d = nullptr;
-    void* d_met[2] = {nullptr, nullptr};
-    void* d_pair = nullptr;            // both slots interleaved (lane = slot), read by the particle kernels
-    float* d_scales[2] = {nullptr, nullptr};
-    double t_slot[2] = {0.0, 0.0};
-    bool loaded[2] = {false, false};
+    void* d_met[kSlots] = {};
+    // slots a < b interleaved, lane 0 = slot a: d_pair[a + b - 1], read by the particle kernels
+    void* d_pair[kSlots] = {};
+    float* d_scales[kSlots] = {};
+    double t_slot[kSlots] = {};
+    bool loaded[kSlots] = {};
     size_t rec_bytes = 0;
     float* d_staging = nullptr;
     double* d_rel_ts = nullptr;
@@ -86,9 +90,9 @@ constexpr double kRadius = 6371000.0;
 constexpr double kPi = 3.14159265358979323846;
 
 void free_ctx(mptrac_ctx* c) {
-    void* ptrs[] = {c->d_plev, c->d_invdp, c->d_kguess, c->d_plev_d, c->d_met[0], c->d_met[1],
-                    c->d_pair, c->d_scales[0], c->d_scales[1], c->d_staging, c->d_rel_ts, c->d_rel_te,
-                    c->d_win};
+    void* ptrs[] = {c->d_plev, c->d_invdp, c->d_kguess, c->d_plev_d, c->d_met[0], c->d_met[1], c->d_met[2],
+                    c->d_pair[0], c->d_pair[1], c->d_pair[2], c->d_scales[0], c->d_scales[1], c->d_scales[2],
+                    c->d_staging, c->d_rel_ts, c->d_rel_te, c->d_win};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete c;
@@ -138,23 +142,49 @@ int check_particles(const mptrac_particles* P, bool need_meso) {
     return MPTRAC_OK;
 }
 
-int ordered_slots(const mptrac_ctx* c, int& a, int& b) {
-    if (!c->loaded[0] || !c->loaded[1])
-        return fail(MPTRAC_E_NOT_INIT, "both met slots must be loaded (slot0 %s, slot1 %s)",
-                    c->loaded[0] ? "loaded" : "empty", c->loaded[1] ? "loaded" : "empty");
-    if (c->t_slot[0] == c->t_slot[1])
-        return fail(MPTRAC_E_NOT_INIT, "met slots hold the same time %g", c->t_slot[0]);
-    a = c->t_slot[0] < c->t_slot[1] ? 0 : 1;
-    b = 1 - a;
-    return MPTRAC_OK;
+// The two loaded slots, consecutive in time, whose interval [t0, t1] contains
+// [tb, te] (to 1e-9 of the interval): s0 the earlier.  E_NOT_INIT without two
+// loaded slots of different times, E_TIME_RANGE when no interval contains it.
+int bracket_slots(const mptrac_ctx* c, double tb, double te, int& s0, int& s1) {
+    int idx[kSlots], m = 0;
+    for (int q = 0; q < kSlots; ++q)
+        if (c->loaded[q]) idx[m++] = q;
+    for (int a = 1; a < m; ++a)   // insertion sort by time
+        for (int b = a; b > 0 && c->t_slot[idx[b]] < c->t_slot[idx[b - 1]]; --b) std::swap(idx[b], idx[b - 1]);
+    bool interval = false;
+    for (int q = 0; q + 1 < m; ++q) {
+        const double t0 = c->t_slot[idx[q]], t1 = c->t_slot[idx[q + 1]];
+        if (!(t1 > t0)) continue;
+        interval = true;
+        const double tol = 1e-9 * (t1 - t0);
+        if (tb >= t0 - tol && te <= t1 + tol) {
+            s0 = idx[q];
+            s1 = idx[q + 1];
+            return MPTRAC_OK;
+        }
+    }
+    if (!interval)
+        return fail(MPTRAC_E_NOT_INIT, "two met slots with different times must be loaded (%d loaded)", m);
+    return fail(MPTRAC_E_TIME_RANGE, "[%.9g, %.9g] lies in no interval of the loaded snapshots", tb, te);
 }
 
-// Time weights of the pair lanes (slot 0, slot 1) for the time fraction w
-// between the earlier snapshot (slot s_early) and the later one.
-void lane_weights(int s_early, double w, float& lane0, float& lane1) {
+// The pair buffer of slots s and o, and the lane slot s has in it.
+void* pair_buffer(const mptrac_ctx* c, int s, int o) { return c->d_pair[std::min(s, o) + std::max(s, o) - 1]; }
+int pair_lane(int s, int o) { return s < o ? 0 : 1; }
+
+// The interleaved records of slots s0 and s1 (lane 0 = the lower slot index)
+// and the lane weights for time fraction w from the earlier slot s0 to s1.
+MetPair pair_of(const mptrac_ctx* c, int s0, int s1) {
+    const int a = std::min(s0, s1), b = std::max(s0, s1);
+    return MetPair{c->d_pair[a + b - 1], {c->d_scales[a], c->d_scales[b]}};
+}
+
+// Time weights of the pair lanes for the time fraction w from the earlier
+// slot s0 to the later slot s1 (lane 0 holds the lower slot index).
+void lane_weights(int s0, int s1, double w, float& lane0, float& lane1) {
     const float early = (float)(1.0 - w), late = (float)w;
-    lane0 = s_early == 0 ? early : late;
-    lane1 = s_early == 0 ? late : early;
+    lane0 = s0 < s1 ? early : late;
+    lane1 = s0 < s1 ? late : early;
 }
 
 int run_transport(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
@@ -178,12 +208,9 @@ int run_transport(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
     int rc = check_particles(P, meso);
     if (rc) return rc;
     int s0, s1;
-    if ((rc = ordered_slots(c, s0, s1))) return rc;
-    const double t0 = c->t_slot[s0], t1 = c->t_slot[s1];
     const double tend = t + (double)nsteps * dt;
-    const double tol = 1e-9 * (t1 - t0);
-    if (t < t0 - tol || tend > t1 + tol)
-        return fail(MPTRAC_E_TIME_RANGE, "[%.9g, %.9g] leaves the loaded snapshots [%.9g, %.9g]", t, tend, t0, t1);
+    if ((rc = bracket_slots(c, t, tend, s0, s1))) return rc;
+    const double t0 = c->t_slot[s0], t1 = c->t_slot[s1];
     if (P->n == 0 || nsteps == 0) return ok();
     // the fused step with both diffusion terms off is exactly the advection kernel
     if (mode == MODE_STEP && !turb && !meso) mode = MODE_ADVECT;
@@ -192,7 +219,7 @@ int run_transport(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
     StepArgs a;
     memset(&a, 0, sizeof(a));
     a.geo = c->geo;
-    a.mp = MetPair{c->d_pair, {c->d_scales[0], c->d_scales[1]}};
+    a.mp = pair_of(c, s0, s1);
     a.n = P->n;
     a.lon = P->lon;
     a.lat = P->lat;
@@ -239,8 +266,8 @@ int run_transport(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
         a.step0 = step0 + (uint64_t)n0;
         for (int q = 0; q < cnt; ++q) {
             const double tn = t + (double)(n0 + q) * dt;
-            lane_weights(s0, (tn - t0) / (t1 - t0), a.wt[4 * q], a.wt[4 * q + 1]);
-            lane_weights(s0, (tn + 0.5 * dt - t0) / (t1 - t0), a.wt[4 * q + 2], a.wt[4 * q + 3]);
+            lane_weights(s0, s1, (tn - t0) / (t1 - t0), a.wt[4 * q], a.wt[4 * q + 1]);
+            lane_weights(s0, s1, (tn + 0.5 * dt - t0) / (t1 - t0), a.wt[4 * q + 2], a.wt[4 * q + 3]);
         }
         if (use_win) MPTRAC_CUDA(launch_windows(c->d_rel_ts, c->d_rel_te, c->n_rel, t, dt, n0, cnt, c->d_win, st));
         // the last launch hands its results to the sort, if one follows
@@ -327,14 +354,14 @@ int mptrac_init_grid(mptrac_ctx** out, const mptrac_grid_desc* g) {
     if (!rc) rc = alloc((void**)&c->d_invdp, nz * sizeof(float));
     if (!rc) rc = alloc((void**)&c->d_kguess, nbins * sizeof(int16_t));
     if (!rc) rc = alloc((void**)&c->d_plev_d, nz * sizeof(double));
-    for (int s = 0; s < 2 && !rc; ++s) {
+    for (int s = 0; s < kSlots && !rc; ++s) {
         rc = alloc(&c->d_met[s], c->rec_bytes);
         if (!rc) rc = alloc((void**)&c->d_scales[s], 4 * nz * sizeof(float));
-    }
-    if (!rc) rc = alloc(&c->d_pair, 2 * c->rec_bytes);
-    if (!rc && cudaMemset(c->d_pair, 0, 2 * c->rec_bytes) != cudaSuccess) {
-        (void)cudaGetLastError();
-        rc = fail(MPTRAC_E_CUDA, "clearing the pair records failed");
+        if (!rc) rc = alloc(&c->d_pair[s], 2 * c->rec_bytes);
+        if (!rc && cudaMemset(c->d_pair[s], 0, 2 * c->rec_bytes) != cudaSuccess) {
+            (void)cudaGetLastError();
+            rc = fail(MPTRAC_E_CUDA, "clearing the pair records failed");
+        }
     }
     if (rc) {
         free_ctx(c);
@@ -405,7 +432,7 @@ int mptrac_load_met(mptrac_ctx* c, int slot, double t, const float* u, const flo
                     const float* omega, const float* T, int src_is_device, uintptr_t stream) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
     DeviceGuard device_guard(c->device);
-    if (slot != 0 && slot != 1) return fail(MPTRAC_E_INVALID_ARG, "slot must be 0 or 1 (got %d)", slot);
+    if (slot < 0 || slot >= kSlots) return fail(MPTRAC_E_INVALID_ARG, "slot must be 0, 1 or 2 (got %d)", slot);
     if (!std::isfinite(t)) return fail(MPTRAC_E_INVALID_ARG, "t must be finite");
     if (!u || !v || !omega) return fail(MPTRAC_E_INVALID_ARG, "u, v and omega must not be NULL");
     if (c->nvars == 4 && !T) return fail(MPTRAC_E_INVALID_ARG, "T must not be NULL when nvars == 4");
@@ -432,7 +459,9 @@ int mptrac_load_met(mptrac_ctx* c, int slot, double t, const float* u, const flo
         }
     }
     MPTRAC_CUDA(launch_pack(c->storage, c->nvars, src[0], src[1], src[2], src[3], c->nx, c->ny, c->nz,
-                            c->d_met[slot], c->d_scales[slot], c->d_pair, slot, st));
+                            c->d_met[slot], c->d_scales[slot], pair_buffer(c, slot, (slot + 1) % kSlots),
+                            pair_lane(slot, (slot + 1) % kSlots), pair_buffer(c, slot, (slot + 2) % kSlots),
+                            pair_lane(slot, (slot + 2) % kSlots), st));
     c->t_slot[slot] = t;
     c->loaded[slot] = true;
     return ok();
@@ -591,18 +620,17 @@ int mptrac_interp(mptrac_ctx* c, int64_t n, const double* lon, const double* lat
     DeviceGuard device_guard(c->device);
     if (n < 0 || n > 0x7FFFFFFF) return fail(MPTRAC_E_INVALID_ARG, "n out of range");
     int s0, s1, rc;
-    if ((rc = ordered_slots(c, s0, s1))) return rc;
+    if ((rc = bracket_slots(c, t, t, s0, s1))) return rc;
     if (n == 0) return ok();
     const void* ptrs[] = {lon, lat, p, ou, ov, ow};
     for (const void* q : ptrs)
         if (!device_accessible(q)) return fail(MPTRAC_E_INVALID_ARG, "interp arrays must be device memory");
     if (ovar && !device_accessible(ovar)) return fail(MPTRAC_E_INVALID_ARG, "out_var is not device memory");
     const double t0 = c->t_slot[s0], t1 = c->t_slot[s1];
-    if (!(t >= t0 && t <= t1)) return fail(MPTRAC_E_TIME_RANGE, "t = %g outside [%g, %g]", t, t0, t1);
     float wl0, wl1;
-    lane_weights(s0, (t - t0) / (t1 - t0), wl0, wl1);
-    MPTRAC_CUDA(launch_interp(c->storage, c->geo, MetPair{c->d_pair, {c->d_scales[0], c->d_scales[1]}}, wl0,
-                              wl1, n, lon, lat, p, ou, ov, ow, ovar, reinterpret_cast<cudaStream_t>(stream)));
+    lane_weights(s0, s1, (t - t0) / (t1 - t0), wl0, wl1);
+    MPTRAC_CUDA(launch_interp(c->storage, c->geo, pair_of(c, s0, s1), wl0, wl1, n, lon, lat, p, ou, ov, ow, ovar,
+                              reinterpret_cast<cudaStream_t>(stream)));
     return ok();
 }
 
@@ -622,7 +650,7 @@ int mptrac_met_slot_info(const mptrac_ctx* c, int slot, const void** records, co
                          double* t, size_t* bytes) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
     DeviceGuard device_guard(c->device);
-    if (slot != 0 && slot != 1) return fail(MPTRAC_E_INVALID_ARG, "slot must be 0 or 1");
+    if (slot < 0 || slot >= kSlots) return fail(MPTRAC_E_INVALID_ARG, "slot must be 0, 1 or 2");
     if (records) *records = c->d_met[slot];
     if (scales) *scales = c->d_scales[slot];
     if (t) *t = c->t_slot[slot];
@@ -634,7 +662,7 @@ int mptrac_met_slot_copy(const mptrac_ctx* c, int slot, void* rec_out, float* sc
                          uintptr_t stream) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
     DeviceGuard device_guard(c->device);
-    if (slot != 0 && slot != 1) return fail(MPTRAC_E_INVALID_ARG, "slot must be 0 or 1");
+    if (slot < 0 || slot >= kSlots) return fail(MPTRAC_E_INVALID_ARG, "slot must be 0, 1 or 2");
     if (rec_out && !device_accessible(rec_out)) return fail(MPTRAC_E_INVALID_ARG, "records_out is not device memory");
     if (sc_out && !device_accessible(sc_out)) return fail(MPTRAC_E_INVALID_ARG, "scales_out is not device memory");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -649,9 +677,8 @@ int mptrac_sample_met(mptrac_ctx* c, const mptrac_particles* P, double t, float*
     int rc = check_particles(P, false);
     if (rc) return rc;
     int s0, s1;
-    if ((rc = ordered_slots(c, s0, s1))) return rc;
+    if ((rc = bracket_slots(c, t, t, s0, s1))) return rc;
     const double t0 = c->t_slot[s0], t1 = c->t_slot[s1];
-    if (!(t >= t0 && t <= t1)) return fail(MPTRAC_E_TIME_RANGE, "t = %g outside [%g, %g]", t, t0, t1);
     if (P->n == 0) return ok();
     if (!device_accessible(out)) return fail(MPTRAC_E_INVALID_ARG, "out must be device memory");
     MPTRAC_CUDA(launch_sample(c->storage, c->geo, MetView{c->d_met[s0], c->d_scales[s0]},
@@ -669,10 +696,8 @@ int mptrac_sediment(mptrac_ctx* c, const mptrac_particles* P, const float* radiu
     int rc = check_particles(P, false);
     if (rc) return rc;
     int s0, s1;
-    if ((rc = ordered_slots(c, s0, s1))) return rc;
+    if ((rc = bracket_slots(c, t, t + nsteps * dt, s0, s1))) return rc;
     const double t0 = c->t_slot[s0], t1 = c->t_slot[s1];
-    const double tol = 1e-9 * (t1 - t0);
-    if (t < t0 - tol || t + nsteps * dt > t1 + tol) return fail(MPTRAC_E_TIME_RANGE, "sedimentation steps leave the loaded snapshots");
     if (P->n == 0 || nsteps == 0) return ok();
     if (!device_accessible(radius) || !device_accessible(density))
         return fail(MPTRAC_E_INVALID_ARG, "radius and density must be device memory");
@@ -811,9 +836,8 @@ int mptrac_surr_features(mptrac_ctx* c, const mptrac_particles* P, double t, flo
     if (rc) return rc;
     if (c->nx < 3 || c->ny < 3 || c->nz < 3) return fail(MPTRAC_E_INVALID_ARG, "surrogate features need nx, ny, nz >= 3");
     int s0, s1;
-    if ((rc = ordered_slots(c, s0, s1))) return rc;
+    if ((rc = bracket_slots(c, t, t, s0, s1))) return rc;
     const double t0 = c->t_slot[s0], t1 = c->t_slot[s1];
-    if (!(t >= t0 && t <= t1)) return fail(MPTRAC_E_TIME_RANGE, "t = %g outside [%g, %g]", t, t0, t1);
     if (P->n == 0) return ok();
     if (!device_accessible(feat)) return fail(MPTRAC_E_INVALID_ARG, "feat must be device memory");
     MPTRAC_CUDA(launch_surr_features(c->storage, c->geo, MetView{c->d_met[s0], c->d_scales[s0]},
@@ -889,9 +913,8 @@ int mptrac_surr_advance(mptrac_ctx* c, mptrac_surr* s, const mptrac_particles* P
     if (rc) return rc;
     if (c->nx < 3 || c->ny < 3 || c->nz < 3) return fail(MPTRAC_E_INVALID_ARG, "surrogate needs nx, ny, nz >= 3");
     int s0, s1;
-    if ((rc = ordered_slots(c, s0, s1))) return rc;
+    if ((rc = bracket_slots(c, t, t, s0, s1))) return rc;
     const double t0 = c->t_slot[s0], t1 = c->t_slot[s1];
-    if (!(t >= t0 && t <= t1)) return fail(MPTRAC_E_TIME_RANGE, "t = %g outside [%g, %g]", t, t0, t1);
     if (!(dt_seg > 0)) return fail(MPTRAC_E_INVALID_ARG, "dt_seg must be > 0");
     if (P->n == 0) return ok();
     if (!device_accessible(fallback)) return fail(MPTRAC_E_INVALID_ARG, "fallback must be device memory");

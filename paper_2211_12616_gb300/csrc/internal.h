@@ -128,11 +128,12 @@ cudaError_t launch_grid_counts(const Geo& g, int64_t n, const double* lon, const
 cudaError_t launch_philox(const uint32_t* ctr, int64_t n, uint32_t k0, uint32_t k1, uint32_t* out,
                           float* normals, cudaStream_t s);
 
-// Packs one snapshot into slot records `rec` (+ scales) and into lane `slot`
-// of the interleaved pair records `pairs`.
+// Packs one snapshot into slot records `rec` (+ scales) and into lane lane0
+// of the interleaved pair records pairs0 and lane lane1 of pairs1 (the two
+// slot pairs the slot belongs to).
 cudaError_t launch_pack(int storage, int nvars, const float* u, const float* v, const float* w,
-                        const float* T, int nx, int ny, int nz, void* rec, float* scales, void* pairs,
-                        int slot, cudaStream_t s);
+                        const float* T, int nx, int ny, int nz, void* rec, float* scales, void* pairs0,
+                        int lane0, void* pairs1, int lane1, cudaStream_t s);
 
 size_t sort_workspace_bytes(int64_t n);
 cudaError_t launch_cell_keys(const Geo& g, int64_t n, const double* lon, const double* lat,

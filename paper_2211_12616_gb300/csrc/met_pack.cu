@@ -9,8 +9,9 @@
 //
 // The transpose goes through shared memory in tiles of 32 longitudes x 32
 // levels: reads are 128-byte rows of one level, writes are runs of 32
-// consecutive records.  The same values go to lane `slot` of the interleaved
-// pair records that the particle kernels read (both slots per grid point).
+// consecutive records.  The same values go to this slot's lane of the
+// interleaved pair records that the particle kernels read (two slots per grid
+// point), in both pair buffers the slot belongs to.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -62,7 +63,8 @@ template <int ST>
 __global__ void __launch_bounds__(256) k_pack(const float* __restrict__ u, const float* __restrict__ v,
                                               const float* __restrict__ w, const float* __restrict__ T,
                                               int nx, int ny, int nz, void* recv,
-                                              const float* __restrict__ scales, void* pairs, int slot) {
+                                              const float* __restrict__ scales, void* pairs0, int lane0,
+                                              void* pairs1, int lane1) {
     __shared__ float tile[4][kTile][kTile + 1];   // [var][level][lon]
     const int i0 = blockIdx.x * kTile, j = blockIdx.y, k0 = blockIdx.z * kTile;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -89,34 +91,42 @@ __global__ void __launch_bounds__(256) k_pack(const float* __restrict__ u, const
         const int i = i0 + il, k = k0 + kl;
         if (i >= nx || k >= nz) continue;
         const int64_t r = ((int64_t)j * nx + i) * nz + k;
-        // the pair record is rewritten whole (read, replace this slot's lane,
+        // each pair record is rewritten whole (read, replace this slot's lane,
         // write): full-sector accesses instead of four scattered partial ones
         if (ST == MPTRAC_FP32) {
             static_cast<float4*>(recv)[r] =
                 make_float4(tile[0][kl][il], tile[1][kl][il], tile[2][kl][il], tile[3][kl][il]);
-            float4* pr = static_cast<float4*>(pairs) + 2 * r;
-            float4 lo = pr[0], hi = pr[1];   // (u0, u1, v0, v1), (w0, w1, T0, T1)
-            if (slot == 0) {
-                lo.x = tile[0][kl][il]; lo.z = tile[1][kl][il]; hi.x = tile[2][kl][il]; hi.z = tile[3][kl][il];
-            } else {
-                lo.y = tile[0][kl][il]; lo.w = tile[1][kl][il]; hi.y = tile[2][kl][il]; hi.w = tile[3][kl][il];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                float4* pr = static_cast<float4*>(q ? pairs1 : pairs0) + 2 * r;
+                const int lane = q ? lane1 : lane0;
+                float4 lo = pr[0], hi = pr[1];   // (u0, u1, v0, v1), (w0, w1, T0, T1)
+                if (lane == 0) {
+                    lo.x = tile[0][kl][il]; lo.z = tile[1][kl][il]; hi.x = tile[2][kl][il]; hi.z = tile[3][kl][il];
+                } else {
+                    lo.y = tile[0][kl][il]; lo.w = tile[1][kl][il]; hi.y = tile[2][kl][il]; hi.w = tile[3][kl][il];
+                }
+                pr[0] = lo;
+                pr[1] = hi;
             }
-            pr[0] = lo;
-            pr[1] = hi;
         } else {
             uint32_t c[4];
 #pragma unroll
             for (int var = 0; var < 4; ++var) c[var] = code16(tile[var][kl][il], ST);
             static_cast<uint2*>(recv)[r] = make_uint2(c[0] | (c[1] << 16), c[2] | (c[3] << 16));
-            uint4* pr = static_cast<uint4*>(pairs) + r;   // words (u, v, omega, T), slot 0 in the low half
-            uint4 q = *pr;
-            const uint32_t keep = slot == 0 ? 0xFFFF0000u : 0x0000FFFFu;
-            const int sh = slot == 0 ? 0 : 16;
-            q.x = (q.x & keep) | (c[0] << sh);
-            q.y = (q.y & keep) | (c[1] << sh);
-            q.z = (q.z & keep) | (c[2] << sh);
-            q.w = (q.w & keep) | (c[3] << sh);
-            *pr = q;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                uint4* pr = static_cast<uint4*>(q ? pairs1 : pairs0) + r;   // words (u, v, omega, T), lane 0 low
+                const int lane = q ? lane1 : lane0;
+                uint4 w4 = *pr;
+                const uint32_t keep = lane == 0 ? 0xFFFF0000u : 0x0000FFFFu;
+                const int sh = lane == 0 ? 0 : 16;
+                w4.x = (w4.x & keep) | (c[0] << sh);
+                w4.y = (w4.y & keep) | (c[1] << sh);
+                w4.z = (w4.z & keep) | (c[2] << sh);
+                w4.w = (w4.w & keep) | (c[3] << sh);
+                *pr = w4;
+            }
         }
     }
 }
@@ -129,8 +139,8 @@ __global__ void k_fill(float* p, int n, float v) {
 }  // namespace
 
 cudaError_t launch_pack(int storage, int nvars, const float* u, const float* v, const float* w,
-                        const float* T, int nx, int ny, int nz, void* rec, float* scales, void* pairs,
-                        int slot, cudaStream_t s) {
+                        const float* T, int nx, int ny, int nz, void* rec, float* scales, void* pairs0,
+                        int lane0, void* pairs1, int lane1, cudaStream_t s) {
     if (nvars < 4) T = nullptr;
     const int64_t plane = (int64_t)nx * ny;
     note_launches(2);
@@ -143,9 +153,9 @@ cudaError_t launch_pack(int storage, int nvars, const float* u, const float* v, 
     if (e != cudaSuccess) return e;
     const dim3 grid((nx + kTile - 1) / kTile, ny, (nz + kTile - 1) / kTile), block(kTile, 8);
     switch (storage) {
-        case MPTRAC_FP32: k_pack<MPTRAC_FP32><<<grid, block, 0, s>>>(u, v, w, T, nx, ny, nz, rec, scales, pairs, slot); break;
-        case MPTRAC_BF16: k_pack<MPTRAC_BF16><<<grid, block, 0, s>>>(u, v, w, T, nx, ny, nz, rec, scales, pairs, slot); break;
-        default: k_pack<MPTRAC_FP16><<<grid, block, 0, s>>>(u, v, w, T, nx, ny, nz, rec, scales, pairs, slot); break;
+        case MPTRAC_FP32: k_pack<MPTRAC_FP32><<<grid, block, 0, s>>>(u, v, w, T, nx, ny, nz, rec, scales, pairs0, lane0, pairs1, lane1); break;
+        case MPTRAC_BF16: k_pack<MPTRAC_BF16><<<grid, block, 0, s>>>(u, v, w, T, nx, ny, nz, rec, scales, pairs0, lane0, pairs1, lane1); break;
+        default: k_pack<MPTRAC_FP16><<<grid, block, 0, s>>>(u, v, w, T, nx, ny, nz, rec, scales, pairs0, lane0, pairs1, lane1); break;
     }
     return cudaGetLastError();
 }

@@ -17,7 +17,10 @@ partly filled wave of its step kernel then overlap with the other groups'
 steps.  A particle's trajectory does not depend on the other particles or on
 their order (counter-based random numbers keyed by particle id), so the
 results are those of G = 1 up to the order of the particles in memory.
-The groups join before every met load, which overwrites a slot they read.
+The met snapshots live in a ring of the context's three slots (snapshot k of
+the run in slot k mod 3): the snapshot an interval two ahead needs is loaded
+on a stream of its own as soon as every group has finished the interval that
+last read the slot it replaces, so loads overlap with the steps.
 
 Snapshots that ``snapshot_at`` returns in host memory (pinned, for the copies
 to overlap) are prefetched: right after an interval's loads, the snapshot the
@@ -50,6 +53,7 @@ class Simulation:
                            for v in self.groups] if sort else [None] * g
         self.workspace = self.workspaces[0]
         self._streams = None
+        self._load_stream = None
         self._pf = None           # host-snapshot prefetch state (copy stream, device buffers, events)
         self.step_hook = None     # called around every mptrac_step: hook(stage, stream)
 
@@ -81,17 +85,20 @@ class Simulation:
         ev.record(cs)
         pf["ready"][t] = (b, ev)
 
-    def _load(self, slot, t, main):
+    def _load(self, ctx, slot, t, stream):
+        """Loads the snapshot at time t into ``slot`` on ``stream`` (from its prefetched device copy
+        if there is one).  Host snapshots without a prefetch go through the context's staging
+        buffer, so the caller keeps such loads on one stream at a time."""
         pf = self._pf
         if pf is not None and t in pf["ready"]:
             b, ev = pf["ready"].pop(t)
-            main.wait_event(ev)
-            self.ctx.load_met(slot, t, *pf["bufs"][b], stream=main)
+            stream.wait_event(ev)
+            ctx.load_met(slot, t, *pf["bufs"][b], stream=stream)
             used = torch.cuda.Event()
-            used.record(main)
+            used.record(stream)
             pf["used"][b] = used
         else:
-            self.ctx.load_met(slot, t, *self.snapshot_at(t), stream=main)
+            ctx.load_met(slot, t, *self.snapshot_at(t), stream=stream)
 
     def _group_streams(self, main):
         """(step streams, sort streams): one of each per group; with one group both are ``main``.
@@ -116,29 +123,37 @@ class Simulation:
         if abs(steps_per_iv * self.dt - self.dt_met) > 1e-9 * self.dt_met:
             raise ValueError("the met interval must be a whole number of steps")
         n_iv = int(round((t_end - t_start) / self.dt_met))
-        ctx, slots = self.ctx, {}
-        main = stream if stream is not None else torch.cuda.current_stream(self.parts.lon.device)
+        ctx = self.ctx
+        dev = self.parts.lon.device
+        main = stream if stream is not None else torch.cuda.current_stream(dev)
         gstreams, sstreams = self._group_streams(main)
+        if self._load_stream is None:
+            self._load_stream = torch.cuda.Stream(device=dev)
+        ls = self._load_stream
+        T = lambda k: t_start + k * self.dt_met          # snapshot k of the run, in slot k % 3
+        loaded = {}                                      # snapshot k -> event after its load
+        if n_iv == 0:
+            return 0
+        # snapshots 0 and 1 in stream order; snapshot 2 (a free slot) on the load stream
+        for k in (0, 1):
+            self._load(ctx, k % 3, T(k), main)
+        ls.wait_stream(main)
+        if n_iv >= 2:
+            self._load(ctx, 2, T(2), ls)
+            loaded[2] = torch.cuda.Event()
+            loaded[2].record(ls)
+        for gs in gstreams:
+            if gs is not main:
+                gs.wait_stream(main)
         step = 0
         sorted_ = False           # particles already sorted by the previous block
         for iv in range(n_iv):
-            ta = t_start + iv * self.dt_met
-            tb = ta + self.dt_met
-            for gs in gstreams:          # the groups finish with the slots before they change
-                if gs is not main:
-                    main.wait_stream(gs)
-            for t, keep in ((ta, tb), (tb, ta)):
-                if t in slots.values():
-                    continue
-                free = [q for q in (0, 1) if q not in slots]
-                slot = free[0] if free else (0 if slots[0] != keep else 1)
-                self._load(slot, t, main)
-                slots[slot] = t
-            if iv + 1 < n_iv:
-                self._prefetch(tb + self.dt_met)   # overlaps with this interval's steps
-            for gs in gstreams:
-                if gs is not main:
-                    gs.wait_stream(main)
+            ta = T(iv)
+            if iv + 1 in loaded:  # the interval's later snapshot came from the load stream
+                for gs in gstreams:
+                    gs.wait_event(loaded[iv + 1])
+            if iv + 3 <= n_iv:
+                self._prefetch(T(iv + 3))        # host snapshots: copied during this interval
             done = 0
             while done < steps_per_iv:
                 cnt = min(self.sort_every, steps_per_iv - done)
@@ -169,9 +184,17 @@ class Simulation:
                 sorted_ = self.do_sort
                 done += cnt
                 step += cnt
+            if iv + 3 <= n_iv:
+                # snapshot iv + 3 replaces snapshot iv, whose last reader was this interval
+                for gs in gstreams:
+                    ls.wait_stream(gs)
+                self._load(ctx, (iv + 3) % 3, T(iv + 3), ls)
+                loaded[iv + 3] = torch.cuda.Event()
+                loaded[iv + 3].record(ls)
         for gs in gstreams:
             if gs is not main:
                 main.wait_stream(gs)
+        main.wait_stream(ls)
         return step
 
 

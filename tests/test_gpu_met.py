@@ -63,10 +63,11 @@ def test_load_met_errors(M):
     grid = grid_2deg_20lev()
     ctx = M.Context(grid)
     u = torch.zeros(grid.nz, grid.ny, grid.nx, device="cuda")
-    with pytest.raises(M.MptracError) as e:
-        ctx.load_met(2, 0.0, u, u, u)
-    assert e.value.code == -1
-    # stepping before both slots are loaded
+    for bad in (3, -1):   # three slots: 0, 1, 2
+        with pytest.raises(M.MptracError) as e:
+            ctx.load_met(bad, 0.0, u, u, u)
+        assert e.value.code == -1
+    # stepping before two slots are loaded
     ctx.load_met(0, 0.0, u, u, u)
     parts = M.Particles.from_numpy({"lon": np.zeros(4), "lat": np.zeros(4), "p": np.full(4, 5e4),
                                     "id": np.arange(4, dtype=np.uint32)})
