@@ -564,10 +564,17 @@ def run_precision(args, rank, world):
         b.record(stream)
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / args.steps
+        # module_meteo: u, v, omega, T sampled at the final positions (this storage's
+        # 12 h snapshots are still loaded)
+        with torch.cuda.stream(stream):
+            sampled = ctx.sample_met(work, PREC_T_END, stream=stream)
+        torch.cuda.synchronize()
+        sampled = sampled.cpu().numpy()
         got = work.to_numpy()
         pos = np.empty(n, dtype=np.int64)
         pos[got["id"]] = np.arange(n)
         finals[name] = {k: got[k][pos[sub_ids]] for k in ("lon", "lat", "p")}
+        finals[name]["sampled"] = sampled[:, pos[sub_ids]]
         results[name] = {"ms_per_pass": ms, "particle_steps_per_s": psteps / (ms / 1000.0),
                          "slot_bytes": int(grid.npoints * (16 if storage == M.MPTRAC_FP32 else 8))}
         ctx.close()
@@ -575,20 +582,28 @@ def run_precision(args, rank, world):
         torch.cuda.empty_cache()
     # float64 oracle on the subset, from the float32 fields (the stored-value error of
     # bf16/fp16 plus the float32 arithmetic of every storage)
-    host = [{k: v.cpu().numpy() for k, v in s.items() if k in ("u", "v", "w")} for s in snaps]
+    host = [{k: v.cpu().numpy() for k, v in s.items() if k in ("u", "v", "w", "T")} for s in snaps]
     del snaps
     torch.cuda.empty_cache()
     sub = {k: v[sub_ids] for k, v in st0.items()}
     t0 = time.perf_counter()
-    ref = run_schedule(grid, lambda t: host[int(round(t / DT_MET))], DT_MET, sub, 0.0, PREC_T_END, DT,
-                       tr.DiffParams(), SEED_RNG)
+    ref = run_schedule(grid, lambda t: {k: host[int(round(t / DT_MET))][k] for k in ("u", "v", "w")}, DT_MET,
+                       sub, 0.0, PREC_T_END, DT, tr.DiffParams(), SEED_RNG)
     oracle_s = time.perf_counter() - t0
+    from oracle import meteo
     for name, fin in finals.items():
         km = great_circle_km(fin["lon"], fin["lat"], ref["lon"], ref["lat"])
         dp = np.abs(fin["p"] - ref["p"]) / ref["p"]
         results[name].update({"km_median": float(np.median(km)), "km_p99": float(np.quantile(km, 0.99)),
                               "km_max": float(km.max()), "dp_rel_median": float(np.median(dp)),
                               "dp_rel_p99": float(np.quantile(dp, 0.99))})
+        # sampled met at this run's own final positions vs the float64 sampling of the
+        # float32 fields there: the storage's and the interpolation's error alone
+        ms_ = meteo.sample(grid, host[1], DT_MET, host[2], 2 * DT_MET, PREC_T_END, fin["lon"], fin["lat"], fin["p"])
+        for q, var in enumerate(("u", "v", "w", "T")):
+            err = np.abs(fin["sampled"][q] - ms_[var])
+            results[name][f"sampled_{var}_abs_median"] = float(np.median(err))
+            results[name][f"sampled_{var}_abs_p99"] = float(np.quantile(err, 0.99))
         results[name]["speedup_vs_fp32"] = results["fp32"]["ms_per_pass"] / results[name]["ms_per_pass"]
     line = {"metric": METRIC, "value": results["bf16"]["particle_steps_per_s"], "unit": "particle-steps/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
