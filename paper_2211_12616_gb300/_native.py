@@ -100,6 +100,8 @@ SIGNATURES = {
                                          C.c_void_p, C.c_void_p]),
     "mptrac_surr_advance": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(ParticlesDesc), C.c_double, C.c_double,
                                       C.c_void_p, C.c_void_p]),
+    "mptrac_surr_set_kernel": (C.c_int, [C.c_void_p, C.c_int]),
+    "mptrac_surr_status": (C.c_int, [C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -371,6 +373,7 @@ def philox(ctr: torch.Tensor, seed: int, with_normals: bool = False, stream=None
 # learned surrogate
 # ---------------------------------------------------------------------------
 SURR_NFEAT, SURR_KPAD, SURR_HIDDEN, SURR_NOUT, SURR_NPARAM = 168, 176, 128, 3, 39555
+SURR_KERNEL_TCGEN05, SURR_KERNEL_MMA_SYNC, SURR_KERNEL_WAIT_TEST = 0, 1, 2
 
 
 class Surrogate:
@@ -432,6 +435,14 @@ class Surrogate:
     def advance(self, ctx: "Context", parts: "Particles", t, dt_seg, fallback: torch.Tensor, stream=None):
         check(load().mptrac_surr_advance(ctx.h, self.h, C.byref(parts.desc()), float(t), float(dt_seg),
                                          _ptr(fallback), _stream(stream)), ctx.h)
+
+    def set_kernel(self, kernel: int):
+        """SURR_KERNEL_TCGEN05 (default) or SURR_KERNEL_MMA_SYNC for the fused inference."""
+        check(load().mptrac_surr_set_kernel(self.h, int(kernel)))
+
+    def status(self, stream=None):
+        """Synchronises the stream; raises MptracError (E_TIMEOUT) if a fused inference gave up a wait."""
+        check(load().mptrac_surr_status(self.h, _stream(stream)))
 
 
 def surr_features(ctx: "Context", parts: "Particles", t, out: torch.Tensor | None = None, stream=None):

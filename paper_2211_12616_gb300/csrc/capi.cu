@@ -927,6 +927,30 @@ int mptrac_surr_advance(mptrac_ctx* c, mptrac_surr* s, const mptrac_particles* P
     return ok();
 }
 
+int mptrac_surr_set_kernel(mptrac_surr* s, int kernel) {
+    if (!s) return fail(MPTRAC_E_NOT_INIT, "surrogate is NULL");
+    if (kernel != MPTRAC_SURR_KERNEL_TCGEN05 && kernel != MPTRAC_SURR_KERNEL_MMA_SYNC &&
+        kernel != MPTRAC_SURR_KERNEL_WAIT_TEST)
+        return fail(MPTRAC_E_INVALID_ARG, "unknown surrogate kernel %d", kernel);
+    s->S.kernel = kernel;
+    return ok();
+}
+
+int mptrac_surr_status(mptrac_surr* s, uintptr_t stream) {
+    if (!s) return fail(MPTRAC_E_NOT_INIT, "surrogate is NULL");
+    DeviceGuard device_guard_s(s->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int flag = 0;
+    MPTRAC_CUDA(cudaMemcpyAsync(&flag, s->S.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MPTRAC_CUDA(cudaStreamSynchronize(st));
+    if (flag) {
+        MPTRAC_CUDA(cudaMemsetAsync(s->S.status, 0, sizeof(int), st));
+        MPTRAC_CUDA(cudaStreamSynchronize(st));
+        return fail(MPTRAC_E_TIMEOUT, "a bounded wait of the fused surrogate inference gave up");
+    }
+    return ok();
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

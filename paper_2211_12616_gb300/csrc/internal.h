@@ -160,6 +160,8 @@ struct Surrogate {
     float *Z1 = nullptr, *Z2 = nullptr, *Yh = nullptr, *Xraw = nullptr;
     uint8_t* env = nullptr;
     float* loss_tmp = nullptr;
+    int* status = nullptr;       // set by a fused-inference kernel whose bounded wait gave up
+    int kernel = MPTRAC_SURR_KERNEL_TCGEN05;
 };
 
 

@@ -229,7 +229,6 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, fl
 // ---------------------------------------------------------------------------
 // Met record access
 // ---------------------------------------------------------------------------
-template <typename T> __device__ __forceinline__ T ldg_rec(const T* p) { return __ldg(p); }
 
 // Shared-memory tables of one block.  NSC = kMaxNZ holds the scales of
 // 16-bit storage; float32 storage needs none (NSC = 1, unused).

@@ -6,8 +6,11 @@
 // Network (per sample): x_hat = (x - mu_x)/sd_x (176 = 168 features + 8 zero
 // pad), z1 = x_hat W1 + b1, h1 = gelu(z1), z2 = h1 W2 + b2, h2 = gelu(z2),
 // y_hat = h2 W3 + b3 (3 outputs, padded to 8 columns), y = y_hat sd_y + mu_y.
-// GEMM operands are bfloat16 with float32 accumulation (mma.sync m16n8k16);
-// biases, GELU, the loss and Adam run in float32 on float32 master weights.
+// GEMM operands are bfloat16 with float32 accumulation: the fused inference
+// runs its layers on the 5th-generation tensor cores (tcgen05.mma, operands
+// in shared memory, accumulators in tensor memory); the training GEMMs and a
+// comparison inference kernel use the warp-level mma.sync m16n8k16.  Biases,
+// GELU, the loss and Adam run in float32 on float32 master weights.
 #include <cmath>
 #include <cstring>
 
@@ -170,10 +173,6 @@ struct GemmArgs {
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float x) {
     return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
 __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
@@ -382,44 +381,14 @@ struct FusedArgs {
     const __nv_bfloat16 *W1b, *W2b, *W3b;
     const float *b1, *b2, *b3p, *mu_x, *isd_x, *mu_y, *sd_y;
     double lon0, pmin, pmax;
+    int* status;            // set to 1 when a bounded wait of the tcgen05 kernel gives up
+    long long wait_cycles;  // limit of each wait for the tensor cores (SM clock cycles)
+    int withhold_mma;       // test hook: issue no MMA (nothing completes, the wait runs out)
 };
 
 constexpr size_t kFusedSmem = (size_t)HID * XS * 2 + (size_t)HID * HS * 2 + (size_t)NOP * HS * 2 +
                               (size_t)(2 * HID + NOP) * 4 + (size_t)2 * KP * 4 + (size_t)FT * XS * 2 +
                               (size_t)FT * HS * 2 + (size_t)FT * NOP * 4 + FT * 4 + (size_t)kMaxNZ * 4;
-
-// nearest node (float64, the definition) and the offsets from it
-__device__ __forceinline__ void nearest_node(const Geo& g, double lon, double lat, double p, int& i0, int& j0,
-                                             int& k0, double& ox, double& oy, double& oz) {
-    double r = fmod(lon - g.lon0_d, 360.0);
-    if (r < 0.0) r += 360.0;
-    const double x = r / g.dlon_d;
-    const double xr = floor(x + 0.5);
-    long long ii = (long long)xr % g.nx;
-    if (ii < 0) ii += g.nx;
-    const double y = (lat - g.lat0_d) / g.dlat_d;
-    long long jj = (long long)floor(y + 0.5);
-    jj = jj < 1 ? 1 : (jj > g.ny - 2 ? g.ny - 2 : jj);
-    const double pc = fmin(fmax(p, g.pmin_d), g.pmax_d);
-    int lo = 0, hi = g.nz;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (g.plev_d[mid] >= pc) lo = mid + 1; else hi = mid;
-    }
-    int k = lo - 1;
-    k = k < 0 ? 0 : (k > g.nz - 2 ? g.nz - 2 : k);
-    double fz = (g.plev_d[k] - pc) / (g.plev_d[k] - g.plev_d[k + 1]);
-    fz = fmin(fmax(fz, 0.0), 1.0);
-    const double z = k + fz;
-    long long kk = (long long)floor(z + 0.5);
-    kk = kk < 1 ? 1 : (kk > g.nz - 2 ? g.nz - 2 : kk);
-    i0 = (int)ii;
-    j0 = (int)jj;
-    k0 = (int)kk;
-    ox = x - xr;
-    oy = y - (double)jj;
-    oz = z - (double)kk;
-}
 
 // Nearest node in float32 (latitude in float-float): used by the fused
 // inference, where a different choice within ~1e-6 cells of a half-cell
@@ -457,6 +426,98 @@ __device__ __forceinline__ void nearest_node_f32(const Geo& g, const float* plev
     ox = x - xr;
     oy = y - (float)jj;
     oz = z - (float)kk;
+}
+
+// The predicted displacement of particle q (normalised outputs y0..y2) followed
+// by the position rules, or the fallback flag outside the envelope.
+__device__ __forceinline__ void apply_displacement(const FusedArgs& a, int64_t q, int env_ok, float y0,
+                                                   float y1, float y2) {
+    const double la = a.lat[q];
+    const bool ok = a.window_ok && env_ok && fabs(la) <= 80.0;
+    a.fallback[q] = ok ? 0 : 1;
+    if (!ok) return;
+    const float dx = y0 * a.sd_y[0] + a.mu_y[0];
+    const float dy = y1 * a.sd_y[1] + a.mu_y[1];
+    const float dz = y2 * a.sd_y[2] + a.mu_y[2];
+    const float cl = cospif((float)la * (1.0f / 180.0f));
+    double lo = a.lon[q] + (double)(dx / ((float)kR * cl) * (float)(180.0 / kPi));
+    double lt = la + (double)(dy * (float)(180.0 / (kPi * kR)));
+    const double pp = a.p[q] * (double)expf(dz);
+    if (lt > 90.0) { lt = 180.0 - lt; lo += 180.0; }
+    else if (lt < -90.0) { lt = -180.0 - lt; lo += 180.0; }
+    if (lo >= a.lon0 + 360.0) lo -= 360.0;
+    if (lo < a.lon0) lo += 360.0;
+    a.lon[q] = lo;
+    a.lat[q] = lt;
+    a.p[q] = fmin(fmax(pp, a.pmin), a.pmax);
+}
+
+// Gather and standardisation of one tile: thread = (particle pl, snapshot sn)
+// reads the 27 stencil records of its snapshot and stores the standardised
+// bf16 features through xs(row, column, value); env[row] = every standardised
+// feature within +-4 (rows past n: zero features, env 0).
+template <int ST, class XStore>
+__device__ __forceinline__ void gather_standardise(const FusedArgs& a, const float* plevs, const float* mu,
+                                                   const float* isd, int64_t tile, int tid, XStore xs, int* env) {
+    const Geo& g = a.g;
+    using R = typename RecT<ST>::T;
+    const int pl = tid >> 1, sn = tid & 1;
+    const int64_t q = tile * FT + pl;
+    float mx = 0.f;
+    if (q < a.n) {
+        int i0, j0, k0;
+        float ox, oy, oz;
+        const double lat = a.lat[q];
+        nearest_node_f32(g, plevs, a.lon[q], lat, a.p[q], i0, j0, k0, ox, oy, oz);
+        const R* rec = static_cast<const R*>(sn ? a.m1.rec : a.m0.rec);
+        const float* sc = sn ? a.m1.scales : a.m0.scales;
+        int im = i0 - 1, ip = i0 + 1;
+        if (im < 0) im += g.nx;
+        if (ip >= g.nx) ip -= g.nx;
+        const int icol[3] = {im, i0, ip};
+        R r[27];
+#pragma unroll
+        for (int c = 0; c < 27; ++c) {
+            const int dk = c / 9 - 1, dj = (c / 3) % 3 - 1, di = c % 3;
+            r[c] = __ldg(rec + ((int64_t)(j0 + dj) * g.nx + icol[di]) * g.nz + (k0 + dk));
+        }
+#pragma unroll
+        for (int c = 0; c < 27; ++c) {
+            float4 v = decode<ST>(r[c]);
+            if (ST != MPTRAC_FP32) {
+                const int kk = k0 + c / 9 - 1;
+                v.x *= sc[kk];
+                v.y *= sc[g.nz + kk];
+                v.z *= sc[2 * g.nz + kk];
+            }
+            const int c0 = sn * 81 + c;
+            const float xu = (v.x - mu[c0]) * isd[c0];
+            const float xv = (v.y - mu[c0 + 27]) * isd[c0 + 27];
+            const float xw = (v.z - mu[c0 + 54]) * isd[c0 + 54];
+            mx = fmaxf(mx, fmaxf(fabsf(xu), fmaxf(fabsf(xv), fabsf(xw))));
+            xs(pl, c0, __float2bfloat16_rn(xu));
+            xs(pl, c0 + 27, __float2bfloat16_rn(xv));
+            xs(pl, c0 + 54, __float2bfloat16_rn(xw));
+        }
+        if (sn == 0) {
+            float snl, csl;
+            sincospif((float)lat * (1.0f / 180.0f), &snl, &csl);
+            const float ex[6] = {ox, oy, oz, a.w, snl, csl};
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const float xe = (ex[c] - mu[162 + c]) * isd[162 + c];
+                mx = fmaxf(mx, fabsf(xe));
+                xs(pl, 162 + c, __float2bfloat16_rn(xe));
+            }
+#pragma unroll
+            for (int c = NF; c < KP; ++c) xs(pl, c, __float2bfloat16(0.f));
+        }
+    } else {
+        for (int c = sn; c < KP; c += 2) xs(pl, c, __float2bfloat16(0.f));
+        mx = 1e30f;
+    }
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+    if (sn == 0) env[pl] = (mx <= 4.f) ? 1 : 0;
 }
 
 template <int ST>
@@ -497,72 +558,11 @@ __global__ void __launch_bounds__(256, 1) k_surr_fused(const FusedArgs a) {
         isd[e] = a.isd_x[e];
     }
     __syncthreads();
-    const Geo& g = a.g;
-    using R = typename RecT<ST>::T;
     const int lane = tid & 31, warp = tid >> 5, gq = lane >> 2, tq = lane & 3;
     const int64_t ntiles = (a.n + FT - 1) / FT;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        // ---- gather and standardise: thread = (particle pl, snapshot sn) ----
-        {
-            const int pl = tid >> 1, sn = tid & 1;
-            const int64_t q = tile * FT + pl;
-            __nv_bfloat16* xr = Xs + pl * XS;
-            float mx = 0.f;
-            if (q < a.n) {
-                int i0, j0, k0;
-                float ox, oy, oz;
-                const double lat = a.lat[q];
-                nearest_node_f32(g, plevs, a.lon[q], lat, a.p[q], i0, j0, k0, ox, oy, oz);
-                const R* rec = static_cast<const R*>(sn ? a.m1.rec : a.m0.rec);
-                const float* sc = sn ? a.m1.scales : a.m0.scales;
-                int im = i0 - 1, ip = i0 + 1;
-                if (im < 0) im += g.nx;
-                if (ip >= g.nx) ip -= g.nx;
-                const int icol[3] = {im, i0, ip};
-                R r[27];
-#pragma unroll
-                for (int c = 0; c < 27; ++c) {
-                    const int dk = c / 9 - 1, dj = (c / 3) % 3 - 1, di = c % 3;
-                    r[c] = __ldg(rec + ((int64_t)(j0 + dj) * g.nx + icol[di]) * g.nz + (k0 + dk));
-                }
-#pragma unroll
-                for (int c = 0; c < 27; ++c) {
-                    float4 v = decode<ST>(r[c]);
-                    if (ST != MPTRAC_FP32) {
-                        const int kk = k0 + c / 9 - 1;
-                        v.x *= sc[kk];
-                        v.y *= sc[g.nz + kk];
-                        v.z *= sc[2 * g.nz + kk];
-                    }
-                    const int c0 = sn * 81 + c;
-                    const float xu = (v.x - mu[c0]) * isd[c0];
-                    const float xv = (v.y - mu[c0 + 27]) * isd[c0 + 27];
-                    const float xw = (v.z - mu[c0 + 54]) * isd[c0 + 54];
-                    mx = fmaxf(mx, fmaxf(fabsf(xu), fmaxf(fabsf(xv), fabsf(xw))));
-                    xr[c0] = __float2bfloat16_rn(xu);
-                    xr[c0 + 27] = __float2bfloat16_rn(xv);
-                    xr[c0 + 54] = __float2bfloat16_rn(xw);
-                }
-                if (sn == 0) {
-                    float snl, csl;
-                    sincospif((float)lat * (1.0f / 180.0f), &snl, &csl);
-                    const float ex[6] = {ox, oy, oz, a.w, snl, csl};
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) {
-                        const float xe = (ex[c] - mu[162 + c]) * isd[162 + c];
-                        mx = fmaxf(mx, fabsf(xe));
-                        xr[162 + c] = __float2bfloat16_rn(xe);
-                    }
-#pragma unroll
-                    for (int c = NF; c < KP; ++c) xr[c] = __float2bfloat16(0.f);
-                }
-            } else {
-                for (int c = sn; c < KP; c += 2) xr[c] = __float2bfloat16(0.f);
-                mx = 1e30f;
-            }
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-            if (sn == 0) env[pl] = (mx <= 4.f) ? 1 : 0;
-        }
+        gather_standardise<ST>(a, plevs, mu, isd, tile, tid,
+                               [&](int r, int c, __nv_bfloat16 v) { Xs[r * XS + c] = v; }, env);
         __syncthreads();
         // ---- MLP: warp owns rows r0 .. r0+15 ----
         const int r0 = warp * 16;
@@ -641,29 +641,271 @@ __global__ void __launch_bounds__(256, 1) k_surr_fused(const FusedArgs a) {
         // ---- apply the displacement (or flag the particle for the fallback) ----
         if (tid < FT) {
             const int64_t q = tile * FT + tid;
-            if (q < a.n) {
-                const double la = a.lat[q];
-                const bool ok = a.window_ok && env[tid] && fabs(la) <= 80.0;
-                a.fallback[q] = ok ? 0 : 1;
-                if (ok) {
-                    const float dx = Ys[tid * NOP + 0] * a.sd_y[0] + a.mu_y[0];
-                    const float dy = Ys[tid * NOP + 1] * a.sd_y[1] + a.mu_y[1];
-                    const float dz = Ys[tid * NOP + 2] * a.sd_y[2] + a.mu_y[2];
-                    const float cl = cospif((float)la * (1.0f / 180.0f));
-                    double lo = a.lon[q] + (double)(dx / ((float)kR * cl) * (float)(180.0 / kPi));
-                    double lt = la + (double)(dy * (float)(180.0 / (kPi * kR)));
-                    const double pp = a.p[q] * (double)expf(dz);
-                    if (lt > 90.0) { lt = 180.0 - lt; lo += 180.0; }
-                    else if (lt < -90.0) { lt = -180.0 - lt; lo += 180.0; }
-                    if (lo >= a.lon0 + 360.0) lo -= 360.0;
-                    if (lo < a.lon0) lo += 360.0;
-                    a.lon[q] = lo;
-                    a.lat[q] = lt;
-                    a.p[q] = fmin(fmax(pp, a.pmin), a.pmax);
-                }
-            }
+            if (q < a.n) apply_displacement(a, q, env[tid], Ys[tid * NOP + 0], Ys[tid * NOP + 1], Ys[tid * NOP + 2]);
         }
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused inference on the 5th-generation tensor cores.  Same gather and
+// standardisation; then each layer of the 128-particle tile is one chain of
+// tcgen05.mma (M = 128 particles; N = 128, 128, 16; K = 176, 128, 128 in steps
+// of 16) issued by one thread, with both operands in shared memory in the
+// K-major core-matrix layout without swizzle and the accumulator in tensor
+// memory.  The epilogues read the accumulators with tcgen05.ld (warp w reads
+// the 32 lanes 32 (w mod 4) + 0..31, half of the columns each), add the bias,
+// apply GELU and write the next layer's operand.  Every wait for the MMA
+// completion is bounded in time; when one gives up the kernel sets *status,
+// stops, frees its tensor memory and returns.
+// ---------------------------------------------------------------------------
+constexpr int KG1 = KP / 8, KG2 = HID / 8;   // core-matrix columns of the K = 176 and K = 128 operands
+constexpr int NW3 = 16;                      // layer 3: the 3 outputs padded to N = 16
+constexpr uint32_t kTmemCols = 256;          // layer 1 in columns 0..127, layer 2 in 128..255, layer 3 in 0..15
+constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at the SM clock
+constexpr long long kTestWaitCycles = 20000000LL;  // ~10 ms: the wait test hook
+
+constexpr size_t kTcW1 = (size_t)HID * KP * 2, kTcW2 = (size_t)HID * HID * 2, kTcW3 = (size_t)NW3 * HID * 2,
+                 kTcX = (size_t)FT * KP * 2, kTcH = (size_t)FT * HID * 2;
+constexpr size_t kTcSmem = kTcW1 + kTcW2 + kTcW3 + kTcX + kTcH + (size_t)(2 * HID + NOP) * 4 +
+                           (size_t)2 * KP * 4 + (size_t)FT * 4 + (size_t)kMaxNZ * 4 + 16;
+static_assert(kTcW1 % 128 == 0 && kTcW2 % 128 == 0 && kTcW3 % 128 == 0 && kTcX % 128 == 0 && kTcH % 128 == 0,
+              "operand blocks keep 128-byte alignment");
+static_assert(kTcSmem <= 227 * 1024, "shared memory of the tcgen05 inference kernel");
+
+// Byte offset of element (row r, column k) of a bf16 operand stored as 8 x 8
+// core matrices of 128 contiguous bytes (8 rows of 16 bytes), core matrix
+// (r / 8, k / 8) at ((r / 8) kg + k / 8) 128: the K-direction core matrices of
+// a row group are adjacent (128 bytes apart), row groups kg * 128 bytes apart.
+__device__ __forceinline__ uint32_t cm_off(int r, int k, int kg) {
+    return (uint32_t)(((((r >> 3) * kg) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start address, leading-dimension byte
+// offset (between the core matrices adjacent in K), stride-dimension byte
+// offset (between adjacent 8-row groups), all in 16-byte units; descriptor
+// version 1; no swizzle, base offset 0.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: float32 accumulator, bf16 A and B, both
+// K-major, N / 8 and M / 16.
+__host__ __device__ constexpr uint32_t umma_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// One layer: D (tensor memory) = A (M x K) * B^T (B stored N x K), K in steps
+// of 16 = two core matrices along K (128 bytes apart; row groups kg * 128).
+__device__ __forceinline__ void umma_layer(uint32_t d_tmem, uint32_t a_addr, uint32_t b_addr, int ksteps, int kg,
+                                           uint32_t idesc) {
+    const uint32_t lbo = 128u, sbo = (uint32_t)kg * 128u;
+    for (int ks = 0; ks < ksteps; ++ks)
+        umma_f16(d_tmem, umma_desc(a_addr + 256u * ks, lbo, sbo), umma_desc(b_addr + 256u * ks, lbo, sbo), idesc,
+                 ks > 0 ? 1u : 0u);
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy shared-memory writes made visible to the tensor cores
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Waits for phase `phase` of the mbarrier, for at most `limit` SM cycles; false when it gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, long long limit) {
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+
+// 16 consecutive float32 accumulator columns of this thread's lane.  The wait
+// names the registers, so that no use of them is scheduled before it.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3])::"memory");
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Epilogue of layers 1 and 2: accumulator columns [c0, c0 + 64) of this
+// thread's row + bias, GELU, bf16, into the next layer's A operand.
+__device__ __forceinline__ void tc_epilogue_gelu(uint32_t taddr, int row, int c0, const float* bias,
+                                                 unsigned char* Hs) {
+#pragma unroll 1
+    for (int ch = 0; ch < 4; ++ch) {
+        const int c = c0 + 16 * ch;
+        float v[16];
+        tmem_ld16(taddr + (uint32_t)c, v);
+        uint32_t pk[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const __nv_bfloat16 lo = __float2bfloat16_rn(gelu(v[2 * i] + bias[c + 2 * i]));
+            const __nv_bfloat16 hi = __float2bfloat16_rn(gelu(v[2 * i + 1] + bias[c + 2 * i + 1]));
+            pk[i] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+        }
+        *reinterpret_cast<uint4*>(Hs + cm_off(row, c, KG2)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        *reinterpret_cast<uint4*>(Hs + cm_off(row, c + 8, KG2)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    }
+}
+
+template <int ST>
+__global__ void __launch_bounds__(256, 1) k_surr_fused_tc(const FusedArgs a) {
+    extern __shared__ __align__(128) unsigned char tc_smem[];
+    unsigned char* W1s = tc_smem;                       // B of layer 1: [HID][KP] core matrices
+    unsigned char* W2s = W1s + kTcW1;                // B of layer 2: [HID][HID]
+    unsigned char* W3s = W2s + kTcW2;                // B of layer 3: [16][HID] (rows 3..15 zero)
+    unsigned char* Xs = W3s + kTcW3;                 // A of layer 1: [FT][KP]
+    unsigned char* Hs = Xs + kTcX;                   // A of layers 2 and 3: [FT][HID]
+    float* bias = reinterpret_cast<float*>(Hs + kTcH);          // b1 | b2 | b3
+    float* mu = bias + 2 * HID + NOP;                            // [KP]
+    float* isd = mu + KP;                                        // [KP]
+    int* env = reinterpret_cast<int*>(isd + KP);                 // [FT]
+    float* plevs = reinterpret_cast<float*>(env + FT);           // [kMaxNZ]
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(plevs + kMaxNZ);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t mb = smem_u32(mbar);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int e = tid; e < a.g.nz; e += blockDim.x) plevs[e] = a.g.plev[e];
+    // weights as B operands (N x K, K-major): W1 [k][n] -> (n, k)
+    for (int e = tid; e < KP * HID; e += blockDim.x) {
+        const int k = e / HID, nn = e % HID;
+        *reinterpret_cast<__nv_bfloat16*>(W1s + cm_off(nn, k, KG1)) = a.W1b[e];
+    }
+    for (int e = tid; e < HID * HID; e += blockDim.x) {
+        const int k = e / HID, nn = e % HID;
+        *reinterpret_cast<__nv_bfloat16*>(W2s + cm_off(nn, k, KG2)) = a.W2b[e];
+    }
+    for (int e = tid; e < NW3 * HID; e += blockDim.x) {
+        const int nn = e / HID, k = e % HID;
+        *reinterpret_cast<__nv_bfloat16*>(W3s + cm_off(nn, k, KG2)) =
+            nn < NOP ? a.W3b[k * NOP + nn] : __float2bfloat16(0.f);
+    }
+    for (int e = tid; e < HID; e += blockDim.x) {
+        bias[e] = a.b1[e];
+        bias[HID + e] = a.b2[e];
+    }
+    if (tid < NOP) bias[2 * HID + tid] = a.b3p[tid];
+    for (int e = tid; e < KP; e += blockDim.x) {
+        mu[e] = a.mu_x[e];
+        isd[e] = a.isd_x[e];
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tmem_slot;
+    // this warp's lanes (rows) and column half in the epilogues
+    const int row = 32 * (warp & 3) + (tid & 31), chalf = warp >> 2;
+    const uint32_t tlane = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
+    const uint32_t xs_a = smem_u32(Xs), hs_a = smem_u32(Hs);
+    const uint32_t w1_a = smem_u32(W1s), w2_a = smem_u32(W2s), w3_a = smem_u32(W3s);
+    uint32_t phase = 0;
+    bool failed = false;
+    const int64_t ntiles = (a.n + FT - 1) / FT;
+    for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+        gather_standardise<ST>(
+            a, plevs, mu, isd, tile, tid,
+            [&](int r, int c, __nv_bfloat16 v) { *reinterpret_cast<__nv_bfloat16*>(Xs + cm_off(r, c, KG1)) = v; },
+            env);
+        // three layers: MMA chain by thread 0, completion on the mbarrier, epilogue by all
+#pragma unroll 1
+        for (int layer = 0; layer < 3; ++layer) {
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            if (tid == 0 && !a.withhold_mma) {
+                tc_fence_after();
+                if (layer == 0)
+                    umma_layer(tbase, xs_a, w1_a, KP / 16, KG1, umma_idesc(FT, HID));
+                else if (layer == 1)
+                    umma_layer(tbase + 128u, hs_a, w2_a, HID / 16, KG2, umma_idesc(FT, HID));
+                else
+                    umma_layer(tbase, hs_a, w3_a, HID / 16, KG2, umma_idesc(FT, NW3));
+                umma_commit(mb);
+            }
+            const bool ok = mbar_wait(mb, phase, a.wait_cycles);
+            phase ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            tc_fence_after();
+            if (layer == 0) {
+                tc_epilogue_gelu(tlane, row, 64 * chalf, bias, Hs);
+            } else if (layer == 1) {
+                tc_epilogue_gelu(tlane + 128u, row, 64 * chalf, bias + HID, Hs);
+            } else if (warp < 4) {
+                float y[4];
+                tmem_ld4(tlane, y);
+                const int64_t q = tile * FT + row;
+                if (q < a.n)
+                    apply_displacement(a, q, env[row], y[0] + bias[2 * HID], y[1] + bias[2 * HID + 1],
+                                       y[2] + bias[2 * HID + 2]);
+            }
+        }
+    }
+    if (failed && tid == 0) atomicExch(a.status, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols) : "memory");
     }
 }
 
@@ -696,12 +938,13 @@ cudaError_t surr_alloc(Surrogate& S, int64_t B) {
                      (void**)&S.W2b, (void**)&S.W3b, (void**)&S.b3p, (void**)&S.mu_x, (void**)&S.isd_x,
                      (void**)&S.mu_y, (void**)&S.isd_y, (void**)&S.sd_y, (void**)&S.Xh, (void**)&S.H1,
                      (void**)&S.H2, (void**)&S.dY, (void**)&S.dZ2, (void**)&S.dZ1, (void**)&S.Z1,
-                     (void**)&S.Z2, (void**)&S.Yh, (void**)&S.Xraw, (void**)&S.env, (void**)&S.loss_tmp};
+                     (void**)&S.Z2, (void**)&S.Yh, (void**)&S.Xraw, (void**)&S.env, (void**)&S.loss_tmp,
+                     (void**)&S.status};
     const size_t sizes[] = {NPAR * 4, NPAR * 4, NPAR * 4, NPAR * 4, KP * HID * 2, HID * HID * 2, HID * NOP * 2,
                             NOP * 4, KP * 4, KP * 4, NOP * 4, NOP * 4, NOP * 4, (size_t)B * KP * 2,
                             (size_t)B * HID * 2, (size_t)B * HID * 2, (size_t)B * NOP * 2,
                             (size_t)B * HID * 2, (size_t)B * HID * 2, (size_t)B * HID * 4,
-                            (size_t)B * HID * 4, (size_t)B * NOP * 4, (size_t)B * KP * 4, (size_t)B, 16};
+                            (size_t)B * HID * 4, (size_t)B * NOP * 4, (size_t)B * KP * 4, (size_t)B, 16, 16};
     for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]); ++i) {
         cudaError_t e = cudaMalloc(ptrs[i], sizes[i]);
         if (e != cudaSuccess) return e;
@@ -714,7 +957,7 @@ cudaError_t surr_alloc(Surrogate& S, int64_t B) {
 void surr_free(Surrogate& S) {
     void* ptrs[] = {S.theta, S.grad, S.m, S.v, S.W1b, S.W2b, S.W3b, S.b3p, S.mu_x, S.isd_x, S.mu_y,
                     S.isd_y, S.sd_y, S.Xh, S.H1, S.H2, S.dY, S.dZ2, S.dZ1, S.Z1, S.Z2, S.Yh, S.Xraw,
-                    S.env, S.loss_tmp};
+                    S.env, S.loss_tmp, S.status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -824,37 +1067,40 @@ cudaError_t launch_colstats(const float* D, int64_t n, int ncol, double* sum, do
     return cudaGetLastError();
 }
 
+template <class K>
+cudaError_t launch_dyn(K kern, int grid, size_t smem, const FusedArgs& a, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 256, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t launch_surr_fused_st(int kernel, int grid, const FusedArgs& a, cudaStream_t s) {
+    if (kernel == MPTRAC_SURR_KERNEL_MMA_SYNC) return launch_dyn(k_surr_fused<ST>, grid, kFusedSmem, a, s);
+    FusedArgs t = a;
+    t.withhold_mma = kernel == MPTRAC_SURR_KERNEL_WAIT_TEST ? 1 : 0;
+    t.wait_cycles = t.withhold_mma ? kTestWaitCycles : kWaitCycles;
+    return launch_dyn(k_surr_fused_tc<ST>, grid, kTcSmem, t, s);
+}
+
 cudaError_t launch_surr_fused(int storage, Surrogate& S, const Geo& g, MetView m0, MetView m1, int64_t n,
                               double* lon, double* lat, double* p, float w, int window_ok, uint8_t* fallback,
                               double lon0, cudaStream_t s) {
     FusedArgs a{g, m0, m1, n, lon, lat, p, fallback, w, window_ok, S.W1b, S.W2b, S.W3b,
                 S.theta + OB1, S.theta + OB2, S.b3p, S.mu_x, S.isd_x, S.mu_y, S.sd_y,
-                lon0, g.pmin_d, g.pmax_d};
+                lon0, g.pmin_d, g.pmax_d, S.status, kWaitCycles, 0};
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t ntiles = (n + FT - 1) / FT;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, sms));
     note_launches(1);
-    cudaError_t e;
     switch (storage) {
-        case MPTRAC_FP32:
-            e = cudaFuncSetAttribute(k_surr_fused<MPTRAC_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
-            if (e != cudaSuccess) return e;
-            k_surr_fused<MPTRAC_FP32><<<grid, 256, kFusedSmem, s>>>(a);
-            break;
-        case MPTRAC_BF16:
-            e = cudaFuncSetAttribute(k_surr_fused<MPTRAC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
-            if (e != cudaSuccess) return e;
-            k_surr_fused<MPTRAC_BF16><<<grid, 256, kFusedSmem, s>>>(a);
-            break;
-        default:
-            e = cudaFuncSetAttribute(k_surr_fused<MPTRAC_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
-            if (e != cudaSuccess) return e;
-            k_surr_fused<MPTRAC_FP16><<<grid, 256, kFusedSmem, s>>>(a);
-            break;
+        case MPTRAC_FP32: return launch_surr_fused_st<MPTRAC_FP32>(S.kernel, grid, a, s);
+        case MPTRAC_BF16: return launch_surr_fused_st<MPTRAC_BF16>(S.kernel, grid, a, s);
+        default: return launch_surr_fused_st<MPTRAC_FP16>(S.kernel, grid, a, s);
     }
-    return cudaGetLastError();
 }
 
 

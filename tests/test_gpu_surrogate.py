@@ -210,3 +210,68 @@ def test_training_gains_over_untrained_and_first_order(M, field):
     first = np.stack([u * 1800.0, v * 1800.0, Yn[:, 2]], axis=1)   # (dz taken exact: favours the baseline)
     first_loss = np.mean(((first - mu_y) / sd_y - yn_true)[:, :2] ** 2) * 2 / 3
     assert val < first_loss, (val, first_loss)
+
+
+def _advance_with(M, sur, ctx, st, kernel, n):
+    sur.set_kernel(kernel)
+    parts = M.Particles.from_numpy(st, meso=False, release=False)
+    fb = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    sur.advance(ctx, parts, 3600.0, 1800.0, fb)
+    sur.status()
+    return parts.to_numpy(), fb.cpu().numpy()
+
+
+@pytest.mark.parametrize("n", [1, 127, 3000, 20_000])
+def test_tcgen05_inference_equals_mma_sync(M, field, n):
+    """The tcgen05 kernel (tensor-memory accumulators) and the warp-level mma.sync kernel give the
+    same particles: same gather, same bf16 operands, same order of the K = 16 accumulations.
+    n spans one partial tile up to several tiles per CTA, with ragged tails."""
+    grid, f0, f1, ctx = field
+    st, X, Y, _ = _dataset(M, grid, ctx, f0, f1, max(n, 64), 13)
+    st = {k: v[:n] for k, v in st.items()}
+    sur = M.Surrogate(4096)
+    sur.set_params(S.flatten(S.init_params(5)).astype(np.float32))
+    mu_x, sd_x = M.colstats(X)
+    mu_y, sd_y = M.colstats(Y)
+    sur.set_norm(mu_x, np.where(sd_x > 1e-12, sd_x, 1.0), mu_y, sd_y)
+    a, fa = _advance_with(M, sur, ctx, st, M.SURR_KERNEL_MMA_SYNC, n)
+    b, fb = _advance_with(M, sur, ctx, st, M.SURR_KERNEL_TCGEN05, n)
+    np.testing.assert_array_equal(fb, fa)
+    moved = fa == 0
+    assert moved.any() or n < 64
+    for k in ("lon", "lat", "p"):
+        np.testing.assert_array_equal(b[k], a[k], err_msg=k)
+
+
+def test_bounded_wait_reports_timeout_and_recovers(M, field):
+    """The tcgen05 kernel with its MMAs withheld: every wait for the tensor cores runs out
+    (about 10 ms), the kernel frees its tensor memory and returns, nothing moves, and
+    mptrac_surr_status reports E_TIMEOUT once.  The next launches run normally."""
+    grid, f0, f1, ctx = field
+    st, X, Y, _ = _dataset(M, grid, ctx, f0, f1, 2000, 17)
+    sur = M.Surrogate(4096)
+    sur.set_params(S.flatten(S.init_params(7)).astype(np.float32))
+    mu_x, sd_x = M.colstats(X)
+    mu_y, sd_y = M.colstats(Y)
+    sur.set_norm(mu_x, np.where(sd_x > 1e-12, sd_x, 1.0), mu_y, sd_y)
+    sur.set_kernel(M.SURR_KERNEL_WAIT_TEST)
+    parts = M.Particles.from_numpy(st, meso=False, release=False)
+    fb = torch.zeros(2000, dtype=torch.uint8, device="cuda")
+    sur.advance(ctx, parts, 3600.0, 1800.0, fb)
+    with pytest.raises(M.MptracError) as e:
+        sur.status()
+    assert e.value.code == -6
+    got = parts.to_numpy()
+    for k in ("lon", "lat", "p"):
+        np.testing.assert_array_equal(got[k], st[k])
+    sur.status()                      # the flag was cleared
+    ref, _ = _advance_with(M, sur, ctx, st, M.SURR_KERNEL_MMA_SYNC, 2000)
+    again, _ = _advance_with(M, sur, ctx, st, M.SURR_KERNEL_TCGEN05, 2000)
+    np.testing.assert_array_equal(again["lon"], ref["lon"])
+
+
+def test_set_kernel_rejects_unknown(M):
+    sur = M.Surrogate(1024)
+    with pytest.raises(M.MptracError) as e:
+        sur.set_kernel(7)
+    assert e.value.code == -1
