@@ -376,24 +376,27 @@ int mptrac_surr_train_step(mptrac_surr* s, const float* x, const float* y, int64
  * integrator (mptrac_advect_masked).  Any n (processed in max_batch chunks). */
 int mptrac_surr_advance(mptrac_ctx* ctx, mptrac_surr* s, const mptrac_particles* parts, double t,
                         double dt_seg, uint8_t* fallback, uintptr_t stream);
-/* Kernel of the fused inference in mptrac_surr_advance:
- *   MPTRAC_SURR_KERNEL_TCGEN05 (default): each layer of a 128-particle tile is
- *     one chain of tcgen05.mma (M = 128, K in steps of 16) issued by one
- *     thread, operands in shared memory, accumulators in tensor memory;
- *   MPTRAC_SURR_KERNEL_MMA_SYNC: warp-level mma.sync m16n8k16 (16 rows per
- *     warp), kept for comparison.
+/* Tensor-core kernels of the surrogate (training GEMMs and the fused
+ * inference in mptrac_surr_advance):
+ *   MPTRAC_SURR_KERNEL_TCGEN05 (default): tcgen05.mma chains issued by one
+ *     thread per CTA (M = 128, K in steps of 16), operands in shared memory,
+ *     accumulators in tensor memory;
+ *   MPTRAC_SURR_KERNEL_MMA_SYNC: warp-level mma.sync m16n8k16, kept for
+ *     comparison.
  *   MPTRAC_SURR_KERNEL_WAIT_TEST: the tcgen05 kernel with its MMAs withheld
  *     and a wait limit of about 10 ms, for tests of the bounded wait: nothing
  *     moves and mptrac_surr_status reports E_TIMEOUT.
- * Both kernels compute the same network in bf16 with float32 accumulation
- * (both tensor-core paths add the K = 16 products in the same order; results
- * have been identical).  E_INVALID_ARG for another value. */
+ * Both compute the same network in bf16 with float32 accumulation and add
+ * the K = 16 products in the same order: the inference results have been
+ * identical, the gradients differ by the grouping of their split-K atomic
+ * sums.  E_INVALID_ARG for another value. */
 #define MPTRAC_SURR_KERNEL_TCGEN05   0
 #define MPTRAC_SURR_KERNEL_MMA_SYNC  1
 #define MPTRAC_SURR_KERNEL_WAIT_TEST 2
 int mptrac_surr_set_kernel(mptrac_surr* s, int kernel);
-/* Synchronises `stream` and reports whether a fused inference launched before
- * gave up a bounded wait for its tensor-core work (about one second):
+/* Synchronises `stream` and reports whether a tcgen05 kernel of this surrogate
+ * launched before gave up a bounded wait for its tensor-core work (about one
+ * second):
  * E_TIMEOUT (the flag is then cleared; the particles of the tiles not reached
  * are left unmoved and their fallback entries are not written), else OK. */
 int mptrac_surr_status(mptrac_surr* s, uintptr_t stream);

@@ -6,11 +6,11 @@
 // Network (per sample): x_hat = (x - mu_x)/sd_x (176 = 168 features + 8 zero
 // pad), z1 = x_hat W1 + b1, h1 = gelu(z1), z2 = h1 W2 + b2, h2 = gelu(z2),
 // y_hat = h2 W3 + b3 (3 outputs, padded to 8 columns), y = y_hat sd_y + mu_y.
-// GEMM operands are bfloat16 with float32 accumulation: the fused inference
-// runs its layers on the 5th-generation tensor cores (tcgen05.mma, operands
-// in shared memory, accumulators in tensor memory); the training GEMMs and a
-// comparison inference kernel use the warp-level mma.sync m16n8k16.  Biases,
-// GELU, the loss and Adam run in float32 on float32 master weights.
+// GEMM operands are bfloat16 with float32 accumulation on the 5th-generation
+// tensor cores (tcgen05.mma, operands in shared memory, accumulators in tensor
+// memory), both in training and in the fused inference; kernels on the
+// warp-level mma.sync m16n8k16 stay selectable for comparison.  Biases, GELU,
+// the loss and Adam run in float32 on float32 master weights.
 #include <cmath>
 #include <cstring>
 
@@ -168,6 +168,8 @@ struct GemmArgs {
     const float* Zin;       // pre-activation for the GELU derivative
     int64_t ldc;
     int64_t n_valid;        // columns >= n_valid are not written
+    int* status;            // tcgen05 kernel: set to 1 when a bounded wait gives up
+    long long wait_cycles;  // tcgen05 kernel: limit of each wait (SM clock cycles)
 };
 
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
@@ -181,6 +183,23 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint
         "{%0,%1,%2,%3};"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int EPI>
+__device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, int64_t m, int64_t n, float v) {
+    if (m >= g.M || n >= g.N || n >= g.n_valid) return;
+    const int64_t o = m * g.ldc + n;
+    if (EPI == EPI_ATOMIC_F32) {
+        atomicAdd(&g.Cf[o], v);
+    } else if (EPI == EPI_BIAS_GELU) {
+        const float z = v + g.bias[n];
+        g.Cf[o] = z;
+        g.Cb[o] = __float2bfloat16_rn(gelu(z));
+    } else if (EPI == EPI_BIAS_F32) {
+        g.Cf[o] = v + g.bias[n];
+    } else {
+        g.Cb[o] = __float2bfloat16_rn(v * gelu_grad(g.Zin[o]));
+    }
 }
 
 constexpr int TM = 64, TN = 64, TK = 32, TKP = TK + 8;
@@ -249,20 +268,7 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
             for (int c = 0; c < 4; ++c) {
                 const int64_t m = m0 + wm * 32 + i * 16 + gq + (c >> 1) * 8;
                 const int64_t n = n0 + wn * 32 + j * 8 + 2 * tq + (c & 1);
-                if (m >= g.M || n >= g.N || n >= g.n_valid) continue;
-                const float v = acc[i][j][c];
-                const int64_t o = m * g.ldc + n;
-                if (EPI == EPI_ATOMIC_F32) {
-                    atomicAdd(&g.Cf[o], v);
-                } else if (EPI == EPI_BIAS_GELU) {
-                    const float z = v + g.bias[n];
-                    g.Cf[o] = z;
-                    g.Cb[o] = __float2bfloat16_rn(gelu(z));
-                } else if (EPI == EPI_BIAS_F32) {
-                    g.Cf[o] = v + g.bias[n];
-                } else {
-                    g.Cb[o] = __float2bfloat16_rn(v * gelu_grad(g.Zin[o]));
-                }
+                gemm_epilogue<EPI>(g, m, n, acc[i][j][c]);
             }
 }
 
@@ -909,9 +915,169 @@ __global__ void __launch_bounds__(256, 1) k_surr_fused_tc(const FusedArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Training GEMM on tcgen05: CTA tile 128 x 128 (M x N), K in chunks of 64 held
+// in two shared-memory stages (A and B of a chunk in the K-major core-matrix
+// layout, written by all threads from any strides), four MMAs of K = 16 per
+// chunk issued by one thread and committed to the stage's mbarrier, so that the
+// loads of chunk i + 1 overlap the MMAs of chunk i.  The accumulator (128
+// lanes x 128 columns of tensor memory) goes through the same epilogues as
+// k_gemm.  Waits are bounded as in k_surr_fused_tc.
+// ---------------------------------------------------------------------------
+constexpr int GT_M = 128, GT_N = 128, GT_K = 64;
+constexpr size_t kGStage = (size_t)(GT_M + GT_N) * GT_K * 2;   // 32 KB per stage
+constexpr size_t kGemmTcSmem = 2 * kGStage + 32;
+constexpr uint32_t kGemmTmemCols = 128;
+
+// Rows [r0, r0 + ROWS) x columns [kb, kb + GT_K) of an operand whose element
+// (row, k) is P[row * s_row + k * s_k], into the core-matrix layout at dst;
+// rows >= nrows and k >= kend are zero.  16-byte loads along k when k is
+// contiguous, along the rows when the rows are, else element by element.
+template <int ROWS>
+__device__ __forceinline__ void load_operand(unsigned char* dst, const __nv_bfloat16* P, int64_t s_row, int64_t s_k,
+                                             int64_t r0, int64_t nrows, int64_t kb, int64_t kend, int tid) {
+    const bool aligned = (reinterpret_cast<uintptr_t>(P) & 15) == 0;
+    if (aligned && s_k == 1 && (s_row & 7) == 0 && (kend & 7) == 0) {
+        for (int e = tid; e < ROWS * (GT_K / 8); e += 256) {
+            const int r = e / (GT_K / 8), c = 8 * (e % (GT_K / 8));
+            const int64_t row = r0 + r, k = kb + c;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (row < nrows && k < kend) v = *reinterpret_cast<const uint4*>(P + row * s_row + k);
+            *reinterpret_cast<uint4*>(dst + cm_off(r, c, GT_K / 8)) = v;
+        }
+    } else if (aligned && s_row == 1 && (s_k & 7) == 0 && (nrows & 7) == 0) {
+        for (int e = tid; e < (ROWS / 8) * GT_K; e += 256) {
+            const int r = 8 * (e % (ROWS / 8)), c = e / (ROWS / 8);
+            const int64_t row = r0 + r, k = kb + c;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (row < nrows && k < kend) v = *reinterpret_cast<const uint4*>(P + row + k * s_k);
+            const unsigned short* h = reinterpret_cast<const unsigned short*>(&v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) *reinterpret_cast<unsigned short*>(dst + cm_off(r + j, c, GT_K / 8)) = h[j];
+        }
+    } else {
+        const __nv_bfloat16 zero = __float2bfloat16(0.f);
+        for (int e = tid; e < ROWS * GT_K; e += 256) {
+            const int r = e / GT_K, c = e % GT_K;
+            const int64_t row = r0 + r, k = kb + c;
+            *reinterpret_cast<__nv_bfloat16*>(dst + cm_off(r, c, GT_K / 8)) =
+                (row < nrows && k < kend) ? P[row * s_row + k * s_k] : zero;
+        }
+    }
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(256, 1) k_gemm_tc(const GemmArgs g) {
+    extern __shared__ __align__(128) unsigned char g_smem[];
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(g_smem + 2 * kGStage);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t m0 = (int64_t)blockIdx.x * GT_M, n0 = (int64_t)blockIdx.y * GT_N;
+    const int64_t kb0 = (int64_t)blockIdx.z * g.kchunk;
+    const int64_t kend = min(g.K, kb0 + g.kchunk);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kGemmTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tmem_slot;
+    const int nchunks = kend > kb0 ? (int)((kend - kb0 + GT_K - 1) / GT_K) : 0;
+    uint32_t waits[2] = {0u, 0u};   // completed waits per stage: the parity of the next
+    bool failed = false;
+    for (int i = 0; i < nchunks; ++i) {
+        const int st = i & 1;
+        if (i >= 2) {   // the MMAs of chunk i - 2 have read this stage
+            const bool ok = mbar_wait(smem_u32(&mbar[st]), waits[st] & 1u, g.wait_cycles);
+            ++waits[st];
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+        }
+        unsigned char* As = g_smem + st * kGStage;
+        unsigned char* Bs = As + (size_t)GT_M * GT_K * 2;
+        const int64_t kb = kb0 + (int64_t)i * GT_K;
+        load_operand<GT_M>(As, g.A, g.sam, g.sak, m0, g.M, kb, kend, tid);
+        load_operand<GT_N>(Bs, g.B, g.sbn, g.sbk, n0, g.N, kb, kend, tid);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a_addr = smem_u32(As), b_addr = smem_u32(Bs);
+#pragma unroll
+            for (int ks = 0; ks < GT_K / 16; ++ks)
+                umma_f16(tbase, umma_desc(a_addr + 256u * ks, 128u, 128u * (GT_K / 8)),
+                         umma_desc(b_addr + 256u * ks, 128u, 128u * (GT_K / 8)), umma_idesc(GT_M, GT_N),
+                         (i > 0 || ks > 0) ? 1u : 0u);
+            umma_commit(smem_u32(&mbar[st]));
+        }
+    }
+    // drain: every commit of both stages has arrived (the last one covers every MMA)
+    for (int st = 0; st < 2 && !failed; ++st) {
+        const uint32_t commits = (uint32_t)((nchunks + 1 - st) / 2);
+        while (waits[st] < commits) {
+            const bool ok = mbar_wait(smem_u32(&mbar[st]), waits[st] & 1u, g.wait_cycles);
+            ++waits[st];
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+        }
+    }
+    if (!failed && nchunks > 0) {
+        tc_fence_after();
+        const int row = 32 * (warp & 3) + (tid & 31);
+        const uint32_t tlane = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
+#pragma unroll 1
+        for (int ch = 0; ch < 4; ++ch) {
+            const int c = 64 * (warp >> 2) + 16 * ch;
+            if (n0 + c >= g.N) break;   // warp-uniform
+            float v[16];
+            tmem_ld16(tlane + (uint32_t)c, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) gemm_epilogue<EPI>(g, m0 + row, n0 + c + j, v[j]);
+        }
+    }
+    if (failed && tid == 0) atomicExch(g.status, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kGemmTmemCols)
+                     : "memory");
+    }
+}
+
 int grid1(int64_t n, int block) {
     int64_t b = (n + block - 1) / block;
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, 1 << 20));
+}
+
+template <int EPI>
+cudaError_t gemm_tc(const GemmArgs& g, int splits, int* status, cudaStream_t s) {
+    GemmArgs a = g;
+    a.status = status;
+    a.wait_cycles = kWaitCycles;
+    if (splits < 1) splits = 1;
+    a.kchunk = ((g.K + splits - 1) / splits + GT_K - 1) / GT_K * GT_K;
+    if (a.kchunk <= 0) a.kchunk = GT_K;
+    const int gz = (int)((g.K + a.kchunk - 1) / a.kchunk);
+    dim3 grid((unsigned)((g.M + GT_M - 1) / GT_M), (unsigned)((g.N + GT_N - 1) / GT_N), (unsigned)std::max(gz, 1));
+    note_launches(1);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmTcSmem);
+    if (e != cudaSuccess) return e;
+    k_gemm_tc<EPI><<<grid, 256, kGemmTcSmem, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <int EPI>
@@ -968,6 +1134,12 @@ cudaError_t surr_cast(Surrogate& S, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// The training GEMMs on the kernel the surrogate selects (tcgen05 unless mma.sync is chosen).
+template <int EPI>
+cudaError_t run_gemm(const Surrogate& S, const GemmArgs& g, int splits, cudaStream_t s) {
+    return S.kernel == MPTRAC_SURR_KERNEL_MMA_SYNC ? gemm<EPI>(g, splits, s) : gemm_tc<EPI>(g, splits, S.status, s);
+}
+
 // Forward of B rows of raw features X (device, [B][KP]) into S.Yh (normalised outputs).
 cudaError_t surr_forward(Surrogate& S, const float* X, int64_t B, cudaStream_t s) {
     note_launches(1);
@@ -978,13 +1150,13 @@ cudaError_t surr_forward(Surrogate& S, const float* X, int64_t B, cudaStream_t s
     g.A = S.Xh; g.B = S.W1b; g.M = B; g.N = HID; g.K = KP;
     g.sam = KP; g.sak = 1; g.sbk = HID; g.sbn = 1;
     g.Cf = S.Z1; g.Cb = S.H1; g.bias = S.theta + OB1; g.ldc = HID; g.n_valid = HID;
-    if ((e = gemm<EPI_BIAS_GELU>(g, 1, s)) != cudaSuccess) return e;
+    if ((e = run_gemm<EPI_BIAS_GELU>(S, g, 1, s)) != cudaSuccess) return e;
     g.A = S.H1; g.B = S.W2b; g.K = HID; g.sam = HID;
     g.Cf = S.Z2; g.Cb = S.H2; g.bias = S.theta + OB2;
-    if ((e = gemm<EPI_BIAS_GELU>(g, 1, s)) != cudaSuccess) return e;
+    if ((e = run_gemm<EPI_BIAS_GELU>(S, g, 1, s)) != cudaSuccess) return e;
     g.A = S.H2; g.B = S.W3b; g.N = NOP; g.sbk = NOP;
     g.Cf = S.Yh; g.Cb = nullptr; g.bias = S.b3p; g.ldc = NOP; g.n_valid = NOP;
-    return gemm<EPI_BIAS_F32>(g, 1, s);
+    return run_gemm<EPI_BIAS_F32>(S, g, 1, s);
 }
 
 // Gradients of the loss for B samples into S.grad (zeroed first); loss added to *loss.
@@ -999,17 +1171,17 @@ cudaError_t surr_backward(Surrogate& S, const float* Yt, int64_t B, float* loss,
     // dW3 = H2^T dY  [HID x NO]
     g.A = S.H2; g.sam = 1; g.sak = HID; g.B = S.dY; g.sbk = NOP; g.sbn = 1;
     g.M = HID; g.N = NOP; g.K = B; g.Cf = S.grad + OW3; g.ldc = NO; g.n_valid = NO;
-    if ((e = gemm<EPI_ATOMIC_F32>(g, splits, s)) != cudaSuccess) return e;
+    if ((e = run_gemm<EPI_ATOMIC_F32>(S, g, splits, s)) != cudaSuccess) return e;
     // dZ2 = (dY W3^T) * gelu'(Z2)
     g = GemmArgs{};
     g.A = S.dY; g.sam = NOP; g.sak = 1; g.B = S.W3b; g.sbk = 1; g.sbn = NOP;
     g.M = B; g.N = HID; g.K = NOP; g.Cb = S.dZ2; g.Zin = S.Z2; g.ldc = HID; g.n_valid = HID;
-    if ((e = gemm<EPI_GELU_BWD>(g, 1, s)) != cudaSuccess) return e;
+    if ((e = run_gemm<EPI_GELU_BWD>(S, g, 1, s)) != cudaSuccess) return e;
     // dW2 = H1^T dZ2, db2
     g = GemmArgs{};
     g.A = S.H1; g.sam = 1; g.sak = HID; g.B = S.dZ2; g.sbk = HID; g.sbn = 1;
     g.M = HID; g.N = HID; g.K = B; g.Cf = S.grad + OW2; g.ldc = HID; g.n_valid = HID;
-    if ((e = gemm<EPI_ATOMIC_F32>(g, splits, s)) != cudaSuccess) return e;
+    if ((e = run_gemm<EPI_ATOMIC_F32>(S, g, splits, s)) != cudaSuccess) return e;
     const int rpb = 512;
     note_launches(1);
     k_colsum_bf16<<<grid1(B, rpb), HID, 0, s>>>(S.dZ2, B, rpb, S.grad + OB2);
@@ -1017,12 +1189,12 @@ cudaError_t surr_backward(Surrogate& S, const float* Yt, int64_t B, float* loss,
     g = GemmArgs{};
     g.A = S.dZ2; g.sam = HID; g.sak = 1; g.B = S.W2b; g.sbk = 1; g.sbn = HID;
     g.M = B; g.N = HID; g.K = HID; g.Cb = S.dZ1; g.Zin = S.Z1; g.ldc = HID; g.n_valid = HID;
-    if ((e = gemm<EPI_GELU_BWD>(g, 1, s)) != cudaSuccess) return e;
+    if ((e = run_gemm<EPI_GELU_BWD>(S, g, 1, s)) != cudaSuccess) return e;
     // dW1 = Xh^T dZ1, db1
     g = GemmArgs{};
     g.A = S.Xh; g.sam = 1; g.sak = KP; g.B = S.dZ1; g.sbk = HID; g.sbn = 1;
     g.M = KP; g.N = HID; g.K = B; g.Cf = S.grad + OW1; g.ldc = HID; g.n_valid = HID;
-    if ((e = gemm<EPI_ATOMIC_F32>(g, splits, s)) != cudaSuccess) return e;
+    if ((e = run_gemm<EPI_ATOMIC_F32>(S, g, splits, s)) != cudaSuccess) return e;
     note_launches(1);
     k_colsum_bf16<<<grid1(B, rpb), HID, 0, s>>>(S.dZ1, B, rpb, S.grad + OB1);
     return cudaGetLastError();

@@ -275,3 +275,27 @@ def test_set_kernel_rejects_unknown(M):
     with pytest.raises(M.MptracError) as e:
         sur.set_kernel(7)
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("batch", [4096, 1000])
+def test_training_gemms_tcgen05_match_mma_sync(M, batch):
+    """The training GEMMs on tcgen05 (128 x 128 tiles, K chunks of 64 in two shared-memory
+    stages) against the warp-level mma.sync GEMMs: the forward outputs agree to float32
+    rounding (same bf16 operands, K = 16 products accumulated in the same order), and the
+    gradients, whose split-K partial sums are added atomically in another grouping, to 1e-5.
+    batch 1000 leaves a ragged 128-row tile and a K range that is not a multiple of 64."""
+    P, mu_x, sd_x, mu_y, sd_y, X, Y = _random_model(9, batch)
+    out = {}
+    for kern in (M.SURR_KERNEL_MMA_SYNC, M.SURR_KERNEL_TCGEN05):
+        sur = M.Surrogate(8192)
+        sur.set_kernel(kern)
+        sur.set_params(S.flatten(P).astype(np.float32))
+        sur.set_norm(mu_x, sd_x, mu_y, sd_y)
+        yh = sur.forward(torch.from_numpy(X).cuda()).cpu().numpy()
+        loss = sur.grads(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()).item()
+        sur.status()
+        out[kern] = (yh, loss, sur.get_grads())
+    a, b = out[M.SURR_KERNEL_MMA_SYNC], out[M.SURR_KERNEL_TCGEN05]
+    np.testing.assert_allclose(b[0], a[0], rtol=1e-6, atol=1e-6 * np.abs(a[0]).max())
+    assert abs(b[1] - a[1]) <= 1e-5 * abs(a[1])
+    np.testing.assert_allclose(b[2], a[2], rtol=1e-5, atol=1e-5 * np.abs(a[2]).max())
