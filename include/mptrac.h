@@ -397,8 +397,9 @@ int mptrac_surr_set_kernel(mptrac_surr* s, int kernel);
 /* Synchronises `stream` and reports whether a tcgen05 kernel of this surrogate
  * launched before gave up a bounded wait for its tensor-core work (about one
  * second):
- * E_TIMEOUT (the flag is then cleared; the particles of the tiles not reached
- * are left unmoved and their fallback entries are not written), else OK. */
+ * E_TIMEOUT (the flag is then cleared; after an inference the particles of
+ * the tiles not reached are left unmoved and their fallback entries are not
+ * written, after a training call the gradients are incomplete), else OK. */
 int mptrac_surr_status(mptrac_surr* s, uintptr_t stream);
 /* mptrac_advect restricted to particles with mask[i] != 0 (DEVICE uint8 [n]). */
 int mptrac_advect_masked(mptrac_ctx* ctx, const mptrac_particles* parts, const uint8_t* mask,
