@@ -20,7 +20,8 @@ results are those of G = 1 up to the order of the particles in memory.
 The met snapshots live in a ring of the context's three slots (snapshot k of
 the run in slot k mod 3): the snapshot an interval two ahead needs is loaded
 on a stream of its own as soon as every group has finished the interval that
-last read the slot it replaces, so loads overlap with the steps.
+last read the slot it replaces, so loads overlap with the steps.  The groups'
+first sorts need no met and overlap the loads of the first two snapshots.
 
 Snapshots that ``snapshot_at`` returns in host memory (pinned, for the copies
 to overlap) are prefetched: right after an interval's loads, the snapshot the
@@ -134,6 +135,9 @@ class Simulation:
         loaded = {}                                      # snapshot k -> event after its load
         if n_iv == 0:
             return 0
+        # the particles are ready here: the first sorts need no met and overlap the loads
+        parts_ready = torch.cuda.Event()
+        parts_ready.record(main)
         # snapshots 0 and 1 in stream order; snapshot 2 (a free slot) on the load stream
         for k in (0, 1):
             self._load(ctx, k % 3, T(k), main)
@@ -162,7 +166,7 @@ class Simulation:
                 for parts, ws, gs, ss in zip(self.groups, self.workspaces, gstreams, sstreams):
                     if self.do_sort and not sorted_:
                         if ss is not gs:
-                            ss.wait_stream(gs)
+                            ss.wait_event(parts_ready)   # the run's first sort: no met needed
                         ctx.sort(parts, ws, stream=ss)
                         if ss is not gs:
                             gs.wait_stream(ss)
