@@ -6,10 +6,10 @@ PyTorch provides device memory and streams only.
 """
 from ._native import (Context, DiffParams, MptracError, Particles, Surrogate, advect_masked, colstats,
                       load, philox, surr_features, surr_targets,
-                      MPTRAC_BF16, MPTRAC_FP16, MPTRAC_FP32, SIGNATURES, LIB_PATH,
+                      MPTRAC_BF16, MPTRAC_FP16, MPTRAC_FP32, MAX_NZ, SIGNATURES, LIB_PATH,
                       SURR_KERNEL_TCGEN05, SURR_KERNEL_MMA_SYNC, SURR_KERNEL_WAIT_TEST)
 
 __all__ = ["Context", "DiffParams", "MptracError", "Particles", "Surrogate", "advect_masked", "colstats",
            "load", "philox", "surr_features", "surr_targets",
-           "MPTRAC_FP32", "MPTRAC_BF16", "MPTRAC_FP16", "SIGNATURES", "LIB_PATH",
+           "MPTRAC_FP32", "MPTRAC_BF16", "MPTRAC_FP16", "MAX_NZ", "SIGNATURES", "LIB_PATH",
            "SURR_KERNEL_TCGEN05", "SURR_KERNEL_MMA_SYNC", "SURR_KERNEL_WAIT_TEST"]

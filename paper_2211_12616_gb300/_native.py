@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmptrac.so")
 
 MPTRAC_FP32, MPTRAC_BF16, MPTRAC_FP16 = 0, 1, 2
+MAX_NZ = 256                      # MPTRAC_MAX_NZ: largest supported number of pressure levels
 STATUS = {0: "OK", -1: "E_INVALID_ARG", -2: "E_OOM", -3: "E_CUDA", -4: "E_TIME_RANGE",
           -5: "E_WORKSPACE", -6: "E_TIMEOUT", -7: "E_NOT_INIT"}
 

@@ -59,5 +59,9 @@ def test_invalid_grid_rejected_on_host(lib):
     assert b"decreasing" in lib.mptrac_last_error(None)
     gd = GridDesc(10, 5, 3, 0.0, 30.0, -90.0, 45.0, plev.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0, 3)
     assert lib.mptrac_init_grid(ctypes.byref(h), ctypes.byref(gd)) == -1
+    many = np.geomspace(1e5, 10.0, M.MAX_NZ + 1)       # one level more than supported
+    gd = GridDesc(10, 5, M.MAX_NZ + 1, 0.0, 36.0, -90.0, 45.0,
+                  many.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0, 3)
+    assert lib.mptrac_init_grid(ctypes.byref(h), ctypes.byref(gd)) == -1
     assert lib.mptrac_sort_workspace_bytes(None, 1000) >= 60 * 1000
     assert lib.mptrac_destroy(None) == 0

@@ -209,3 +209,42 @@ def test_checkpoint_resume_bit_identical(M, fourier):
     ga, gc = a.to_numpy(), c.to_numpy()
     for k in ("lon", "lat", "p", "up", "vp", "wp", "id"):
         np.testing.assert_array_equal(ga[k], gc[k], err_msg=k)
+
+
+def test_fused_step_over_launch_limit(M, fourier):
+    """300 fused steps in one call run as launches of 128, 128 and 44 steps (the time-weight
+    table of one launch holds 128); the result matches the oracle and three calls of 100."""
+    grid, f0, f1 = fourier
+    ctx = make_ctx(M, grid, [f0, f1], [0.0, T6H])
+    met = tr.Met(grid, 0.0, f0, T6H, f1)
+    st0 = uniform_particles(3001, grid.plev, seed=31)
+    prm = M.DiffParams()
+    a, b = M.Particles.from_numpy(st0), M.Particles.from_numpy(st0)
+    ctx.step(a, 0.0, 60.0, prm, 17, 0, 300)
+    for k in range(3):
+        ctx.step(b, k * 6000.0, 60.0, prm, 17, 100 * k, 100)
+    torch.cuda.synchronize()
+    ga, gb = a.to_numpy(), b.to_numpy()
+    for k in ("lon", "lat", "p", "up", "vp", "wp"):
+        np.testing.assert_array_equal(ga[k], gb[k], err_msg=k)
+    ref = tr.step(met, st0, 0.0, 60.0, tr.DiffParams(), 17, 0, 300)
+    assert_positions_close(ga, ref, what="300 fused steps", lon_metric="arc")
+
+
+def test_maximum_level_count(M):
+    """MPTRAC_MAX_NZ = 256 levels: fused steps with diffusion and the sort keys against the
+    oracle (the shared level tables and the level search at their largest)."""
+    grid = grid_global(36, 19, 256, 1e5, 10.0)
+    m = fourier_modes(5)
+    f0, f1 = fourier_snapshot(grid, m, 0.0), fourier_snapshot(grid, m, T6H)
+    ctx = make_ctx(M, grid, [f0, f1], [0.0, T6H])
+    met = tr.Met(grid, 0.0, f0, T6H, f1)
+    st0 = uniform_particles(2000, grid.plev, seed=33)
+    parts = M.Particles.from_numpy(st0)
+    ctx.step(parts, 600.0, 180.0, M.DiffParams(), 23, 0, 20)
+    torch.cuda.synchronize()
+    got = parts.to_numpy()
+    ref = tr.step(met, st0, 600.0, 180.0, tr.DiffParams(), 23, 0, 20)
+    assert_positions_close(got, ref, what="256 levels", lon_metric="arc")
+    keys = ctx.cell_keys(parts).cpu().numpy()
+    np.testing.assert_array_equal(keys, osort.cell_keys(grid, got["lon"], got["lat"], got["p"]))
