@@ -498,8 +498,11 @@ __device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
 // value weighted by the interpolation weights, sum_q w_q (x_q - mean)^2.  With
 // the weights summing to 1 it equals S - m^2, where m = sum_q w_q (x_q - x_0)
 // and S = sum_q w_q (x_q - x_0)^2 are taken relative to corner 0, and mean =
-// x_0 + m: the differences to a corner are of the size of the spread, so
-// nothing cancels, and corner 0's weight is not needed.
+// x_0 + m; corner 0's weight is not needed.  The rounding of S - m^2 is at
+// most a few float32 ulps of S: where the true spread is smaller (a point on
+// or within ~1e-7 cells of a corner other than 0) the result can come out
+// slightly negative, and the caller clamps it at 0.  The subgrid sigma then
+// errs by at most about sqrt(2 eps) |x_q - x_0|, 3.5e-4 of the corner difference.
 __device__ __forceinline__ void mean_and_var(const f2_t* x, const Weights8& W, f2_t& mean, f2_t& var) {
     f2_t m, S;
 #pragma unroll
@@ -543,7 +546,7 @@ __device__ __forceinline__ void eval_wind(const MetPair& mp, const S& s, const G
             f2_t t, vr;
             mean_and_var(x, W, t, vr);
             o[v] = tlerp(t, wl, wh);
-            sg[v] = tlerp(vr, wl, wh);
+            sg[v] = fmaxf(tlerp(vr, wl, wh), 0.f);   // rounding of S - m^2 below 0 (see mean_and_var)
         } else {
             o[v] = tlerp(trilinear(x, W), wl, wh);
         }

@@ -248,3 +248,33 @@ def test_maximum_level_count(M):
     assert_positions_close(got, ref, what="256 levels", lon_metric="arc")
     keys = ctx.cell_keys(parts).cpu().numpy()
     np.testing.assert_array_equal(keys, osort.cell_keys(grid, got["lon"], got["lat"], got["p"]))
+
+
+def test_degenerate_positions(M, fourier):
+    """Fused steps with diffusion from the degenerate places of the method: exactly on and
+    within metres of the poles (diffusion carries particles over the pole: reflection and
+    longitude + 180), on the longitude seam, on the top and bottom levels and outside the
+    level range (clamped).  Against the oracle, by great-circle distance."""
+    grid, f0, f1 = fourier
+    ctx = make_ctx(M, grid, [f0, f1], [0.0, T6H])
+    met = tr.Met(grid, 0.0, f0, T6H, f1)
+    lats = [90.0, -90.0, 89.9999, -89.9999, 89.999999, 0.0, 45.0]
+    lons = [0.0, 359.99999999999994, 180.0, 3.0]
+    ps = [grid.plev[0], grid.plev[-1], grid.plev[0] * 1.05, grid.plev[-1] * 0.9, 50000.0]
+    L = np.array([(lo, la, p) for la in lats for lo in lons for p in ps])
+    n = len(L)
+    st0 = uniform_particles(n, grid.plev, seed=41)
+    st0["lon"], st0["lat"], st0["p"] = L[:, 0].copy(), L[:, 1].copy(), L[:, 2].copy()
+    parts = M.Particles.from_numpy(st0)
+    ctx.step(parts, 0.0, 180.0, M.DiffParams(), 29, 0, 12)
+    torch.cuda.synchronize()
+    got = parts.to_numpy()
+    ref = tr.step(met, st0, 0.0, 180.0, tr.DiffParams(), 29, 0, 12)
+    assert_positions_close(got, ref, what="degenerate positions", lon_metric="arc")
+    assert np.all(np.abs(got["lat"]) <= 90.0)
+    assert np.all((got["lon"] >= 0.0) & (got["lon"] < 360.0))
+    assert np.all((got["p"] >= grid.plev[-1]) & (got["p"] <= grid.plev[0]))
+    # some particles did cross a pole (their longitude moved by about 180 degrees)
+    dlon = np.abs(((got["lon"] - st0["lon"]) + 180.0) % 360.0 - 180.0)
+    near_pole = np.abs(st0["lat"]) > 89.99
+    assert np.any(dlon[near_pole] > 90.0)
