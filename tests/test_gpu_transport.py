@@ -278,3 +278,29 @@ def test_degenerate_positions(M, fourier):
     dlon = np.abs(((got["lon"] - st0["lon"]) + 180.0) % 360.0 - 180.0)
     near_pole = np.abs(st0["lat"]) > 89.99
     assert np.any(dlon[near_pole] > 90.0)
+
+
+@pytest.mark.parametrize("dt", [180.0, 3600.0])
+def test_minimum_grid_and_long_steps(M, dt):
+    """The smallest grid the ABI accepts (2 x 2 x 2: two meridians, the two poles, two levels)
+    with random winds, and steps of an hour: fused steps with diffusion and the sort keys
+    against the oracle.  With hour-long steps the particles stay within 80 degrees of the
+    equator: closer to a pole one step turns the longitude by a large part of a circle, and
+    the trajectory over several steps amplifies float32 rounding beyond the tolerance (one
+    step still agrees to 3e-7 degrees there)."""
+    grid = grid_global(2, 2, 2, 1e5, 1e3)
+    rng = np.random.default_rng(5)
+    snaps = [{k: (rng.standard_normal((2, 2, 2)) * s).astype(np.float32)
+              for k, s in (("u", 20.0), ("v", 10.0), ("w", 0.3))} for _ in range(2)]
+    ctx = make_ctx(M, grid, snaps, [0.0, T6H])
+    met = tr.Met(grid, 0.0, snaps[0], T6H, snaps[1])
+    st0 = uniform_particles(3000, grid.plev, seed=7, lat_max=80.0 if dt > 1000.0 else 90.0)
+    parts = M.Particles.from_numpy(st0)
+    nsteps = 5 if dt > 1000.0 else 20
+    ctx.step(parts, 0.0, dt, M.DiffParams(), 3, 0, nsteps)
+    torch.cuda.synchronize()
+    got = parts.to_numpy()
+    ref = tr.step(met, st0, 0.0, dt, tr.DiffParams(), 3, 0, nsteps)
+    assert_positions_close(got, ref, what=f"2x2x2 grid, dt {dt}", lon_metric="arc")
+    keys = ctx.cell_keys(parts).cpu().numpy()
+    np.testing.assert_array_equal(keys, osort.cell_keys(grid, got["lon"], got["lat"], got["p"]))
