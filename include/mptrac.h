@@ -183,7 +183,8 @@ int mptrac_advect(mptrac_ctx* ctx, const mptrac_particles* parts, double t, doub
 
 /* nsteps diffusion-only steps (module_diffusion_turb + module_diffusion_meso +
  * module_position): subgrid variance and displacement at the current position.
- * Random numbers: Philox4x32-10, counter (id, step0 + n, stream 0|1, release),
+ * Random numbers: Philox4x32-10, counter (id, step0 + n, stream 0|1, release)
+ * with the low 32 bits of step0 + n (the draws repeat after 2^32 steps),
  * key (seed low, seed high words).  up/vp/wp must be non-NULL when
  * prm->meso != 0.  Same time-range rule as mptrac_advect. */
 int mptrac_diffuse(mptrac_ctx* ctx, const mptrac_particles* parts, double t, double dt,

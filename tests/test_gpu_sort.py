@@ -87,3 +87,21 @@ def test_keys_next_to_cell_faces(M):
     ref = osort.sort_state(grid, st)
     for k in ("lon", "lat", "p", "id"):
         np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
+
+
+@pytest.mark.parametrize("n", [0, 3000])
+def test_all_keys_equal_keeps_the_order(M, n):
+    """Every particle in one cell (one key): the stable sort leaves the arrays as they are;
+    an empty set is a no-op."""
+    grid = grid_2deg_20lev()
+    ctx = _ctx(M, grid)
+    st = uniform_particles(n, grid.plev, seed=5)
+    st["lon"][:], st["lat"][:], st["p"][:] = 123.4, -56.7, 45000.0
+    st["id"] = np.random.default_rng(1).permutation(n).astype(np.uint32)
+    st["up"] = np.arange(n, dtype=np.float32)
+    parts = M.Particles.from_numpy(st)
+    ctx.sort(parts)
+    torch.cuda.synchronize()
+    got = parts.to_numpy()
+    for k in ("lon", "lat", "p", "id", "release", "up"):
+        np.testing.assert_array_equal(got[k], st[k], err_msg=k)

@@ -304,3 +304,18 @@ def test_minimum_grid_and_long_steps(M, dt):
     assert_positions_close(got, ref, what=f"2x2x2 grid, dt {dt}", lon_metric="arc")
     keys = ctx.cell_keys(parts).cpu().numpy()
     np.testing.assert_array_equal(keys, osort.cell_keys(grid, got["lon"], got["lat"], got["p"]))
+
+
+def test_step_counter_wraps_at_32_bits(M, fourier):
+    """The random-number counter takes the low 32 bits of step0 + n: a run whose global step
+    crosses 2^32 matches the oracle, whose counter words are 32-bit too."""
+    grid, f0, f1 = fourier
+    ctx = make_ctx(M, grid, [f0, f1], [0.0, T6H])
+    met = tr.Met(grid, 0.0, f0, T6H, f1)
+    st0 = uniform_particles(2000, grid.plev, seed=43)
+    parts = M.Particles.from_numpy(st0)
+    step0 = 2**32 - 3
+    ctx.step(parts, 0.0, 180.0, M.DiffParams(), 11, step0, 6)
+    torch.cuda.synchronize()
+    ref = tr.step(met, st0, 0.0, 180.0, tr.DiffParams(), 11, step0, 6)
+    assert_positions_close(parts.to_numpy(), ref, what="step counter wrap", lon_metric="arc")
