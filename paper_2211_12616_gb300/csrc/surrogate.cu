@@ -991,13 +991,13 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc(const GemmArgs g) {
     tc_fence_after();
     const uint32_t tbase = *tmem_slot;
     const int nchunks = kend > kb0 ? (int)((kend - kb0 + GT_K - 1) / GT_K) : 0;
-    uint32_t waits[2] = {0u, 0u};   // completed waits per stage: the parity of the next
+    uint32_t waits0 = 0u, waits1 = 0u;   // completed waits per stage: the parity of the next
     bool failed = false;
     for (int i = 0; i < nchunks; ++i) {
         const int st = i & 1;
         if (i >= 2) {   // the MMAs of chunk i - 2 have read this stage
-            const bool ok = mbar_wait(smem_u32(&mbar[st]), waits[st] & 1u, g.wait_cycles);
-            ++waits[st];
+            const bool ok = mbar_wait(smem_u32(&mbar[st]), (st ? waits1 : waits0) & 1u, g.wait_cycles);
+            if (st) ++waits1; else ++waits0;
             if (__syncthreads_or(!ok)) {
                 failed = true;
                 break;
@@ -1023,15 +1023,14 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc(const GemmArgs g) {
         }
     }
     // drain: every commit of both stages has arrived (the last one covers every MMA)
-    for (int st = 0; st < 2 && !failed; ++st) {
+#pragma unroll
+    for (int st = 0; st < 2; ++st) {
         const uint32_t commits = (uint32_t)((nchunks + 1 - st) / 2);
-        while (waits[st] < commits) {
-            const bool ok = mbar_wait(smem_u32(&mbar[st]), waits[st] & 1u, g.wait_cycles);
-            ++waits[st];
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                break;
-            }
+        uint32_t& waits = st ? waits1 : waits0;
+        while (!failed && waits < commits) {
+            const bool ok = mbar_wait(smem_u32(&mbar[st]), waits & 1u, g.wait_cycles);
+            ++waits;
+            if (__syncthreads_or(!ok)) failed = true;
         }
     }
     if (!failed && nchunks > 0) {
