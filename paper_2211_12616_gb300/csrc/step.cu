@@ -184,13 +184,6 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// top 23 bits m -> (m + 1/2) 2^-23 in (0, 1): the float with exponent 0 and
-// mantissa m is 1 + m 2^-23, and subtracting 1 - 2^-24 from it is exact
-// (the difference (2m + 1) 2^-24 has at most 24 significant bits).
-__device__ __forceinline__ float u23(uint32_t x) {
-    return __fsub_rn(__uint_as_float(0x3F800000u | (x >> 9)), 0.999999940395355224609375f);
-}
-
 // Philox4x32-10 with the key schedule taken from the launch arguments
 // (round r uses ks[2r], ks[2r + 1]).
 __device__ __forceinline__ uint4 philox4x32_10_ks(uint4 c, const uint32_t* ks) {
@@ -204,22 +197,30 @@ __device__ __forceinline__ uint4 philox4x32_10_ks(uint4 c, const uint32_t* ks) {
     return c;
 }
 
-// Box-Muller pair from two words.  -ln(u) comes from the hardware log2 where
-// it is at least 2^-6 (relative error ~1e-7 there) and from the series
-// t + t^2/2 + t^3/3 + t^4/4 of -ln(1 - t), t = 1 - u (exact), below that
-// (truncation < t^5/5 relative, < 2e-8); the angle 2 pi u_b is shifted to
-// (-pi, pi) where the hardware sine/cosine have absolute error < 4e-7.
+// Box-Muller pair from two words, z = -r (cos th, sin th) with r^2 = -2 ln u_a
+// and th = 2 pi (u_b - 1/2).  A word's top 23 bits m give the uniform
+// (m + 1/2) 2^-23 in (0, 1) as F - (1 - 2^-24), F = 1 + m 2^-23 the float with
+// exponent 0 and mantissa m; the difference (2m + 1) 2^-24 has at most 24
+// significant bits, so it is exact, and so is t = 1 - u_a.  r^2 comes from the hardware
+// log2 where u_a >= 1 - 2^-6 does not hold (relative error ~1e-7 there) and
+// from the series 2 (t + t^2/2 + t^3/3 + t^4/4) of -2 ln(1 - t) below that
+// (truncation < t^5/5 relative, < 2e-8); the factor 2 sits in the
+// coefficients, which doubles every rounded step exactly.  The angle is one
+// multiply-add on F_b, 2 pi F_b - 2 pi (3/2 - 2^-24), in (-pi, pi) where the
+// hardware sine/cosine have absolute error < 4e-7; its own rounding adds
+// < 1e-6.
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1) {
-    const float ua = u23(a), ub = u23(b);
-    const float t = 1.0f - ua;
-    float nl;
+    const float Fa = __uint_as_float(0x3F800000u | (a >> 9));
+    const float Fb = __uint_as_float(0x3F800000u | (b >> 9));
+    const float ua = __fsub_rn(Fa, 0.999999940395355224609375f);
+    const float t = __fsub_rn(1.0f, ua);
+    float r2;
     if (t < 0.015625f)
-        nl = t * fmaf(t, fmaf(t, fmaf(t, 0.25f, 0.33333333333333333f), 0.5f), 1.0f);
+        r2 = t * fmaf(t, fmaf(t, fmaf(t, 0.5f, 0.66666666666666667f), 1.0f), 2.0f);
     else
-        nl = -__log2f(ua) * 0.69314718055994531f;
-    const float r2 = 2.0f * nl;
+        r2 = __log2f(ua) * -1.3862943611198906f;
     const float r = r2 * rsqrtf(r2);
-    const float th = 6.2831853071795865f * (ub - 0.5f);
+    const float th = fmaf(6.2831853071795865f, Fb, -9.424777586262351f);
     float sn, cs;
     __sincosf(th, &sn, &cs);
     z0 = -r * cs;
