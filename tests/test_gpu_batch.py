@@ -29,11 +29,15 @@ def _at(snaps):
 
 
 def test_sort_at_matches_oracle(M, case):
+    """Times before every release, at the start, in the middle, and after every release has
+    ended (nothing active: every key is the same and the order is kept); some particles
+    carry a release index beyond the table (never active)."""
     grid, snaps, rel = case
     ctx = M.Context(grid)
-    st = rel.particles
+    st = {k: v.copy() for k, v in rel.particles.items()}
+    st["release"][::53] = len(rel.t_start) + 3
     ctx.set_releases(rel.t_start, rel.t_end)
-    for t in (0.0, 5 * 3600.0, 9 * 3600.0):
+    for t in (-3600.0, 0.0, 5 * 3600.0, 9 * 3600.0, 1e7):
         parts = M.Particles.from_numpy(st)
         ctx.sort_at(parts, t)
         torch.cuda.synchronize()

@@ -95,3 +95,35 @@ def test_sedimentation_needs_temperature(M):
     with pytest.raises(M.MptracError) as e:
         ctx.sediment(parts, one, one, 0.0, 0.1, 1)
     assert e.value.code == -1
+
+
+def test_sampling_and_settling_at_degenerate_positions(M):
+    """Met sampling and sedimentation from the poles, the longitude seam, grid nodes, the top
+    and bottom levels and pressures outside the level range (clamped), against the oracle."""
+    from oracle import sedi
+    grid = grid_global(90, 46, 25)
+    m = fourier_modes(8, with_T=True)
+    f0, f1 = fourier_snapshot(grid, m, 0.0), fourier_snapshot(grid, m, T6H)
+    ctx = make_ctx(M, grid, [f0, f1], [0.0, T6H], nvars=4)
+    lats = [90.0, -90.0, 89.99999, 0.0, 44.0]
+    lons = [0.0, 359.99999999999994, 180.0, 4.0]
+    ps = [grid.plev[0], grid.plev[-1], grid.plev[0] * 1.1, grid.plev[-1] * 0.8, grid.plev[12]]
+    L = np.array([(lo, la, p) for la in lats for lo in lons for p in ps])
+    st = uniform_particles(len(L), grid.plev, seed=3)
+    st["lon"], st["lat"], st["p"] = L[:, 0].copy(), L[:, 1].copy(), L[:, 2].copy()
+    parts = M.Particles.from_numpy(st, meso=False)
+    out = ctx.sample_met(parts, 5400.0).cpu().numpy()
+    ref = meteo.sample(grid, f0, 0.0, f1, T6H, 5400.0, st["lon"], st["lat"], st["p"])
+    for i, (v, scale) in enumerate((("u", 20.0), ("v", 20.0), ("w", 0.5), ("T", 300.0))):
+        assert np.all(np.isfinite(out[i])), v
+        assert np.abs(out[i] - ref[v]).max() < 8e-5 * scale, v
+    r = np.full(len(L), 5e-6, np.float32)
+    rho_p = np.full(len(L), 2000.0, np.float32)
+    ctx.sediment(parts, torch.from_numpy(r).cuda(), torch.from_numpy(rho_p).cuda(), 600.0, 60.0, 10)
+    torch.cuda.synchronize()
+    got = parts.to_numpy()
+    refp = sedi.sediment(grid, f0["T"], 0.0, f1["T"], T6H, st, r.astype(np.float64), rho_p.astype(np.float64),
+                         600.0, 60.0, 10)
+    assert np.all(np.isfinite(got["p"]))
+    np.testing.assert_allclose(got["p"], refp, rtol=1e-4)
+    assert np.all((got["p"] >= grid.plev[-1]) & (got["p"] <= grid.plev[0]))
