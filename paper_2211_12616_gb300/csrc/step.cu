@@ -236,7 +236,7 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, fl
 template <int NSC>
 struct SmemT {
     float plev[kMaxNZ];
-    float inv_dp[kMaxNZ];
+    float4 lv[kMaxNZ];     // level k: (plev[k], plev[k + 1], 1 / (plev[k] - plev[k + 1]), 0)
     int16_t kguess[kGuessBins];
     float2 sc[3][NSC];     // scales of u, v, omega per level as pairs (slot 0, slot 1)
 };
@@ -295,10 +295,19 @@ __device__ __forceinline__ Cell locate(float lon, ff d, float p, const Geo& g, c
         b = min(max(b, 0), g.nbins - 1);
         k = s.kguess[b];
     }
-    while (k > 0 && s.plev[k] < pc) --k;
-    while (k < g.nz - 2 && s.plev[k + 1] >= pc) ++k;
+    // one 16-byte load gives both bounds of level k and the inverse spacing; the
+    // walk to another level (rare: the level of the previous evaluation is the
+    // first guess) reloads it
+    float4 e = s.lv[k];
+    if (k > 0 && e.x < pc) {
+        do { --k; } while (k > 0 && s.plev[k] < pc);
+        e = s.lv[k];
+    } else if (k < g.nz - 2 && e.y >= pc) {
+        do { ++k; } while (k < g.nz - 2 && s.plev[k + 1] >= pc);
+        e = s.lv[k];
+    }
     c.k = k;
-    c.fz = clamp01((s.plev[k] - pc) * s.inv_dp[k]);
+    c.fz = clamp01((e.x - pc) * e.z);
     c.gz = 1.f - c.fz;
     return c;
 }
@@ -562,7 +571,7 @@ __device__ __forceinline__ void load_tables(SmemT<NSC>& s, const Geo& g, const f
                                             bool scales) {
     for (int q = threadIdx.x; q < g.nz; q += blockDim.x) {
         s.plev[q] = g.plev[q];
-        s.inv_dp[q] = g.inv_dp[q];
+        s.lv[q] = make_float4(g.plev[q], q + 1 < g.nz ? g.plev[q + 1] : g.plev[q], g.inv_dp[q], 0.f);
     }
     for (int q = threadIdx.x; q < g.nbins; q += blockDim.x) s.kguess[q] = g.kguess[q];
     if (NSC > 1 && scales) {
