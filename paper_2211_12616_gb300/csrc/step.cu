@@ -184,11 +184,17 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// Philox4x32-10 with the key schedule taken from the launch arguments
-// (round r uses ks[2r], ks[2r + 1]).
-__device__ __forceinline__ uint4 philox4x32_10_ks(uint4 c, const uint32_t* ks) {
+// Philox4x32-10 of the counter (id, step, stream, release) under the key
+// schedule taken from the launch arguments (round r uses ks[2r], ks[2r + 1]),
+// entered after round 0.  Round 0 multiplies the id word, which does not change
+// with the step, and the stream word, a constant (0 or 1): its state is
+// (step ^ ks[0], lo(M1 stream), hi(M0 id) ^ release ^ ks[1], lo(M0 id)), whose
+// last two words (r0z, r0w) are formed once per particle.
+__device__ __forceinline__ uint4 philox_after_round0(uint32_t step, uint32_t stream, uint32_t r0z, uint32_t r0w,
+                                                     const uint32_t* ks) {
+    uint4 c = make_uint4(step ^ ks[0], stream ? 0xCD9E8D57u : 0u, r0z, r0w);
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
+    for (int r = 1; r < 10; ++r) {
         uint32_t hi0, lo0, hi1, lo1;
         mul_wide(0xD2511F53u, c.x, hi0, lo0);
         mul_wide(0xCD9E8D57u, c.z, hi1, lo1);
@@ -632,17 +638,25 @@ struct Normals {
     float m0, m1, m2;   // mesoscale: u, v, omega
 };
 
+// Round-0 words of a particle's counters (see philox_after_round0).
+struct Round0 {
+    uint32_t z, w;
+};
+__device__ __forceinline__ Round0 round0(const StepArgs& a, uint32_t pid, uint32_t rel) {
+    uint32_t hi, lo;
+    mul_wide(0xD2511F53u, pid, hi, lo);
+    return {hi ^ rel ^ a.ks[1], lo};
+}
+
 // draw 0: the turbulent normals and the first mesoscale one
-__device__ __forceinline__ void draw_turb(const StepArgs& a, uint32_t pid, uint32_t step, uint32_t rel,
-                                          Normals& z) {
-    const uint4 wd = philox4x32_10_ks(make_uint4(pid, step, 0u, rel), a.ks);
+__device__ __forceinline__ void draw_turb(const StepArgs& a, Round0 r0, uint32_t step, Normals& z) {
+    const uint4 wd = philox_after_round0(step, 0u, r0.z, r0.w, a.ks);
     box_muller(wd.x, wd.y, z.t0, z.t1);
     box_muller(wd.z, wd.w, z.t2, z.m0);
 }
 // draw 1: the other two mesoscale normals
-__device__ __forceinline__ void draw_meso(const StepArgs& a, uint32_t pid, uint32_t step, uint32_t rel,
-                                          Normals& z) {
-    const uint4 wd = philox4x32_10_ks(make_uint4(pid, step, 1u, rel), a.ks);
+__device__ __forceinline__ void draw_meso(const StepArgs& a, Round0 r0, uint32_t step, Normals& z) {
+    const uint4 wd = philox_after_round0(step, 1u, r0.z, r0.w, a.ks);
     box_muller(wd.x, wd.y, z.m1, z.m2);
 }
 
@@ -718,6 +732,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
         ff d = ff_make(a.lat[idx] - g.lat0_d);   // latitude as d = lat - lat0
         ff p = ff_make(a.p[idx]);
         const uint32_t pid = a.id[idx];
+        const Round0 r0 = round0(a, pid, rel);
         float up = 0.f, vp = 0.f, wp = 0.f;
         Cache cc;
         cc.init(s_cc);
@@ -733,8 +748,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
             // parts compiled in they are made first, so that their integer
             // work interleaves with the dependent chain of the advection.
             if (EARLY_DRAWS) {
-                draw_turb(a, pid, step, rel, z);
-                draw_meso(a, pid, step, rel, z);
+                draw_turb(a, r0, step, z);
+                draw_meso(a, r0, step, z);
             }
             // increments of this step (lon and lat in degrees, p in Pa)
             float ilon = 0.f, ilat = 0.f, ip = 0.f;
@@ -769,8 +784,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
             if (MODE != MODE_ADVECT && (use_turb || use_meso)) {
                 // ---- module_diffusion_turb / module_diffusion_meso ----
                 // at the position after advection: lat + ilat, p + ip
-                if (!EARLY_DRAWS && (use_turb || use_meso)) draw_turb(a, pid, step, rel, z);
-                if (!EARLY_DRAWS && use_meso) draw_meso(a, pid, step, rel, z);
+                if (!EARLY_DRAWS && (use_turb || use_meso)) draw_turb(a, r0, step, z);
+                if (!EARLY_DRAWS && use_meso) draw_meso(a, r0, step, z);
                 float dxm = 0.f, dym = 0.f, dpp = 0.f;
                 if (use_turb) {
                     dxm = a.sh * z.t0;
