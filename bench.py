@@ -221,7 +221,7 @@ def run_reference(args, rank, world):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config(n_sample, {"oracle_sample_particles": n_sample}),
+            "config": _config(args.particles, {"oracle_sample_particles": n_sample}),
             "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": workers, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
