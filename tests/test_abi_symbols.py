@@ -65,3 +65,24 @@ def test_invalid_grid_rejected_on_host(lib):
     assert lib.mptrac_init_grid(ctypes.byref(h), ctypes.byref(gd)) == -1
     assert lib.mptrac_sort_workspace_bytes(None, 1000) >= 60 * 1000
     assert lib.mptrac_destroy(None) == 0
+
+
+def test_binding_constants_match_the_header():
+    """The constants the Python binding hard-codes equal the #defines of include/mptrac.h."""
+    import pathlib
+    import re
+
+    import paper_2211_12616_gb300._native as N
+    hdr = (pathlib.Path(__file__).resolve().parents[1] / "include" / "mptrac.h").read_text()
+    d = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+MPTRAC_(\w+)\s+(-?\d+)", hdr)}
+    assert (N.MPTRAC_FP32, N.MPTRAC_BF16, N.MPTRAC_FP16) == (d["FP32"], d["BF16"], d["FP16"])
+    assert N.MAX_NZ == d["MAX_NZ"]
+    assert (N.SURR_NFEAT, N.SURR_KPAD, N.SURR_HIDDEN, N.SURR_NOUT, N.SURR_NPARAM) == (
+        d["SURR_NFEAT"], d["SURR_KPAD"], d["SURR_HIDDEN"], d["SURR_NOUT"], d["SURR_NPARAM"])
+    assert (N.SURR_KERNEL_TCGEN05, N.SURR_KERNEL_MMA_SYNC, N.SURR_KERNEL_WAIT_TEST) == (
+        d["SURR_KERNEL_TCGEN05"], d["SURR_KERNEL_MMA_SYNC"], d["SURR_KERNEL_WAIT_TEST"])
+    for code, name in N.STATUS.items():
+        assert d[name] == code, name
+    # the surrogate's parameter count follows from its layer sizes
+    assert d["SURR_NPARAM"] == d["SURR_KPAD"] * d["SURR_HIDDEN"] + d["SURR_HIDDEN"] + \
+        d["SURR_HIDDEN"] ** 2 + d["SURR_HIDDEN"] + d["SURR_HIDDEN"] * d["SURR_NOUT"] + d["SURR_NOUT"]
