@@ -86,3 +86,21 @@ def test_binding_constants_match_the_header():
     # the surrogate's parameter count follows from its layer sizes
     assert d["SURR_NPARAM"] == d["SURR_KPAD"] * d["SURR_HIDDEN"] + d["SURR_HIDDEN"] + \
         d["SURR_HIDDEN"] ** 2 + d["SURR_HIDDEN"] + d["SURR_HIDDEN"] * d["SURR_NOUT"] + d["SURR_NOUT"]
+
+
+def test_binding_signatures_match_the_header_prototypes():
+    """Every prototype of include/mptrac.h has a binding with the same number of arguments,
+    and the binding declares nothing the header does not."""
+    import pathlib
+    import re
+
+    import paper_2211_12616_gb300._native as N
+    hdr = (pathlib.Path(__file__).resolve().parents[1] / "include" / "mptrac.h").read_text()
+    code = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    protos = {}
+    for m in re.finditer(r"\b(mptrac_\w+)\s*\(([^;{}]*?)\)\s*;", code, flags=re.S):
+        args = m.group(2).strip()
+        protos[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    assert set(protos) == set(N.SIGNATURES)
+    for name, (_, argtypes) in N.SIGNATURES.items():
+        assert len(argtypes) == protos[name], name
