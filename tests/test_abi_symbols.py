@@ -104,3 +104,12 @@ def test_binding_signatures_match_the_header_prototypes():
     assert set(protos) == set(N.SIGNATURES)
     for name, (_, argtypes) in N.SIGNATURES.items():
         assert len(argtypes) == protos[name], name
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libmptrac.so the binding raises; there is no CPU fallback."""
+    import paper_2211_12616_gb300._native as N
+    monkeypatch.setattr(N, "_lib", None)
+    monkeypatch.setattr(N, "LIB_PATH", str(tmp_path / "libmptrac.so"))
+    with pytest.raises(ImportError, match="no CPU fallback"):
+        N.load()
