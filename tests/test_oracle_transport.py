@@ -206,3 +206,25 @@ def test_fused_step_identities():
     d = tr.step(met0, st0, 0.0, 180.0, prm, 9, 3, 7)
     for k in ("lon", "lat", "p", "up"):
         np.testing.assert_array_equal(c[k], d[k])
+
+
+def test_schedule_over_intervals_equals_one_long_run():
+    """The interval driver on a time-independent field equals one fused run over the whole
+    span with the global step index running on (the second interval starts at step 120):
+    counters and interval boundaries add nothing of their own.  Turbulent diffusion only:
+    the mesoscale memory r = 1 - 2 dt/(t1 - t0) depends on the interval length by its
+    definition, so it differs between one 12 h interval and two of 6 h."""
+    from oracle.driver import run_schedule
+    from workloads import uniform_particles
+    grid = grid_2deg_20lev()
+    snap = cfg1_snapshot(grid)
+    st0 = uniform_particles(300, grid.plev, seed=3, lat_max=80.0)
+    st0["up"] = np.zeros(300)
+    st0["vp"] = np.zeros(300)
+    st0["wp"] = np.zeros(300)
+    prm = tr.DiffParams(meso=False)
+    a = run_schedule(grid, lambda t: snap, 21600.0, st0, 0.0, 2 * 21600.0, 180.0, prm, 9)
+    met = tr.Met(grid, 0.0, snap, 2 * 21600.0, snap)
+    b = tr.step(met, st0, 0.0, 180.0, prm, 9, 0, 240)
+    for k in ("lon", "lat", "p"):
+        np.testing.assert_allclose(a[k], b[k], rtol=0, atol=1e-9)
