@@ -25,6 +25,15 @@ z2 = h1 W2 + b2, h2 = gelu(z2);  y_hat = h2 W3 + b3;  y = y_hat sd_y + mu_y,
 with gelu(x) = x/2 (1 + erf(x/sqrt 2)).  Loss: mean over samples and the 3
 outputs of (y_hat - (y_target - mu_y)/sd_y)^2.  Optimiser: Adam (Kingma & Ba,
 2015) with bias correction.
+
+The network is a BF16 network: every operand of its matrix products is a
+bfloat16 value, accumulated exactly (here: in float64).  ``forward`` and
+``loss_and_grads`` take that rounding as ``rnd`` (``bf16_round``; None = no
+rounding, the real-valued network).  With it, the forward pass rounds the
+hidden activations h1, h2 before they enter the next product, and the backward
+pass rounds the upstream gradients dy, dz2, dz1 before they enter theirs; each
+bias gradient is the column sum of the same rounded gradient that its layer's
+weight gradient uses.  The caller rounds the weights and x_hat.
 """
 from __future__ import annotations
 
@@ -130,27 +139,49 @@ def normalise(X, mu, sd):
     return (np.asarray(X, np.float64) - mu) / sd
 
 
-def forward(P, xh):
+def bf16_round(x):
+    """Nearest bfloat16 value (8 significant bits), ties to even; finite normal inputs and zero."""
+    m, e = np.frexp(np.asarray(x, np.float64))
+    return np.ldexp(np.round(np.ldexp(m, 8)), e - 8)
+
+
+def _identity(a):
+    return a
+
+
+def forward(P, xh, rnd=None):
+    """Normalised outputs and the activations (xh, z1, h1, z2, h2), h before rounding."""
+    r = rnd or _identity
     z1 = xh @ P["W1"] + P["b1"]
     h1 = gelu(z1)
-    z2 = h1 @ P["W2"] + P["b2"]
+    z2 = r(h1) @ P["W2"] + P["b2"]
     h2 = gelu(z2)
-    yh = h2 @ P["W3"] + P["b3"]
+    yh = r(h2) @ P["W3"] + P["b3"]
     return yh, (xh, z1, h1, z2, h2)
 
 
-def loss_and_grads(P, xh, yt_hat):
-    """MSE loss in normalised units and its gradients with respect to every parameter."""
-    yh, (x, z1, h1, z2, h2) = forward(P, xh)
+def loss_and_grads(P, xh, yt_hat, rnd=None, trace=None):
+    """MSE loss in normalised units and its gradients with respect to every parameter.
+
+    ``trace`` (a dict, optional) receives the forward activations and the
+    upstream gradients dy, dz2, dz1 before rounding.
+    """
+    r = rnd or _identity
+    yh, (x, z1, h1, z2, h2) = forward(P, xh, rnd)
     n = xh.shape[0]
-    r = yh - yt_hat
-    loss = float(np.mean(r * r))
-    dy = 2.0 * r / (n * NOUT)
-    g = {"W3": h2.T @ dy, "b3": dy.sum(axis=0)}
-    dz2 = (dy @ P["W3"].T) * gelu_grad(z2)
-    g["W2"], g["b2"] = h1.T @ dz2, dz2.sum(axis=0)
-    dz1 = (dz2 @ P["W2"].T) * gelu_grad(z1)
+    res = yh - yt_hat
+    loss = float(np.mean(res * res))
+    dy_raw = 2.0 * res / (n * NOUT)
+    dy = r(dy_raw)
+    g = {"W3": r(h2).T @ dy, "b3": dy.sum(axis=0)}
+    dz2_raw = (dy @ P["W3"].T) * gelu_grad(z2)
+    dz2 = r(dz2_raw)
+    g["W2"], g["b2"] = r(h1).T @ dz2, dz2.sum(axis=0)
+    dz1_raw = (dz2 @ P["W2"].T) * gelu_grad(z1)
+    dz1 = r(dz1_raw)
     g["W1"], g["b1"] = x.T @ dz1, dz1.sum(axis=0)
+    if trace is not None:
+        trace.update(yh=yh, z1=z1, h1=h1, z2=z2, h2=h2, dy=dy_raw, dz2=dz2_raw, dz1=dz1_raw)
     return loss, g
 
 

@@ -337,8 +337,10 @@ int mptrac_init_grid(mptrac_ctx** out, const mptrac_grid_desc* g) {
         kg[b] = (int16_t)k;
     }
     c->rec_bytes = (size_t)npts * (g->storage == MPTRAC_FP32 ? 16 : 8);
+    // npts < 2^31 (checked above), so key_bits <= 31: cell keys and the release-aware sort's
+    // inactive key 2^key_bits fit a 32-bit word.
     c->key_bits = 0;
-    while (c->key_bits < 32 && ((uint64_t)1 << c->key_bits) < (uint64_t)npts) ++c->key_bits;
+    while (c->key_bits < 31 && ((uint64_t)1 << c->key_bits) < (uint64_t)npts) ++c->key_bits;
 
     auto alloc = [&](void** p, size_t bytes) -> int {
         cudaError_t ee = cudaMalloc(p, bytes);

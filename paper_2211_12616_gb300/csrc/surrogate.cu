@@ -292,7 +292,7 @@ __global__ void k_normalise(const float* __restrict__ X, int64_t n, const float*
 }
 
 // loss = mean (y_hat - t_hat)^2 over the 3 outputs; dY = 2 (y_hat - t_hat)/(3B) (bf16, 8 columns);
-// db3 += column sums of dY (float32)
+// db3 += column sums of the bf16 dY (the operand the W3 gradient uses), summed in float32
 __global__ void k_loss(const float* __restrict__ Yh, const float* __restrict__ Yt, int64_t B,
                        const float* mu_y, const float* isd_y, __nv_bfloat16* dY, float* loss, float* db3) {
     __shared__ float red[4][32];
@@ -305,8 +305,9 @@ __global__ void k_loss(const float* __restrict__ Yh, const float* __restrict__ Y
         for (int j = 0; j < NO; ++j) {
             const float r = Yh[q * NOP + j] - (Yt[q * NO + j] - mu_y[j]) * isd_y[j];
             l += r * r;
-            dd[j] = scale * r;
-            dY[q * NOP + j] = __float2bfloat16_rn(dd[j]);
+            const __nv_bfloat16 g = __float2bfloat16_rn(scale * r);
+            dd[j] = __bfloat162float(g);
+            dY[q * NOP + j] = g;
         }
 #pragma unroll
         for (int j = NO; j < NOP; ++j) dY[q * NOP + j] = __float2bfloat16(0.f);

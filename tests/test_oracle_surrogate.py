@@ -135,3 +135,64 @@ def test_envelope():
     xh[3, 170] = 99.0        # padding is ignored
     lat = np.array([10.0, 10.0, 85.0, -20.0])
     np.testing.assert_array_equal(S.in_envelope(xh, lat), [True, False, False, True])
+
+
+def test_bf16_round_matches_torch_and_ties():
+    rng = np.random.default_rng(11)
+    x = (rng.standard_normal(20000) * np.exp(rng.uniform(-20, 20, 20000))).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(S.bf16_round(x.astype(np.float64)), ref)
+    # ties go to the even neighbour; 8 significant bits
+    cases = {1 + 2.0**-8: 1.0, 1 + 3 * 2.0**-8: 1 + 2.0**-6, 1 + 2.0**-7: 1 + 2.0**-7,
+             -(1 + 2.0**-8): -1.0, 0.0: 0.0, 3 * 2.0**-9: 3 * 2.0**-9, 255.5: 256.0, 257.0: 256.0}
+    for a, b in cases.items():
+        assert S.bf16_round(np.array([a]))[0] == b, (a, b)
+
+
+class _RoundValue(torch.autograd.Function):
+    """Rounds the value to bfloat16 (torch's cast); the gradient passes unchanged."""
+    @staticmethod
+    def forward(ctx, x):
+        return x.to(torch.bfloat16).to(torch.float64)
+
+    @staticmethod
+    def backward(ctx, g):
+        return g
+
+
+class _RoundGrad(torch.autograd.Function):
+    """Passes the value unchanged; rounds the incoming gradient to bfloat16."""
+    @staticmethod
+    def forward(ctx, x):
+        return x.clone()
+
+    @staticmethod
+    def backward(ctx, g):
+        return g.to(torch.bfloat16).to(torch.float64)
+
+
+def test_bf16_network_matches_torch_autograd_with_rounding_hooks():
+    """The BF16 network (rounded activations forward, rounded upstream gradients backward)
+    against torch autograd, whose chain rule sees the roundings only as value hooks."""
+    rng = np.random.default_rng(12)
+    P = {k: (S.bf16_round(v) if k.startswith("W") else v) for k, v in _params(2).items()}
+    xh = S.bf16_round(rng.standard_normal((96, S.KPAD)))
+    xh[:, S.NFEAT:] = 0
+    yt = rng.standard_normal((96, S.NOUT))
+    trace = {}
+    loss, g = S.loss_and_grads(P, xh, yt, rnd=S.bf16_round, trace=trace)
+    T = {k: torch.from_numpy(v.copy()).requires_grad_(True) for k, v in P.items()}
+    gel = lambda z: torch.nn.functional.gelu(z, approximate="none")
+    z1 = _RoundGrad.apply(torch.from_numpy(xh) @ T["W1"] + T["b1"])
+    z2 = _RoundGrad.apply(_RoundValue.apply(gel(z1)) @ T["W2"] + T["b2"])
+    y = _RoundGrad.apply(_RoundValue.apply(gel(z2)) @ T["W3"] + T["b3"])
+    tl = ((y - torch.from_numpy(yt)) ** 2).mean()
+    tl.backward()
+    assert abs(loss - tl.item()) < 1e-12
+    np.testing.assert_allclose(trace["yh"], y.detach().numpy(), rtol=1e-12, atol=1e-14)
+    for k in T:
+        np.testing.assert_allclose(g[k], T[k].grad.numpy(), rtol=1e-10, atol=1e-13, err_msg=k)
+    # the rounding changes the result (it is not a no-op here) but only by bf16 amounts
+    _, g0 = S.loss_and_grads(P, xh, yt)
+    rel = np.abs(g["W1"][:S.NFEAT] - g0["W1"][:S.NFEAT]).max() / np.abs(g0["W1"]).max()
+    assert 1e-5 < rel < 5e-2, rel
