@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -41,10 +42,10 @@ SEED_RNG = 2
 # captures of full-size launches of variant 2 with the hand-off to the sort (see
 # profiles/).  A schedule without a capture reports None, and so does any launch
 # after the kernel changes, until it is captured again.
-TRAFFIC_PER_LAUNCH = {2: 156724480}   # 142.14 MB read + 14.58 MB written, 5e5 particles (two groups)
+TRAFFIC_PER_LAUNCH = {2: 156415232}   # 142.14 MB read + 14.27 MB written, 5e5 particles (two groups)
 # sha256 (first 16 hex digits) of the fused step's sources when the counters
 # were taken; a different hash means the kernel changed and traffic is None
-TRAFFIC_KERNEL_SHA = "0fe44f9507e684ec"
+TRAFFIC_KERNEL_SHA = "a42e11224a29b6ba"
 TRAFFIC_SOURCES = ("paper_2211_12616_gb300/csrc/step.cu", "paper_2211_12616_gb300/csrc/internal.h",
                    "paper_2211_12616_gb300/csrc/cell_key.cuh", "paper_2211_12616_gb300/csrc/met_record.cuh")
 
@@ -124,22 +125,66 @@ class ClockSampler:
 
 
 # Algorithmic operations of one fused step of one particle (advection +
-# turbulent + mesoscale diffusion), counted from the formulas: one operation per
-# add, multiply, fused multiply-add, compare, conversion, integer op or
-# transcendental.  The kernel itself executes more instructions (addressing,
-# predication, clamps); this is the work the method needs.
+# turbulent + mesoscale diffusion), counted from the method's formulas, not from
+# the kernel: one operation per add, multiply, fused multiply-add, compare,
+# conversion or integer op.  The position update counts as the method states it
+# (three float64 additions), not as the float-float arithmetic that stands in for
+# them; the Philox key schedule is per seed, not per particle-step.  The kernel
+# executes more instructions (addressing, predication, clamps, float-float).
 ALU_OPS_PER_PARTICLE_STEP = {
-    "locate, 2 evaluations x (lon 5 + lat 5 + level 6)": 32,
-    "trilinear, 2 evaluations x 2 snapshots x 3 variables x 7 lerps x 2 + time lerps 2 x 6": 180,
-    "subgrid variance: weights 12 + 2 snapshots x 3 variables x 8 corners x 3 + time 6": 162,
-    "midpoint stages: cos(lat) 4 + 3 increments x 3, twice; midpoint position rules 6": 32,
-    "Philox4x32-10, 2 calls x 10 rounds x 8": 160,
-    "Box-Muller, 4 pairs x 16": 64,
+    "locate, 2 evaluations x (lon 5 + lat 5 + level search 6)": 32,
+    "trilinear, 2 evaluations x 2 snapshots x 3 variables x 7 lerps x 2 + time lerps 2 x 3 x 2": 180,
+    "subgrid variance: corner weights 12 + 2 snapshots x 3 variables x 8 corners x 3 + time lerps 6": 162,
+    "midpoint stages: 3 increments x 3, twice; midpoint position rules 6": 24,
+    "Philox4x32-10, 2 calls x 10 rounds x (2 wide multiplies = 4 + 4 xor)": 160,
+    "Box-Muller, 3 pairs x (2 uniforms x 2 + -2 ln u 1 + angle 1 + 2 products)": 24,
     "turbulent + mesoscale displacements and AR(1) update": 34,
-    "float-float position accumulation, 9 additions x 6": 54,
+    "position update: increments summed 3 x 2, then 3 float64 additions": 9,
     "position rules": 6,
 }
 ALU_OPS = sum(ALU_OPS_PER_PARTICLE_STEP.values())
+# transcendentals, charged against the special-function units' own rate
+MUFU_OPS_PER_PARTICLE_STEP = {
+    "cos(lat): midpoint stage 1, stage 2, diffusion conversion": 3,
+    "Box-Muller, 3 pairs x (log, sqrt, sin, cos)": 12,
+}
+MUFU_OPS = sum(MUFU_OPS_PER_PARTICLE_STEP.values())
+MUFU_PER_SM_PER_CLK = 16      # 4 results per clock on each of the SM's 4 sub-partitions
+# per-step stencil gather of the gather roofline: 2 evaluations x 8 corners x one
+# 32-byte pair record (a corner's u, v, omega, T on both snapshots, float32)
+L2_BYTES_PER_PARTICLE_STEP = 2 * 8 * 32
+# particle stream of one launch, per particle: lon, lat, p (float64) and u', v', w'
+# (float32) read and written, id and release id read
+PARTICLE_STREAM_BYTES = 2 * (3 * 8 + 3 * 4) + 2 * 4
+
+
+def measure_copy_gbs(dev, mb, reps):
+    """Bandwidth of mptrac_copy_probe on two buffers of ``mb`` MiB: read + write bytes of one launch
+    of ``reps`` repetitions (loads and stores cached in L2 only) over its CUDA-event time, the best
+    of 5 launches after 2 warm-up launches.  Changes no setting of the GPU."""
+    import torch
+
+    import paper_2211_12616_gb300 as M
+    n = mb * (1 << 20) // 4
+    a = torch.ones(n, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    best = 0.0
+    for i in range(7):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        M.copy_probe(a, b, reps)
+        e1.record()
+        torch.cuda.synchronize()
+        if i >= 2:
+            best = max(best, 2 * 4 * n * reps / (e0.elapsed_time(e1) / 1000.0) / 1e9)
+    del a, b
+    return best
+
+
+def measure_l2_gbs(dev):
+    """L2 bandwidth: the copy probe on source and destination of 8, 16 and 24 MiB each (resident in
+    L2 together), 100 repetitions per launch; the best size."""
+    return max(measure_copy_gbs(dev, mb, 100) for mb in (8, 16, 24))
 
 
 def _peaks():
@@ -149,6 +194,73 @@ def _peaks():
         return float(d["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+def great_circle_km(lon1, lat1, lon2, lat2):
+    """Haversine distance on the sphere of radius 6371 km (degrees in)."""
+    p1, p2 = np.radians(lat1), np.radians(lat2)
+    dl = np.radians(np.asarray(lon2) - np.asarray(lon1))
+    h = np.sin((p2 - p1) / 2) ** 2 + np.cos(p1) * np.cos(p2) * np.sin(dl / 2) ** 2
+    return 2 * 6371.0 * np.arcsin(np.sqrt(np.clip(h, 0.0, 1.0)))
+
+
+def final_subset(parts, n_sub):
+    """lon, lat, p of the particles with id < n_sub, in id order."""
+    d = parts.to_numpy()
+    keep = d["id"] < n_sub
+    o = np.argsort(d["id"][keep])
+    return {k: d[k][keep][o] for k in ("lon", "lat", "p")}
+
+
+def error_summary(got, ref):
+    km = great_circle_km(got["lon"], got["lat"], ref["lon"], ref["lat"])
+    dp = np.abs(got["p"] - ref["p"]) / ref["p"]
+    return {"km_median": float(np.median(km)), "km_p99": float(np.quantile(km, 0.99)), "km_max": float(km.max()),
+            "dp_rel_median": float(np.median(dp)), "dp_rel_p99": float(np.quantile(dp, 0.99))}
+
+
+# launch schedule of the batched form in the default line (the autotuner's choice on this
+# workload: register corner cache with 128 registers, one sort per met interval)
+BATCH_SCHEDULE = {"variant": 1, "persistent": False, "sort_every": 120}
+
+
+def storage_figures(dev, grid, snaps, init, best, steps, warmup, n_sub, fp32_ms):
+    """The headline workload with the met fields stored as bf16 or fp16 with level scales:
+    rate, speed-up over float32 storage, and the final positions of the first particles."""
+    import torch
+
+    import paper_2211_12616_gb300 as M
+    from paper_2211_12616_gb300.simulation import Simulation, periodic_snapshots
+
+    out, finals = {}, {}
+    stream = torch.cuda.Stream(device=dev)
+    for name, storage in (("bf16", M.MPTRAC_BF16), ("fp16", M.MPTRAC_FP16)):
+        ctx = M.Context(grid, storage)
+        ctx.set_launch(best["variant"], best["persistent"])
+        work = init.clone()
+        sim = Simulation(ctx, periodic_snapshots(snaps, DT_MET), DT_MET, work, DT, M.DiffParams(), SEED_RNG,
+                         SORT_EVERY, groups=best["groups"])
+
+        def one_pass():
+            with torch.cuda.stream(stream):
+                work.copy_(init)
+                sim.run(0.0, T_END, stream=stream)
+        for _ in range(warmup):
+            one_pass()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            one_pass()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        out[name] = {"ms_per_pass": ms, "particle_steps_per_s": init.n * (T_END / DT) / (ms / 1000.0),
+                     "speedup_vs_fp32": fp32_ms / ms, "slot_bytes": int(grid.npoints * 8)}
+        finals[name] = final_subset(work, n_sub)
+        ctx.close()
+        del sim, work
+    return out, finals
 
 
 # --------------------------------------------------------------------------
@@ -168,13 +280,14 @@ def _oracle_setup(offset: int, n: int):
 
 
 def oracle_sample_rate(n_sample: int, t_end: float = T_END):
-    """Times the FP64 oracle on the first ``n_sample`` particles of the workload (this process)."""
+    """Times the FP64 oracle on the first ``n_sample`` particles of the workload (this process);
+    returns (particle-steps/s, seconds, the oracle's final state of those particles)."""
     run = _oracle_setup(0, n_sample)
     t0 = time.perf_counter()
-    run(t_end)
+    final = run(t_end)
     el = time.perf_counter() - t0
     psteps = n_sample * (t_end / DT)
-    return psteps / el, el
+    return psteps / el, el, final
 
 
 def _oracle_worker(offset, n, t_end, barrier, out):
@@ -380,18 +493,39 @@ def run_ours(args, rank, world):
         e2e = {"value": aggregate_rate(psteps_per_pass * k2, world, ms2), "unit": "particle-steps/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
+    # ---- the added forms on the same GPU: 16-bit storage, batched releases, surrogate ----
+    forms, finals = None, {}
+    n_sub = int(os.environ.get("BENCH_ORACLE_SAMPLE", "8000"))
+    if world == 1 and not args.no_forms:
+        finals["fp32"] = final_subset(work, n_sub)
+        t_forms = time.perf_counter()
+        storage, f16 = storage_figures(dev, grid, snaps, init, best, max(1, args.steps // 2), 1, n_sub,
+                                       ms_max / args.steps)
+        finals.update(f16)
+        forms = {"storage": storage,
+                 "batch": batch_figures(dev, grid, snaps, 2, 1, schedule=BATCH_SCHEDULE),
+                 "surrogate": surrogate_figures(dev, grid, snaps, 10_000_000, 10_000_000, 4)}
+        forms["seconds"] = time.perf_counter() - t_forms
+        torch.cuda.empty_cache()
+
     if rank != 0:
         return
     hbm_peak, peak_kind = _peaks()
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = clk.get("sm_max_mhz") or 2070.0
+    kernel_rate = psteps_per_launch / (step_avg_ms / 1000.0)       # particle-steps/s of the step launches
     alu_peak = n_sm * 128 * sm_mhz * 1e6 / 1e12          # TOP/s: one op per lane per clock
-    alu_achieved = ALU_OPS * psteps_per_launch / (step_avg_ms / 1000.0) / 1e12
-    # per-step stencil gather (no reuse between steps): 2 evaluations x 2 snapshots x
-    # 8 corners x 16 B records + the particle stream spread over SORT_EVERY steps
-    stencil_b = 2 * 2 * 8 * 16
-    stream_b = (2 * (3 * 8 + 3 * 4) + 2 * 4) / SORT_EVERY
-    gather_rate = hbm_peak * 1e9 / (stencil_b + stream_b)
+    alu_achieved = ALU_OPS * kernel_rate / 1e12
+    mufu_peak = n_sm * MUFU_PER_SM_PER_CLK * sm_mhz * 1e6 / 1e12
+    mufu_achieved = MUFU_OPS * kernel_rate / 1e12
+    # the gather roofline: T = max(B_HBM / BW_HBM, B_L2 / BW_L2) per particle-step, with
+    # B_L2 the per-step stencil gather and B_HBM the particle stream plus the compulsory met
+    # bytes (every pair record of the interval read once per launch: an upper bound)
+    l2_gbs = measure_l2_gbs(dev)
+    stream_b = PARTICLE_STREAM_BYTES * (n / n_groups) / psteps_per_launch
+    met_b = 32.0 * grid.nx * grid.ny * grid.nz / psteps_per_launch
+    b_hbm = stream_b + met_b
+    t_roof = max(b_hbm / (hbm_peak * 1e9), L2_BYTES_PER_PARTICLE_STEP / (l2_gbs * 1e9))
     traffic = (TRAFFIC_PER_LAUNCH.get(n_groups)
                if best["variant"] == 2 and kernel_sha() == TRAFFIC_KERNEL_SHA else None)
     line = {
@@ -408,32 +542,50 @@ def run_ours(args, rank, world):
                      "timing": "union of the launch intervals (CUDA events on each group's stream) / launches",
                      "mean_event_ms_per_launch": sum(step_ms) / len(step_ms),
                      "ops_per_particle_step": ALU_OPS,
-                     "peak_kind": f"derived: {n_sm} SMs x 128 lanes x {sm_mhz:.0f} MHz, one op per lane per clock"},
-        "gather_roofline": {"bytes_per_particle_step": stencil_b + stream_b, "peak_gbs": hbm_peak,
-                            "peak_kind": f"{peak_kind} hbm_gbs",
-                            "roofline_particle_steps_per_s": gather_rate,
-                            "rate_over_bound": (psteps_per_launch / (step_avg_ms / 1000.0)) / gather_rate,
+                     "ops_counted": "the method's operations (bench.py ALU_OPS_PER_PARTICLE_STEP), not the kernel's",
+                     "peak_kind": f"derived: {n_sm} SMs x 128 lanes x {sm_mhz:.0f} MHz, one op per lane per clock",
+                     "mufu": {"ops_per_particle_step": MUFU_OPS, "achieved": mufu_achieved, "peak": mufu_peak,
+                              "unit": "TOP/s", "frac": mufu_achieved / mufu_peak,
+                              "peak_kind": f"derived: {n_sm} SMs x {MUFU_PER_SM_PER_CLK} per clock x "
+                                           f"{sm_mhz:.0f} MHz"}},
+        "gather_roofline": {"b_l2_per_particle_step": L2_BYTES_PER_PARTICLE_STEP, "l2_gbs": l2_gbs,
+                            "l2_kind": "measured here: device copy resident in L2 (read + write bytes)",
+                            "b_hbm_per_particle_step": b_hbm, "hbm_gbs": hbm_peak,
+                            "hbm_kind": f"{peak_kind} hbm_gbs",
+                            "t_roof_ns": t_roof * 1e9, "roofline_particle_steps_per_s": 1.0 / t_roof,
+                            "achieved_particle_steps_per_s": kernel_rate,
+                            "frac": kernel_rate * t_roof,
+                            "pass_frac": value * t_roof,
+                            "hbm_only_particle_steps_per_s": hbm_peak * 1e9 / b_hbm,
                             "hbm": ({"traffic_bytes_per_launch": traffic,
                                      "achieved_gbs": traffic / (step_avg_ms / 1000.0) / 1e9,
                                      "frac": traffic / (step_avg_ms / 1000.0) / 1e9 / hbm_peak}
                                     if traffic else None),
-                            "note": "per-step stencil gather without reuse between steps; the kernel keeps a "
-                                    "cell's corners in registers across steps and runs above that bound, so "
-                                    "the bounds that apply are the ALU roofline and the measured DRAM "
-                                    "traffic (hbm) against the copy bandwidth"},
+                            "note": "the per-step stencil gather term assumes no reuse between steps; the kernel "
+                                    "keeps a cell's corners in registers while the particle stays in the cell, "
+                                    "so it is bound by the ALU roofline, and the HBM-only bound is given beside"},
         "clocks": clk, "gpu_launches": int(launches),
         "e2e": e2e,
+        "forms": forms,
     }
     if not args.no_cpu_baseline:
         n_sample = int(os.environ.get("BENCH_ORACLE_SAMPLE", "8000"))
         workers = os.cpu_count() or 1
-        rate1, el1 = oracle_sample_rate(n_sample)
+        rate1, el1, oracle_final = oracle_sample_rate(n_sample)
         rate, el = oracle_all_cores(n_sample // 2, workers)
         line["cpu_baseline"] = {"value": rate, "unit": "particle-steps/s", "cores": workers, "kind": "oracle",
                                 "sample": f"{workers} processes x {n_sample // 2} particles of the 1e6 (disjoint), "
                                           f"full 24 h (480 steps), {el:.1f} s of numpy float64 on every host core",
                                 "single_core": {"value": rate1, "sample": f"first {n_sample} particles, "
                                                 f"full 24 h, {el1:.1f} s on one core"}}
+        # the oracle's final state of the same particles is the reference of the storage forms
+        if forms is not None and n_sample == n_sub:
+            for name, fin in finals.items():
+                err = error_summary(fin, oracle_final)
+                if name == "fp32":
+                    line["accuracy_vs_oracle"] = dict(err, particles=n_sub)
+                else:
+                    forms["storage"][name].update(err)
     print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -444,21 +596,20 @@ def run_ours(args, rank, world):
 BATCH_RELEASES, BATCH_SEED, BATCH_T_END = 64, 4, 72 * 3600.0
 
 
-def run_batch(args, rank, world):
+def batch_figures(dev, grid, snaps, steps, warmup, count_scale=1.0, schedule=None):
+    """Batched releases on one GPU: rate of the 72 h pass replayed from CUDA graphs.
+
+    ``schedule`` None: the autotuner picks the launch variant, persistence and sort interval
+    on one met interval; else that schedule (dict variant, persistent, sort_every)."""
     import torch
 
     import paper_2211_12616_gb300 as M
     from paper_2211_12616_gb300.autotune import autotune, candidates
     from paper_2211_12616_gb300.batch import BatchedRun
     from paper_2211_12616_gb300.simulation import periodic_snapshots
-    from workloads import column_releases, fourier_modes, fourier_snapshot, grid_1deg_60lev
+    from workloads import column_releases
 
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    torch.cuda.set_device(dev)
-    grid = grid_1deg_60lev()
-    modes = fourier_modes(SEED_FIELD)
-    snaps = [fourier_snapshot(grid, modes, h * DT_MET, device=dev, as_numpy=False) for h in range(4)]
-    rel = column_releases(BATCH_RELEASES, BATCH_SEED, count_scale=args.count_scale)
+    rel = column_releases(BATCH_RELEASES, BATCH_SEED, count_scale=count_scale)
     init = M.Particles.from_numpy(rel.particles, device=dev)
     work = init.clone()
     ctx = M.Context(grid, M.MPTRAC_FP32)
@@ -473,11 +624,13 @@ def run_batch(args, rank, world):
     def sched(cfg):   # the schedule keys BatchedRun takes (one particle group: graphs span all releases)
         return {k: cfg[k] for k in ("variant", "persistent", "sort_every")}
 
-    def make(cfg):
-        run = BatchedRun(ctx, at, DT_MET, work, rel.t_start, rel.t_end, DT, prm, SEED_RNG, **sched(cfg))
-        return lambda: run.run_eager(0.0, DT_MET, stream=stream)
-
-    best, timings = autotune(make, lambda: work.copy_(init), candidates(), stream, repeats=1)
+    if schedule is None:
+        def make(cfg):
+            run = BatchedRun(ctx, at, DT_MET, work, rel.t_start, rel.t_end, DT, prm, SEED_RNG, **sched(cfg))
+            return lambda: run.run_eager(0.0, DT_MET, stream=stream)
+        best, timings = autotune(make, lambda: work.copy_(init), candidates(), stream, repeats=1)
+    else:
+        best, timings = dict(schedule), None
     run = BatchedRun(ctx, at, DT_MET, work, rel.t_start, rel.t_end, DT, prm, SEED_RNG, **sched(best))
     work.copy_(init)
     run.run_eager(0.0, DT_MET, stream=stream)      # first-use set-up outside capture
@@ -489,34 +642,52 @@ def run_batch(args, rank, world):
             work.copy_(init)
             run.replay()
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         one_pass()
     torch.cuda.synchronize()
-    clocks = ClockSampler(dev.index)
-    clocks.start()
-    time.sleep(0.3)
     l0 = M.load().mptrac_kernel_launches()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         one_pass()
     b.record(stream)
     torch.cuda.synchronize()
-    ms = a.elapsed_time(b)
+    ms = a.elapsed_time(b) / steps
+    out = {"particle_steps_per_s": psteps / (ms / 1000.0), "ms_per_pass": ms, "particles": int(rel.counts.sum()),
+           "active_particle_steps_per_pass": psteps, "schedule": best, "autotuned": schedule is None,
+           "candidates_ms": timings, "host_launches_in_timed_region": int(M.load().mptrac_kernel_launches() - l0),
+           "workload": f"{BATCH_RELEASES} column releases (1-20 km), counts log-uniform 1e3-1e6 x {count_scale}, "
+                       "durations 6-72 h, 1deg 60-level field, 72 h, CUDA graph per met interval"}
+    run = None
+    ctx.close()
+    return out
+
+
+def run_batch(args, rank, world):
+    import torch
+
+    from workloads import fourier_modes, fourier_snapshot, grid_1deg_60lev
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    grid = grid_1deg_60lev()
+    modes = fourier_modes(SEED_FIELD)
+    snaps = [fourier_snapshot(grid, modes, h * DT_MET, device=dev, as_numpy=False) for h in range(4)]
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    time.sleep(0.3)
+    f = batch_figures(dev, grid, snaps, args.steps, args.warmup, args.count_scale)
     clk = clocks.stop()
-    line = {"metric": METRIC, "value": psteps * args.steps / (ms / 1000.0), "unit": "particle-steps/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+    line = {"metric": METRIC, "value": f["particle_steps_per_s"], "unit": "particle-steps/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": f["ms_per_pass"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"{BATCH_RELEASES} column releases (1-20 km), counts log-uniform 1e3-1e6 "
-                                   f"x {args.count_scale}, durations 6-72 h, 1deg 60-level field, 72 h, "
-                                   "CUDA graph per met interval, autotuned schedule",
-                       "particles": int(rel.counts.sum()), "active_particle_steps_per_pass": psteps,
-                       "autotuned": best, "candidates_ms": timings},
+            "config": {"workload": f["workload"] + ", autotuned schedule", "particles": f["particles"],
+                       "active_particle_steps_per_pass": f["active_particle_steps_per_pass"],
+                       "autotuned": f["schedule"], "candidates_ms": f["candidates_ms"]},
             "clocks": clk, "gpu_launches_captured": "graph replay (launch counter counts host launches only)",
-            "host_launches_in_timed_region": int(M.load().mptrac_kernel_launches() - l0)}
+            "host_launches_in_timed_region": f["host_launches_in_timed_region"]}
     print(json.dumps(line), flush=True)
-    ctx.close()
 
 
 # --------------------------------------------------------------------------
@@ -525,14 +696,65 @@ def run_batch(args, rank, world):
 PREC_T_END, PREC_SEED, PREC_N, PREC_SUB = 12 * 3600.0, 3, 10_000_000, 10_000
 
 
+PREC_HORIZONS = (3600.0, 21600.0, 43200.0)
+
+
+def _precision_subset_gpu(M, grid, snaps, storage, sub, diffuse):
+    """The subset stepped alone (its trajectories do not depend on other particles) on this
+    storage: states at every horizon, and u, v, omega, T sampled at the 12 h positions."""
+    import torch
+    ctx = M.Context(grid, storage, nvars=4)
+    for slot in (0, 1):
+        f = snaps[slot]
+        ctx.load_met(slot, slot * DT_MET, f["u"], f["v"], f["w"], f["T"])
+    parts = M.Particles.from_numpy(sub)
+    prm = M.DiffParams(turb=diffuse, meso=diffuse)
+    out, step, t = {}, 0, 0.0
+    for h in PREC_HORIZONS:
+        while t < h:
+            if t >= 2 * DT_MET - 1e-6:
+                raise ValueError("horizon beyond the loaded snapshots")
+            if t >= DT_MET - 1e-6 and step == int(round(DT_MET / DT)):
+                f = snaps[2]
+                ctx.load_met(2, 2 * DT_MET, f["u"], f["v"], f["w"], f["T"])
+            t_next = min(h, (math.floor(t / DT_MET + 1e-9) + 1) * DT_MET)
+            n_steps = int(round((t_next - t) / DT))
+            ctx.step(parts, t, DT, prm, SEED_RNG, step, n_steps)
+            step += n_steps
+            t = t_next
+        torch.cuda.synchronize()
+        d = parts.to_numpy()
+        o = np.argsort(d["id"])
+        out[h] = {k: d[k][o] for k in ("lon", "lat", "p")}
+    sampled = ctx.sample_met(parts, PREC_HORIZONS[-1]).cpu().numpy()[:, np.argsort(parts.to_numpy()["id"])]
+    ctx.close()
+    return out, sampled
+
+
+def _precision_oracle(grid, host, sub, diffuse):
+    """The float64 oracle on the subset: states at every horizon (the cpu_baseline leg)."""
+    from oracle import transport as tr
+    prm = tr.DiffParams(turb=diffuse, meso=diffuse)
+    mets = [tr.Met(grid, q * DT_MET, {k: host[q][k] for k in ("u", "v", "w")},
+                   (q + 1) * DT_MET, {k: host[q + 1][k] for k in ("u", "v", "w")}) for q in (0, 1)]
+    out, st, step, t = {}, sub, 0, 0.0
+    for h in PREC_HORIZONS:
+        while t < h:
+            q = int(math.floor(t / DT_MET + 1e-9))
+            t_next = min(h, (q + 1) * DT_MET)
+            n_steps = int(round((t_next - t) / DT))
+            st = tr.step(mets[q], st, t, DT, prm, SEED_RNG, step, n_steps)
+            step += n_steps
+            t = t_next
+        out[h] = {k: st[k] for k in ("lon", "lat", "p")}
+    return out
+
+
 def run_precision(args, rank, world):
     import torch
 
     import paper_2211_12616_gb300 as M
-    from oracle import transport as tr
-    from oracle.driver import run_schedule
-    from oracle.errors import great_circle_km
-    from paper_2211_12616_gb300.simulation import Simulation, periodic_snapshots
+    from paper_2211_12616_gb300.simulation import Simulation
     from workloads import fourier_modes, fourier_snapshot, grid_03deg_137lev, uniform_particles
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
@@ -546,12 +768,13 @@ def run_precision(args, rank, world):
     prm = M.DiffParams()
     stream = torch.cuda.Stream(device=dev)
     sub_ids = np.linspace(0, n - 1, min(PREC_SUB, n)).astype(np.int64)
+    sub = {k: v[sub_ids] for k, v in st0.items()}
     psteps = n * int(round(PREC_T_END / DT))
     at = lambda t: (snaps[int(round(t / DT_MET))]["u"], snaps[int(round(t / DT_MET))]["v"],
                     snaps[int(round(t / DT_MET))]["w"], snaps[int(round(t / DT_MET))]["T"])
-    results = {}
-    finals = {}
-    for name, storage in (("fp32", M.MPTRAC_FP32), ("bf16", M.MPTRAC_BF16), ("fp16", M.MPTRAC_FP16)):
+    results, subset = {}, {}
+    storages = (("fp32", M.MPTRAC_FP32), ("bf16", M.MPTRAC_BF16), ("fp16", M.MPTRAC_FP16))
+    for name, storage in storages:
         ctx = M.Context(grid, storage, nvars=4)
         ctx.set_launch(2, False)
         work = init.clone()
@@ -571,54 +794,55 @@ def run_precision(args, rank, world):
         b.record(stream)
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / args.steps
-        # module_meteo: u, v, omega, T sampled at the final positions (this storage's
-        # 12 h snapshots are still loaded)
-        with torch.cuda.stream(stream):
-            sampled = ctx.sample_met(work, PREC_T_END, stream=stream)
-        torch.cuda.synchronize()
-        sampled = sampled.cpu().numpy()
-        got = work.to_numpy()
-        pos = np.empty(n, dtype=np.int64)
-        pos[got["id"]] = np.arange(n)
-        finals[name] = {k: got[k][pos[sub_ids]] for k in ("lon", "lat", "p")}
-        finals[name]["sampled"] = sampled[:, pos[sub_ids]]
         results[name] = {"ms_per_pass": ms, "particle_steps_per_s": psteps / (ms / 1000.0),
                          "slot_bytes": int(grid.npoints * (16 if storage == M.MPTRAC_FP32 else 8))}
         ctx.close()
         del work, sim
         torch.cuda.empty_cache()
-    # float64 oracle on the subset, from the float32 fields (the stored-value error of
-    # bf16/fp16 plus the float32 arithmetic of every storage)
+        for diffuse in (True, False):
+            subset[(name, diffuse)] = _precision_subset_gpu(M, grid, snaps, storage, sub, diffuse)
     host = [{k: v.cpu().numpy() for k, v in s.items() if k in ("u", "v", "w", "T")} for s in snaps]
     del snaps
     torch.cuda.empty_cache()
-    sub = {k: v[sub_ids] for k, v in st0.items()}
+    # cpu_baseline leg: the float64 oracle on the subset, from the float32 fields, with and
+    # without diffusion; its states are the reference of every error below (the stored-value
+    # error of bf16/fp16 plus the float32 arithmetic of every storage)
     t0 = time.perf_counter()
-    ref = run_schedule(grid, lambda t: {k: host[int(round(t / DT_MET))][k] for k in ("u", "v", "w")}, DT_MET,
-                       sub, 0.0, PREC_T_END, DT, tr.DiffParams(), SEED_RNG)
+    ref = {d: _precision_oracle(grid, host, sub, d) for d in (True, False)}
     oracle_s = time.perf_counter() - t0
     from oracle import meteo
-    for name, fin in finals.items():
-        km = great_circle_km(fin["lon"], fin["lat"], ref["lon"], ref["lat"])
-        dp = np.abs(fin["p"] - ref["p"]) / ref["p"]
-        results[name].update({"km_median": float(np.median(km)), "km_p99": float(np.quantile(km, 0.99)),
-                              "km_max": float(km.max()), "dp_rel_median": float(np.median(dp)),
-                              "dp_rel_p99": float(np.quantile(dp, 0.99))})
-        # sampled met at this run's own final positions vs the float64 sampling of the
-        # float32 fields there: the storage's and the interpolation's error alone
-        ms_ = meteo.sample(grid, host[1], DT_MET, host[2], 2 * DT_MET, PREC_T_END, fin["lon"], fin["lat"], fin["p"])
-        for q, var in enumerate(("u", "v", "w", "T")):
-            err = np.abs(fin["sampled"][q] - ms_[var])
-            results[name][f"sampled_{var}_abs_median"] = float(np.median(err))
-            results[name][f"sampled_{var}_abs_p99"] = float(np.quantile(err, 0.99))
+    for name, _ in storages:
+        horizons = {}
+        for diffuse in (True, False):
+            states, sampled = subset[(name, diffuse)]
+            for h in PREC_HORIZONS:
+                horizons[f"{'diffusion' if diffuse else 'advection'}_{h / 3600:g}h"] = error_summary(
+                    states[h], ref[diffuse][h])
+            if diffuse:
+                results[name].update(horizons[f"diffusion_{PREC_T_END / 3600:g}h"])
+                # sampled met at this run's own final positions vs the float64 sampling of the
+                # float32 fields there: the storage's and the interpolation's error alone
+                fin = states[PREC_HORIZONS[-1]]
+                ms_ = meteo.sample(grid, host[1], DT_MET, host[2], 2 * DT_MET, PREC_T_END, fin["lon"], fin["lat"],
+                                   fin["p"])
+                for q, var in enumerate(("u", "v", "w", "T")):
+                    err = np.abs(sampled[q] - ms_[var])
+                    results[name][f"sampled_{var}_abs_median"] = float(np.median(err))
+                    results[name][f"sampled_{var}_abs_p99"] = float(np.quantile(err, 0.99))
+        results[name]["horizons"] = horizons
         results[name]["speedup_vs_fp32"] = results["fp32"]["ms_per_pass"] / results[name]["ms_per_pass"]
+    oracle_psteps = 2 * sub_ids.size * int(round(PREC_T_END / DT))
     line = {"metric": METRIC, "value": results["bf16"]["particle_steps_per_s"], "unit": "particle-steps/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": results["bf16"]["ms_per_pass"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16 storage / f32 arithmetic", "data": "synthetic",
             "config": {"workload": "0.3deg 1200x601x137 multiscale Fourier wind (256 modes), u/v/omega/T, "
                                    f"{n} particles, 12 h (240 fused steps), sort every 20; error vs the float64 "
-                                   f"oracle on {sub_ids.size} particles", "oracle_seconds": oracle_s},
+                                   f"oracle on {sub_ids.size} particles, with and without diffusion, at "
+                                   "1 h, 6 h and 12 h"},
+            "cpu_baseline": {"value": oracle_psteps / oracle_s, "unit": "particle-steps/s", "cores": 1,
+                             "kind": "oracle", "sample": f"{sub_ids.size} particles x 12 h, with and without "
+                                                         f"diffusion: {oracle_s:.1f} s"},
             "precision": results}
     print(json.dumps(line), flush=True)
 
@@ -629,41 +853,36 @@ def run_precision(args, rank, world):
 SURR_SEED, SURR_T_END = 5, 48 * 3600.0
 
 
-def run_surrogate_bench(args, rank, world):
+def surrogate_figures(dev, grid, snaps, n, n_train, epochs):
+    """Trains the surrogate on ``n_train`` plain 30-minute trajectories, then runs ``n`` particles
+    for 48 h three ways: plain midpoint at 180 s (the reference trajectory), plain midpoint at
+    1800 s, and the surrogate with the plain fallback; times and great-circle errors."""
     import torch
 
     import paper_2211_12616_gb300 as M
-    from oracle.errors import great_circle_km
     from paper_2211_12616_gb300 import learn
     from paper_2211_12616_gb300.simulation import periodic_snapshots
-    from workloads import fourier_modes, fourier_snapshot, grid_1deg_60lev, uniform_particles
+    from workloads import initial_weights, uniform_particles
 
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    torch.cuda.set_device(dev)
-    grid = grid_1deg_60lev()
-    modes = fourier_modes(SEED_FIELD)
-    snaps = [fourier_snapshot(grid, modes, h * DT_MET, device=dev, as_numpy=False) for h in range(4)]
     at = periodic_snapshots(snaps, DT_MET)
     ctx = M.Context(grid, M.MPTRAC_FP32)
     ctx.set_launch(2, False)
-    n_train = args.train_samples
     src = lambda count, seed: uniform_particles(count, grid.plev, SURR_SEED * 100000 + seed, lat_max=80.0)
     t0 = time.perf_counter()
     X, Y = learn.make_dataset(ctx, at, DT_MET, n_train, src)
     t_data = time.perf_counter() - t0
     sur = M.Surrogate(65536)
-    from oracle import surrogate as oS      # initial weights only (uniform fan-in init from a seed)
-    sur.set_params(oS.flatten(oS.init_params(SURR_SEED)).astype(np.float32))
+    sur.set_params(initial_weights(SURR_SEED))
     t0 = time.perf_counter()
-    hist, val = learn.train(sur, X, Y, epochs=args.epochs, batch=8192, lr=2e-3, lr_min=2e-5)
+    hist, val = learn.train(sur, X, Y, epochs=epochs, batch=8192, lr=2e-3, lr_min=2e-5)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del X, Y
     torch.cuda.empty_cache()
-    n = args.particles
     st0 = uniform_particles(n, grid.plev, SURR_SEED)
     init = M.Particles.from_numpy(st0, device=dev, meso=False, release=False)
     stream = torch.cuda.Stream(device=dev)
+    ws = torch.empty(ctx.sort_workspace_bytes(n), dtype=torch.uint8, device=dev)
 
     def timed(fn, parts):
         parts.copy_(init)
@@ -676,15 +895,15 @@ def run_surrogate_bench(args, rank, world):
         torch.cuda.synchronize()
         return a.elapsed_time(b), out
 
-    runs = {}
-    plain = init.clone()
-    ms_plain, _ = timed(lambda P: learn.run_plain(ctx, P, at, DT_MET, 0.0, SURR_T_END, stream=stream), plain)
-    coarse = init.clone()
+    plain, coarse, sur_p = init.clone(), init.clone(), init.clone()
+    run_sur = lambda P: learn.run_surrogate(ctx, sur, P, at, DT_MET, 0.0, SURR_T_END, stream=stream, workspace=ws)
+    timed(run_sur, sur_p)                                   # first use: set-up outside the timing
+    ms_plain, _ = timed(lambda P: learn.run_plain(ctx, P, at, DT_MET, 0.0, SURR_T_END, stream=stream,
+                                                  workspace=ws), plain)
     ms_coarse, _ = timed(lambda P: learn.run_plain(ctx, P, at, DT_MET, 0.0, SURR_T_END, dt=learn.DT_SEG,
-                                                   stream=stream), coarse)
-    sur_p = init.clone()
-    ms_sur, fb = timed(lambda P: learn.run_surrogate(ctx, sur, P, at, DT_MET, 0.0, SURR_T_END, stream=stream),
-                       sur_p)
+                                                   stream=stream, workspace=ws), coarse)
+    ms_sur, fb = timed(run_sur, sur_p)
+
     def by_id(parts):
         d = parts.to_numpy()
         o = np.argsort(d["id"])
@@ -692,6 +911,7 @@ def run_surrogate_bench(args, rank, world):
 
     ref = by_id(plain)
     substeps = n * int(round(SURR_T_END / DT))
+    runs = {}
     for name, parts, ms in (("plain_dt180", plain, ms_plain), ("midpoint_dt1800", coarse, ms_coarse),
                             ("surrogate", sur_p, ms_sur)):
         got = by_id(parts)
@@ -702,13 +922,32 @@ def run_surrogate_bench(args, rank, world):
                       "km_p99": float(np.quantile(km, 0.99)), "dp_rel_median": float(np.median(dp)),
                       "dp_rel_p99": float(np.quantile(dp, 0.99))}
     runs["surrogate"]["fallback_fraction"] = float(fb)
+    ctx.close()
+    return {"runs": runs, "train_seconds": t_train, "dataset_seconds": t_data, "epochs": epochs,
+            "train_samples": n_train, "particles": n, "train_loss": hist, "val_loss": val,
+            "workload": f"surrogate trained on {n_train} plain 30-min trajectories of the 1deg field, "
+                        f"{n} particles, 48 h; errors against plain midpoint at 180 s"}
+
+
+def run_surrogate_bench(args, rank, world):
+    import torch
+
+    from workloads import fourier_modes, fourier_snapshot, grid_1deg_60lev
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    grid = grid_1deg_60lev()
+    modes = fourier_modes(SEED_FIELD)
+    snaps = [fourier_snapshot(grid, modes, h * DT_MET, device=dev, as_numpy=False) for h in range(4)]
+    f = surrogate_figures(dev, grid, snaps, args.particles, args.train_samples, args.epochs)
+    runs = f["runs"]
     line = {"metric": METRIC, "value": runs["surrogate"]["substep_equivalents_per_s"], "unit": "particle-steps/s",
-            "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": ms_sur, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 MLP / f32", "data": "synthetic",
-            "config": {"workload": f"surrogate: trained on {n_train} plain 30-min trajectories (1deg field), "
-                                   f"{n} particles, 48 h; value in 180-s substep equivalents per second",
-                       "train_seconds": t_train, "dataset_seconds": t_data, "epochs": args.epochs,
-                       "train_loss": hist, "val_loss": val},
+            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": runs["surrogate"]["ms_per_48h"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 MLP / f32",
+            "data": "synthetic",
+            "config": {"workload": f["workload"] + "; value in 180-s substep equivalents per second",
+                       "train_seconds": f["train_seconds"], "dataset_seconds": f["dataset_seconds"],
+                       "epochs": f["epochs"], "train_loss": f["train_loss"], "val_loss": f["val_loss"]},
             "surrogate": runs}
     print(json.dumps(line), flush=True)
 
@@ -772,6 +1011,8 @@ def main():
     ap.add_argument("--particles", type=int, default=N_PART)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the 16-bit storage, batched and surrogate figures of the default line")
     ap.add_argument("--workload", default="transport", choices=["transport", "batch", "precision", "surrogate", "next"])
     ap.add_argument("--train-samples", type=int, default=10_000_000)
     ap.add_argument("--epochs", type=int, default=4)

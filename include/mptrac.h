@@ -436,6 +436,16 @@ int mptrac_met_slot_info(const mptrac_ctx* ctx, int slot, const void** records,
 /* Number of CUDA kernels this library has launched in this process so far. */
 uint64_t mptrac_kernel_launches(void);
 
+/* Measurement aid, with no counterpart in the paper: one launch that copies
+ * `bytes` bytes from DEVICE src to DEVICE dst `reps` times, loads and stores
+ * cached in L2 only (not L1), each repetition with another thread-to-element
+ * mapping.  With src and dst resident in L2 together (2 * bytes well below
+ * the L2 size) it measures the L2 bandwidth that the gather roofline divides
+ * by; with buffers far larger than L2, the DRAM copy bandwidth.  bytes must be
+ * a multiple of 16 and both pointers 16-byte aligned (E_INVALID_ARG
+ * otherwise); reps >= 1.  Asynchronous on `stream`. */
+int mptrac_copy_probe(const void* src, void* dst, size_t bytes, int reps, uintptr_t stream);
+
 /* Copies met slot `slot` into caller-owned DEVICE buffers: records_out
  * (mptrac_met_slot_info's `bytes` bytes) and scales_out (4*nz float32), on
  * `stream`.  Either output may be NULL. */

@@ -75,6 +75,7 @@ SIGNATURES = {
                                        C.POINTER(C.c_double), C.POINTER(C.c_size_t)]),
     "mptrac_met_slot_copy": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mptrac_kernel_launches": (C.c_uint64, []),
+    "mptrac_copy_probe": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p]),
     "mptrac_sort_noalloc": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_void_p]),
     "mptrac_sort_at": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_double, C.c_void_p, C.c_size_t,
                                  C.c_void_p]),
@@ -368,6 +369,13 @@ def philox(ctr: torch.Tensor, seed: int, with_normals: bool = False, stream=None
     z = torch.empty(4, n, dtype=torch.float32, device=ctr.device) if with_normals else None
     check(load().mptrac_philox(_ptr(ctr), n, int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out), _ptr(z), _stream(stream)))
     return (out, z) if with_normals else out
+
+
+def copy_probe(src: torch.Tensor, dst: torch.Tensor, reps: int, stream=None):
+    """``mptrac_copy_probe``: one launch copying src into dst ``reps`` times through L2."""
+    nbytes = src.numel() * src.element_size()
+    assert dst.numel() * dst.element_size() >= nbytes
+    check(load().mptrac_copy_probe(_ptr(src), _ptr(dst), nbytes, int(reps), _stream(stream)))
 
 
 # ---------------------------------------------------------------------------

@@ -287,6 +287,20 @@ extern "C" {
 
 uint64_t mptrac_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int mptrac_copy_probe(const void* src, void* dst, size_t bytes, int reps, uintptr_t stream) {
+    if (reps < 1) return fail(MPTRAC_E_INVALID_ARG, "reps must be >= 1");
+    if (bytes % 16 || (reinterpret_cast<uintptr_t>(src) & 15) || (reinterpret_cast<uintptr_t>(dst) & 15))
+        return fail(MPTRAC_E_INVALID_ARG, "bytes must be a multiple of 16 and both pointers 16-byte aligned");
+    if (bytes == 0) return ok();
+    if (!device_accessible(src) || !device_accessible(dst))
+        return fail(MPTRAC_E_INVALID_ARG, "src and dst must be device memory");
+    int dev = 0, sms = 0;
+    MPTRAC_CUDA(cudaGetDevice(&dev));
+    MPTRAC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    MPTRAC_CUDA(launch_copy_probe(src, dst, bytes, reps, sms, reinterpret_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
 int mptrac_init_grid(mptrac_ctx** out, const mptrac_grid_desc* g) {
     if (!out || !g) return fail(MPTRAC_E_INVALID_ARG, "NULL argument");
     *out = nullptr;
@@ -382,13 +396,10 @@ int mptrac_init_grid(mptrac_ctx** out, const mptrac_grid_desc* g) {
     G.nx = g->nx; G.ny = g->ny; G.nz = nz; G.nbins = nbins;
     G.lon0 = (float)g->lon0;
     G.inv_dlon = (float)(1.0 / g->dlon);
+    G.inv_dlon_lo = (float)(1.0 / g->dlon - (double)G.inv_dlon);
     G.lat0 = (float)g->lat0;
     G.inv_dlat = (float)(1.0 / g->dlat);
     G.inv_dlat_lo = (float)(1.0 / g->dlat - (double)G.inv_dlat);
-    {
-        volatile float l0 = G.lon0;   // the float sum the kernels compare against
-        G.lon1 = l0 + 360.0f;
-    }
     G.dn = (float)(90.0 - g->lat0);
     G.dn_lo = (float)((90.0 - g->lat0) - (double)G.dn);
     G.ds = (float)(-90.0 - g->lat0);

@@ -20,7 +20,7 @@ constexpr int kBlock = 256;               // threads per block of the particle k
 struct Geo {
     int nx, ny, nz, nbins;
     float lon0, inv_dlon, lat0, inv_dlat, inv_dlat_lo;   // 1/dlat as float-float (hi, lo)
-    float lon1;                   // lon0 + 360 (float sum): longitudes live in [lon0, lon1)
+    float inv_dlon_lo;            // 1/dlon = inv_dlon + inv_dlon_lo (float-float)
     // The particle kernels carry latitude as d = lat - lat0.  The poles and the
     // equator in that coordinate: dn = 90 - lat0, ds = -90 - lat0 as float-float,
     // dmid = -lat0 (exact).
@@ -131,6 +131,7 @@ cudaError_t launch_philox(const uint32_t* ctr, int64_t n, uint32_t k0, uint32_t 
 // Packs one snapshot into slot records `rec` (+ scales) and into lane lane0
 // of the interleaved pair records pairs0 and lane lane1 of pairs1 (the two
 // slot pairs the slot belongs to).
+cudaError_t launch_copy_probe(const void* src, void* dst, size_t bytes, int reps, int num_sms, cudaStream_t s);
 cudaError_t launch_pack(int storage, int nvars, const float* u, const float* v, const float* w,
                         const float* T, int nx, int ny, int nz, void* rec, float* scales, void* pairs0,
                         int lane0, void* pairs1, int lane1, cudaStream_t s);

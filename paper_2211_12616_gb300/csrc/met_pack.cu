@@ -160,4 +160,34 @@ cudaError_t launch_pack(int storage, int nvars, const float* u, const float* v, 
     return cudaGetLastError();
 }
 
+namespace {
+// Copy of n 16-byte elements, `reps` times, loads and stores cached in L2 only.
+// Each repetition shifts the block-to-element mapping by one block, and every
+// thread keeps four loads in flight before its stores.
+__global__ void __launch_bounds__(512) k_copy_probe(const uint4* __restrict__ src, uint4* __restrict__ dst,
+                                                    int64_t n, int reps) {
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    for (int r = 0; r < reps; ++r) {
+        const int64_t b = (blockIdx.x + (unsigned)r) % gridDim.x;
+        int64_t i = b * blockDim.x + threadIdx.x;
+        for (; i + 3 * T < n; i += 4 * T) {
+            const uint4 a0 = __ldcg(src + i), a1 = __ldcg(src + i + T);
+            const uint4 a2 = __ldcg(src + i + 2 * T), a3 = __ldcg(src + i + 3 * T);
+            __stcg(dst + i, a0);
+            __stcg(dst + i + T, a1);
+            __stcg(dst + i + 2 * T, a2);
+            __stcg(dst + i + 3 * T, a3);
+        }
+        for (; i < n; i += T) __stcg(dst + i, __ldcg(src + i));
+    }
+}
+}  // namespace
+
+cudaError_t launch_copy_probe(const void* src, void* dst, size_t bytes, int reps, int num_sms, cudaStream_t s) {
+    note_launches(1);
+    k_copy_probe<<<4 * num_sms, 512, 0, s>>>(static_cast<const uint4*>(src), static_cast<uint4*>(dst),
+                                             (int64_t)(bytes / 16), reps);
+    return cudaGetLastError();
+}
+
 }  // namespace mptrac

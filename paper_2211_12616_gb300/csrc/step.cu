@@ -78,6 +78,13 @@ __device__ __forceinline__ ff ff_add_inc(ff a, float b) {
     lo = __fsub_rn(lo, __fsub_rn(hi, s));
     return {hi, lo};
 }
+// The same sum left unnormalised (|lo| may reach an ulp of hi): enough for a
+// position that only places a wind evaluation (the midpoint), 2 fewer operations.
+__device__ __forceinline__ ff ff_add_inc_raw(ff a, float b) {
+    const float s = __fadd_rn(a.hi, b);
+    const float e = __fsub_rn(b, __fsub_rn(s, a.hi));
+    return {s, __fadd_rn(a.lo, e)};
+}
 __device__ __forceinline__ bool ff_less(ff a, float bh, float bl) {
     return a.hi < bh || (a.hi == bh && a.lo < bl);
 }
@@ -125,36 +132,38 @@ __device__ __forceinline__ void reflect(ff& d, float ph, float pl) {
     d.lo = __fsub_rn(l, __fsub_rn(d.hi, h));
 }
 
-// module_position on (lon, d = lat - lat0, p): reflect over the poles
-// (lon + 180), wrap lon into [lon0, lon0 + 360), clamp p to the level range.
+// module_position on (e = lon - lon0, d = lat - lat0, p): reflect over the
+// poles (longitude + 180), wrap e into [0, 360), clamp p to the level range.
 // The hi parts decide whether any rule can apply; the exact float-float
 // comparisons run only then.
-__device__ __forceinline__ void position_rules(ff& lon, ff& d, ff& p, const Geo& g) {
+__device__ __forceinline__ void horizontal_rules(ff& e, ff& d, const Geo& g) {
     if (ff_greater(d, g.dn, g.dn_lo)) {
         reflect(d, g.dn, g.dn_lo);
-        lon = ff_add(lon, 180.f);
+        e = ff_add(e, 180.f);
     } else if (ff_less(d, g.ds, g.ds_lo)) {
         reflect(d, g.ds, g.ds_lo);
-        lon = ff_add(lon, 180.f);
+        e = ff_add(e, 180.f);
     }
-    const float L0 = g.lon0, L1 = g.lon1;
-    if (!ff_less(lon, L1, 0.f) || ff_less(lon, L0, 0.f)) {
-        float turns = floorf((lon.hi - L0) * (1.0f / 360.0f));
+    if (!ff_less(e, 360.f, 0.f) || ff_less(e, 0.f, 0.f)) {
+        float turns = floorf(e.hi * (1.0f / 360.0f));
         if (isfinite(turns)) {
-            lon = ff_add(lon, -360.f * turns);
-            if (!ff_less(lon, L1, 0.f)) lon = ff_add(lon, -360.f);
-            if (ff_less(lon, L0, 0.f)) lon = ff_add(lon, 360.f);
+            e = ff_add(e, -360.f * turns);
+            if (!ff_less(e, 360.f, 0.f)) e = ff_add(e, -360.f);
+            if (ff_less(e, 0.f, 0.f)) e = ff_add(e, 360.f);
         }
     }
+}
+
+__device__ __forceinline__ void position_rules(ff& e, ff& d, ff& p, const Geo& g) {
+    horizontal_rules(e, d, g);
     if (ff_less(p, g.pmin, g.pmin_lo)) { p.hi = g.pmin; p.lo = g.pmin_lo; }
     if (ff_greater(p, g.pmax, g.pmax_lo)) { p.hi = g.pmax; p.lo = g.pmax_lo; }
 }
 
-__device__ __forceinline__ void position_bc(ff& lon, ff& d, ff& p, const Geo& g) {
+__device__ __forceinline__ void position_bc(ff& e, ff& d, ff& p, const Geo& g) {
     // NaN fails every comparison and also takes the exact path (which leaves it)
-    if (!(d.hi < g.dn && d.hi > g.ds && lon.hi < g.lon1 && lon.hi > g.lon0 && p.hi > g.pmin &&
-          p.hi < g.pmax))
-        position_rules(lon, d, p, g);
+    if (!(d.hi < g.dn && d.hi > g.ds && e.hi < 360.f && e.hi > 0.f && p.hi > g.pmin && p.hi < g.pmax))
+        position_rules(e, d, p, g);
 }
 
 // ---------------------------------------------------------------------------
@@ -259,32 +268,36 @@ struct Cell {
 
 __device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.f), 1.f); }
 
-// The latitude enters as d = lat - lat0 in float-float.  The latitude
-// fraction is formed in float-float and both weights are
-// computed directly, so that next to a pole the small weight keeps its
-// relative precision (winds there vanish like the distance to the pole while
-// the longitude increment divides by cos(lat)).  The level search starts from
-// `k_hint` (the level of the previous evaluation; < 0: none), else from the
-// ln(p) table, and walks to the bracketing pair.
+// Longitude and latitude enter as e = lon - lon0 and d = lat - lat0 in
+// float-float, and both cell coordinates x = e / dlon, y = d / dlat are formed
+// in float-float: on a fine grid whose spacing has no exact float inverse
+// (0.3 degrees), a float32 x near the eastern end (x ~ 1200) would carry
+// ~1e-4 cells of error, which steep grid-scale winds turn into metres per
+// hour.  Both latitude weights are computed directly, so that next to a pole
+// the small weight keeps its relative precision (winds there vanish like the
+// distance to the pole while the longitude increment divides by cos(lat)).
+// The level search starts from `k_hint` (the level of the previous evaluation;
+// < 0: none), else from the ln(p) table, and walks to the bracketing pair.
 template <class S>
-__device__ __forceinline__ Cell locate(float lon, ff d, float p, const Geo& g, const S& s,
-                                       int k_hint) {
+__device__ __forceinline__ Cell locate(ff e, ff d, float p, const Geo& g, const S& s, int k_hint) {
     Cell c;
-    // The longitude has been wrapped into [lon0, lon0 + 360), so x >= 0 and
-    // x - floor(x) is exact and in [0, 1]; i == nx (x rounded up to nx) wraps
-    // to 0, and the clamp keeps a NaN's index inside the grid.  Explicitly
-    // rounded operations: a multiply-subtract fused by the compiler in some
-    // instantiations only would make results depend on the launch variant.
-    const float x = __fmul_rn(__fsub_rn(lon, g.lon0), g.inv_dlon);
-    const float xf = floorf(x);
+    // e is in [0, 360), so xh >= 0 and xh - floor(xh) is exact and in [0, 1);
+    // i == nx (xh rounded up to nx) wraps to 0, and the clamp keeps a NaN's
+    // index inside the grid.  The correction xe is below an ulp of xh: the
+    // weights may leave [0, 1] by that much, a continuous extrapolation.
+    const float xh = __fmul_rn(e.hi, g.inv_dlon);
+    float xe = fmaf(e.hi, g.inv_dlon, -xh);
+    xe = fmaf(e.hi, g.inv_dlon_lo, xe);
+    xe = fmaf(e.lo, g.inv_dlon, xe);
+    const float xf = floorf(xh);
     int i = (int)xf;
     if (i >= g.nx) i -= g.nx;
     c.i = min(max(i, 0), g.nx - 1);
-    c.fx = __fsub_rn(x, xf);
+    c.fx = __fadd_rn(__fsub_rn(xh, xf), xe);
     c.gx = __fsub_rn(1.f, c.fx);
 
-    // y = d / dlat as float-float (yh + ye), d = lat - lat0; the row index is
-    // clamped as a float (exact small integers), which saves converting it back
+    // y = d / dlat as float-float (yh + ye); the row index is clamped as a
+    // float (exact small integers), which saves converting it back
     const float yh = d.hi * g.inv_dlat;
     float ye = fmaf(d.hi, g.inv_dlat, -yh);
     ye = fmaf(d.hi, g.inv_dlat_lo, ye);
@@ -304,16 +317,16 @@ __device__ __forceinline__ Cell locate(float lon, ff d, float p, const Geo& g, c
     // one 16-byte load gives both bounds of level k and the inverse spacing; the
     // walk to another level (rare: the level of the previous evaluation is the
     // first guess) reloads it
-    float4 e = s.lv[k];
-    if (k > 0 && e.x < pc) {
+    float4 lv = s.lv[k];
+    if (k > 0 && lv.x < pc) {
         do { --k; } while (k > 0 && s.plev[k] < pc);
-        e = s.lv[k];
-    } else if (k < g.nz - 2 && e.y >= pc) {
+        lv = s.lv[k];
+    } else if (k < g.nz - 2 && lv.y >= pc) {
         do { ++k; } while (k < g.nz - 2 && s.plev[k + 1] >= pc);
-        e = s.lv[k];
+        lv = s.lv[k];
     }
     c.k = k;
-    c.fz = clamp01((e.x - pc) * e.z);
+    c.fz = clamp01((lv.x - pc) * lv.z);
     c.gz = 1.f - c.fz;
     return c;
 }
@@ -593,31 +606,10 @@ __device__ __forceinline__ void load_tables(SmemT<NSC>& s, const Geo& g, const f
 // Pieces of the step: midpoint position rules, random draws
 // ---------------------------------------------------------------------------
 // Midpoint position rules: latitude reflected over the poles (longitude +
-// 180), longitude wrapped into [lon0, lon0 + 360).  The pressure needs no
-// rule here: `locate` clamps it to the level range.  The midpoint only places
-// the second wind evaluation, so its longitude needs no more than float
-// precision.
-__device__ __forceinline__ void midpoint_rules(float& lon, ff& d, const Geo& g) {
-    if (ff_greater(d, g.dn, g.dn_lo)) {
-        reflect(d, g.dn, g.dn_lo);
-        lon += 180.f;
-    } else if (ff_less(d, g.ds, g.ds_lo)) {
-        reflect(d, g.ds, g.ds_lo);
-        lon += 180.f;
-    }
-    const float L0 = g.lon0, L1 = g.lon1;
-    if (!(lon < L1) || lon < L0) {
-        const float turns = floorf((lon - L0) * (1.0f / 360.0f));
-        if (isfinite(turns)) {
-            lon = fmaf(-360.f, turns, lon);
-            if (lon >= L1) lon -= 360.f;
-            if (lon < L0) lon += 360.f;
-        }
-    }
-}
-
-__device__ __forceinline__ void midpoint_bc(float& lon, ff& d, const Geo& g) {
-    if (!(d.hi < g.dn && d.hi > g.ds && lon < g.lon1 && lon >= g.lon0)) midpoint_rules(lon, d, g);
+// 180), longitude wrapped into [0, 360) (as e = lon - lon0).  The pressure
+// needs no rule here: `locate` clamps it to the level range.
+__device__ __forceinline__ void midpoint_bc(ff& e, ff& d, const Geo& g) {
+    if (!(d.hi < g.dn && d.hi > g.ds && e.hi < 360.f && e.hi >= 0.f)) horizontal_rules(e, d, g);
 }
 
 // sqrt(x), x >= 0 (a weighted sum of squares), by the approximate square root
@@ -728,8 +720,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
             if (emit) hand_off(a, s, idx, a.lon[idx], a.lat[idx], a.p[idx], a.id[idx], false);
             continue;
         }
-        ff lon = ff_make(a.lon[idx]);
-        ff d = ff_make(a.lat[idx] - g.lat0_d);   // latitude as d = lat - lat0
+        ff lon = ff_make(a.lon[idx] - g.lon0_d);   // longitude as e = lon - lon0
+        ff d = ff_make(a.lat[idx] - g.lat0_d);     // latitude as d = lat - lat0
         ff p = ff_make(a.p[idx]);
         const uint32_t pid = a.id[idx];
         const Round0 r0 = round0(a, pid, rel);
@@ -758,14 +750,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
                 // ---- module_advection: explicit midpoint ----
                 const float wl0 = a.wt[4 * sidx], wh0 = a.wt[4 * sidx + 1];
                 const float wlm = a.wt[4 * sidx + 2], whm = a.wt[4 * sidx + 3];
-                const Cell c1 = locate(lon.hi, d, p.hi, g, s, cc.k);
+                const Cell c1 = locate(lon, d, p.hi, g, s, cc.k);
                 Wind V;
                 if (MODE != MODE_ADVECT && use_meso)
                     eval_wind<ST, true>(a.mp, s, g, c1, wl0, wh0, cc, V, var);
                 else
                     eval_wind<ST, false>(a.mp, s, g, c1, wl0, wh0, cc, V, var);
                 const float cl = coslat(d, 0.f, g);
-                float lon_m = lon.hi + __fdividef(a.hk * V.u, cl);
+                ff lon_m = ff_add_inc_raw(lon, __fdividef(a.hk * V.u, cl));
                 ff d_m = ff_add_inc(d, a.hk * V.v);
                 const float p_m = p.hi + a.half_dt * V.w;
                 midpoint_bc(lon_m, d_m, g);
@@ -777,7 +769,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
                 ilat = a.dk * V2.v;
                 ip = a.dt * V2.w;
             } else if (use_meso) {
-                const Cell c1 = locate(lon.hi, d, p.hi, g, s, cc.k);
+                const Cell c1 = locate(lon, d, p.hi, g, s, cc.k);
                 Wind V;
                 eval_wind<ST, true>(a.mp, s, g, c1, a.wt[4 * sidx], a.wt[4 * sidx + 1], cc, V, var);
             }
@@ -811,7 +803,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
             // ---- module_position ----
             position_bc(lon, d, p, g);
         }
-        const double lon_out = ff_val(lon), lat_out = ff_val(d) + g.lat0_d, p_out = ff_val(p);
+        const double lon_out = ff_val(lon) + g.lon0_d, lat_out = ff_val(d) + g.lat0_d, p_out = ff_val(p);
         if (emit) {
             if (use_meso) {
                 a.emit.copy.f[0][idx] = up;
@@ -861,7 +853,7 @@ __global__ void __launch_bounds__(kBlock) k_interp(Geo g, MetPair mp, float wl, 
     load_tables(s, g, mp.scales[0], mp.scales[1], ST != MPTRAC_FP32);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
-        const Cell c = locate(ff_make(lon[idx]).hi, ff_make(lat[idx] - g.lat0_d), ff_make(p[idx]).hi, g, s, -1);
+        const Cell c = locate(ff_make(lon[idx] - g.lon0_d), ff_make(lat[idx] - g.lat0_d), ff_make(p[idx]).hi, g, s, -1);
         Wind V, var;
         RegCache cc;
         cc.init(nullptr);
@@ -887,7 +879,7 @@ __global__ void __launch_bounds__(kBlock) k_sample(Geo g, MetView m0, MetView m1
     using R = typename RecT<ST>::T;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
-        const Cell c = locate(ff_make(lon[idx]).hi, ff_make(lat[idx] - g.lat0_d), ff_make(p[idx]).hi, g, s, -1);
+        const Cell c = locate(ff_make(lon[idx] - g.lon0_d), ff_make(lat[idx] - g.lat0_d), ff_make(p[idx]).hi, g, s, -1);
         const int i1 = (c.i + 1 == g.nx) ? 0 : c.i + 1;
         const int col[4] = {c.j * g.nx + c.i, c.j * g.nx + i1, (c.j + 1) * g.nx + c.i, (c.j + 1) * g.nx + i1};
         float res[2][4];
@@ -947,14 +939,14 @@ __global__ void __launch_bounds__(kBlock) k_sedi(const SediArgs a) {
     constexpr float Rd = 287.058f, G = 9.80665f;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < a.n; idx += stride) {
-        const float lonf = ff_make(a.lon[idx]).hi;
+        const ff e = ff_make(a.lon[idx] - g.lon0_d);
         const ff d = ff_make(a.lat[idx] - g.lat0_d);
         ff p = ff_make(a.p[idx]);
         const float r = a.radius[idx], rp = a.rho_p[idx];
         int ccol = -1, ck = -1;
         float T0[8], T1[8];
         for (int n = 0; n < a.nsteps; ++n) {
-            const Cell c = locate(lonf, d, p.hi, g, s, ck);
+            const Cell c = locate(e, d, p.hi, g, s, ck);
             const int col = c.j * g.nx + c.i;
             if (col != ccol || c.k != ck) {
                 const int i1 = (c.i + 1 == g.nx) ? 0 : c.i + 1;

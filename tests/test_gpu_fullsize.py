@@ -69,3 +69,55 @@ def test_bench_workload_sampled_parity(M):
     assert stats["km_max"] < 0.0111 and stats["dlat_max"] < 1e-4, stats
     assert stats["dp_rel_max"] < 1e-5, stats
     ctx.close()
+
+
+@pytest.fixture(scope="module")
+def large_grid(M):
+    """The 0.3 degree x 137 level grid (98.8 M points) with the multiscale 256-mode wind."""
+    from workloads import grid_03deg_137lev
+    grid = grid_03deg_137lev()
+    modes = fourier_modes(3, n_modes=256, multiscale=True)
+    snaps = [fourier_snapshot(grid, modes, h * DT_MET, device="cuda", as_numpy=False) for h in range(2)]
+    ctx = M.Context(grid, M.MPTRAC_FP32)
+    for slot, f in enumerate(snaps):
+        ctx.load_met(slot, slot * DT_MET, f["u"], f["v"], f["w"])
+    torch.cuda.synchronize()
+    met = tr.Met(grid, 0.0, {k: v.cpu().numpy() for k, v in snaps[0].items()},
+                 DT_MET, {k: v.cpu().numpy() for k, v in snaps[1].items()})
+    del snaps
+    torch.cuda.empty_cache()
+    yield grid, ctx, met
+    ctx.close()
+
+
+@pytest.mark.parametrize("diffuse", [False, True])
+def test_large_grid_parity(M, large_grid, diffuse):
+    """The largest grid of the workloads: each pair-record buffer holds 98.8 M records of 32 B
+    (3.2 GB), so the records of the last rows lie beyond 2^31 bytes.  2e4 particles spread over the
+    grid, plus particles placed in the last latitude rows, the last longitude column and the top
+    levels (the largest record offsets), take 20 fused steps against the oracle at the transport
+    tolerances, with and without diffusion."""
+    from _gpu_common import assert_positions_close
+    grid, ctx, met = large_grid
+    st0 = uniform_particles(20_000, grid.plev, 61)
+    rng = np.random.default_rng(62)
+    m = 2000
+    st0["lat"][:m] = rng.uniform(89.0, 89.99, m)                 # j = ny - 2 and around
+    st0["lon"][:m // 2] = rng.uniform(359.0, 359.99, m // 2)     # i = nx - 1, the seam cell
+    st0["p"][:m // 2] = np.exp(rng.uniform(np.log(grid.plev[-1]), np.log(grid.plev[-8]), m // 2))
+    parts = M.Particles.from_numpy(st0)
+    ctx.step(parts, 0.0, DT, M.DiffParams(turb=diffuse, meso=diffuse), 5, 0, 20)
+    torch.cuda.synchronize()
+    got = parts.to_numpy()
+    ref = tr.step(met, st0, 0.0, DT, tr.DiffParams(turb=diffuse, meso=diffuse), 5, 0, 20)
+    lon_metric = "arc" if diffuse else "deg"
+    away = np.abs(st0["lat"]) < 89.0        # the literal longitude criterion away from the pole rows
+    a = assert_positions_close({k: v[away] for k, v in got.items()}, {k: v[away] for k, v in ref.items()},
+                               what=f"0.3 deg x 137 levels, diffusion {diffuse}", lon_metric=lon_metric)
+    b = assert_positions_close(got, ref, what=f"0.3 deg x 137 levels incl. pole rows, diffusion {diffuse}",
+                               lon_metric="arc")
+    print(f"0.3 deg grid, diffusion {diffuse}: max |dlon| {a[0]:.2e}, |dlat| {a[1]:.2e} deg, |dp|/p {a[2]:.2e}; "
+          f"with the pole rows: |dlat| {b[1]:.2e} deg, |dp|/p {b[2]:.2e}")
+    # the particles placed at the largest offsets did move with the wind there
+    moved = great_circle_km(got["lon"][:m], got["lat"][:m], st0["lon"][:m], st0["lat"][:m])
+    assert np.median(moved) > 0.1

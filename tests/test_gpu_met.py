@@ -74,3 +74,22 @@ def test_load_met_errors(M):
     with pytest.raises(M.MptracError) as e:
         ctx.advect(parts, 0.0, 180.0, 1)
     assert e.value.code == -7
+
+
+def test_copy_probe_copies_and_checks_its_arguments(M):
+    """The bandwidth probe copies its source exactly (any repetition count, a ragged element count)
+    and rejects sizes that are not whole 16-byte elements and unaligned pointers on the host."""
+    src = torch.arange(4 * 1_000_003, dtype=torch.float32, device="cuda")
+    dst = torch.zeros_like(src)
+    for reps in (1, 3):
+        dst.zero_()
+        M.copy_probe(src, dst, reps)
+        torch.cuda.synchronize()
+        assert torch.equal(dst, src)
+    with pytest.raises(M.MptracError) as e:
+        M.copy_probe(src[1:], dst[1:], 1)          # 4-byte offset: not 16-byte aligned
+    assert e.value.code == -1
+    with pytest.raises(M.MptracError):
+        M.copy_probe(src[:6], dst[:6], 1)          # 24 bytes: not whole 16-byte elements
+    with pytest.raises(M.MptracError):
+        M.copy_probe(src, dst, 0)

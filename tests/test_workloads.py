@@ -95,3 +95,11 @@ def test_column_releases():
         sel = st["release"] == r
         assert sel.sum() == rel.counts[r]
         assert np.unique(st["lon"][sel]).size == 1 and np.unique(st["lat"][sel]).size == 1
+
+
+def test_initial_weights_are_the_oracle_init():
+    """The network's seeded starting point equals the oracle's own draw (same order, same rule)."""
+    from oracle import surrogate as S
+    from workloads import initial_weights
+    for seed in (0, 5):
+        np.testing.assert_array_equal(initial_weights(seed), S.flatten(S.init_params(seed)).astype(np.float32))
