@@ -172,9 +172,90 @@ struct GemmArgs {
     long long wait_cycles;  // tcgen05 kernel: limit of each wait (SM clock cycles)
 };
 
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+// GELU(x) = x Phi(x), Phi the standard normal distribution function, without
+// the special-function unit.  For |x| <= 4.5, Phi(x) = 1/2 + x P(z) with
+// z = x^2 / 10.125 - 1 in [-1, 1] and P of degree 12; x is clamped to
+// [-4.5, 4.5] (beyond, Phi is within 3.4e-6 of 0 or 1).  The coefficients were
+// fitted here: least squares on [0, 4.5], reweighted toward equal ripple; the
+// error of Phi is below 4.2e-8 with the coefficients rounded to float32 and
+// below 1.1e-7 evaluated in float32, the accuracy of 0.5 (1 + erff(x / sqrt 2)).
+// Every operation is
+// explicitly rounded, so that the scalar form and the packed form (two values
+// per instruction, lanes rounding like the scalar instructions) agree bit for bit.
+constexpr float kPhiT = 4.5f, kPhiS = 2.0f / (4.5f * 4.5f);
+
+// P(z) by Horner's rule, highest coefficient first (the coefficients of z^12 .. z^0)
+__device__ __forceinline__ float phi_poly(float x) {
+    const float xc = fminf(fmaxf(x, -kPhiT), kPhiT);
+    const float z = __fmaf_rn(xc, __fmul_rn(xc, kPhiS), -1.f);
+    float q = 1.186082663e-04f;
+    q = __fmaf_rn(q, z, -3.718789958e-04f);
+    q = __fmaf_rn(q, z, 6.197711336e-04f);
+    q = __fmaf_rn(q, z, -1.314797322e-03f);
+    q = __fmaf_rn(q, z, 3.128047800e-03f);
+    q = __fmaf_rn(q, z, -6.279318128e-03f);
+    q = __fmaf_rn(q, z, 1.122274343e-02f);
+    q = __fmaf_rn(q, z, -1.857017539e-02f);
+    q = __fmaf_rn(q, z, 2.833536640e-02f);
+    q = __fmaf_rn(q, z, -4.018990323e-02f);
+    q = __fmaf_rn(q, z, 5.469672382e-02f);
+    q = __fmaf_rn(q, z, -7.718981802e-02f);
+    q = __fmaf_rn(q, z, 1.569049954e-01f);
+    return __fmaf_rn(xc, q, 0.5f);
+}
+__device__ __forceinline__ float gelu(float x) { return __fmul_rn(x, phi_poly(x)); }
 __device__ __forceinline__ float gelu_grad(float x) {
-    return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+    return phi_poly(x) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+
+// Pairs of float32 values in one 64-bit register for Blackwell's packed
+// float32x2 instructions (each lane rounds exactly like the scalar instruction).
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2_pack(float a, float b) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_split(f2_t v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+    f2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
+    f2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
+    f2_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_dup(float a) { return f2_pack(a, a); }
+
+// gelu of both lanes of x: the same operations as gelu(), two values per instruction
+__device__ __forceinline__ f2_t gelu2(f2_t x) {
+    float a, b;
+    f2_split(x, a, b);
+    const f2_t xc = f2_pack(fminf(fmaxf(a, -kPhiT), kPhiT), fminf(fmaxf(b, -kPhiT), kPhiT));
+    const f2_t z = f2_fma(xc, f2_mul(xc, f2_dup(kPhiS)), f2_dup(-1.f));
+    f2_t q = f2_dup(1.186082663e-04f);
+    q = f2_fma(q, z, f2_dup(-3.718789958e-04f));
+    q = f2_fma(q, z, f2_dup(6.197711336e-04f));
+    q = f2_fma(q, z, f2_dup(-1.314797322e-03f));
+    q = f2_fma(q, z, f2_dup(3.128047800e-03f));
+    q = f2_fma(q, z, f2_dup(-6.279318128e-03f));
+    q = f2_fma(q, z, f2_dup(1.122274343e-02f));
+    q = f2_fma(q, z, f2_dup(-1.857017539e-02f));
+    q = f2_fma(q, z, f2_dup(2.833536640e-02f));
+    q = f2_fma(q, z, f2_dup(-4.018990323e-02f));
+    q = f2_fma(q, z, f2_dup(5.469672382e-02f));
+    q = f2_fma(q, z, f2_dup(-7.718981802e-02f));
+    q = f2_fma(q, z, f2_dup(1.569049954e-01f));
+    return f2_mul(x, f2_fma(xc, q, f2_dup(0.5f)));
 }
 
 __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
@@ -435,11 +516,27 @@ __device__ __forceinline__ void nearest_node_f32(const Geo& g, const float* plev
     oz = z - (float)kk;
 }
 
-// The predicted displacement of particle q (normalised outputs y0..y2) followed
-// by the position rules, or the fallback flag outside the envelope.
-__device__ __forceinline__ void apply_displacement(const FusedArgs& a, int64_t q, int env_ok, float y0,
-                                                   float y1, float y2) {
-    const double la = a.lat[q];
+struct Pos {
+    double lon, lat, p;
+};
+
+// Position of particle q (zeros past n).
+__device__ __forceinline__ Pos pos_of(const FusedArgs& a, int64_t q) {
+    if (q >= a.n) return Pos{0.0, 0.0, 0.0};
+    return Pos{a.lon[q], a.lat[q], a.p[q]};
+}
+
+// Position of the particle of (particle, snapshot) item `tid` of tile `tile`.
+__device__ __forceinline__ Pos load_pos(const FusedArgs& a, int64_t tile, int tid) {
+    return pos_of(a, tile * FT + (tid >> 1));
+}
+
+// The predicted displacement of particle q at position `pos` (normalised
+// outputs y0..y2) followed by the position rules, or the fallback flag outside
+// the envelope.
+__device__ __forceinline__ void apply_displacement(const FusedArgs& a, int64_t q, const Pos& pos, int env_ok,
+                                                   float y0, float y1, float y2) {
+    const double la = pos.lat;
     const bool ok = a.window_ok && env_ok && fabs(la) <= 80.0;
     a.fallback[q] = ok ? 0 : 1;
     if (!ok) return;
@@ -447,9 +544,9 @@ __device__ __forceinline__ void apply_displacement(const FusedArgs& a, int64_t q
     const float dy = y1 * a.sd_y[1] + a.mu_y[1];
     const float dz = y2 * a.sd_y[2] + a.mu_y[2];
     const float cl = cospif((float)la * (1.0f / 180.0f));
-    double lo = a.lon[q] + (double)(dx / ((float)kR * cl) * (float)(180.0 / kPi));
+    double lo = pos.lon + (double)(dx / ((float)kR * cl) * (float)(180.0 / kPi));
     double lt = la + (double)(dy * (float)(180.0 / (kPi * kR)));
-    const double pp = a.p[q] * (double)expf(dz);
+    const double pp = pos.p * (double)expf(dz);
     if (lt > 90.0) { lt = 180.0 - lt; lo += 180.0; }
     else if (lt < -90.0) { lt = -180.0 - lt; lo += 180.0; }
     if (lo >= a.lon0 + 360.0) lo -= 360.0;
@@ -460,12 +557,13 @@ __device__ __forceinline__ void apply_displacement(const FusedArgs& a, int64_t q
 }
 
 // Gather and standardisation of one tile: thread = (particle pl, snapshot sn)
-// reads the 27 stencil records of its snapshot and stores the standardised
-// bf16 features through xs(row, column, value); env[row] = every standardised
-// feature within +-4 (rows past n: zero features, env 0).
+// at position `pos` reads the 27 stencil records of its snapshot and stores the
+// standardised bf16 features through xs(row, column, value); env[row] = every
+// standardised feature within +-4 (rows past n: zero features, env 0).
 template <int ST, class XStore>
 __device__ __forceinline__ void gather_standardise(const FusedArgs& a, const float* plevs, const float* mu,
-                                                   const float* isd, int64_t tile, int tid, XStore xs, int* env) {
+                                                   const float* isd, int64_t tile, int tid, Pos pos, XStore xs,
+                                                   int* env) {
     const Geo& g = a.g;
     using R = typename RecT<ST>::T;
     const int pl = tid >> 1, sn = tid & 1;
@@ -474,8 +572,8 @@ __device__ __forceinline__ void gather_standardise(const FusedArgs& a, const flo
     if (q < a.n) {
         int i0, j0, k0;
         float ox, oy, oz;
-        const double lat = a.lat[q];
-        nearest_node_f32(g, plevs, a.lon[q], lat, a.p[q], i0, j0, k0, ox, oy, oz);
+        const double lat = pos.lat;
+        nearest_node_f32(g, plevs, pos.lon, lat, pos.p, i0, j0, k0, ox, oy, oz);
         const R* rec = static_cast<const R*>(sn ? a.m1.rec : a.m0.rec);
         const float* sc = sn ? a.m1.scales : a.m0.scales;
         int im = i0 - 1, ip = i0 + 1;
@@ -568,7 +666,7 @@ __global__ void __launch_bounds__(256, 1) k_surr_fused(const FusedArgs a) {
     const int lane = tid & 31, warp = tid >> 5, gq = lane >> 2, tq = lane & 3;
     const int64_t ntiles = (a.n + FT - 1) / FT;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        gather_standardise<ST>(a, plevs, mu, isd, tile, tid,
+        gather_standardise<ST>(a, plevs, mu, isd, tile, tid, load_pos(a, tile, tid),
                                [&](int r, int c, __nv_bfloat16 v) { Xs[r * XS + c] = v; }, env);
         __syncthreads();
         // ---- MLP: warp owns rows r0 .. r0+15 ----
@@ -648,7 +746,9 @@ __global__ void __launch_bounds__(256, 1) k_surr_fused(const FusedArgs a) {
         // ---- apply the displacement (or flag the particle for the fallback) ----
         if (tid < FT) {
             const int64_t q = tile * FT + tid;
-            if (q < a.n) apply_displacement(a, q, env[tid], Ys[tid * NOP + 0], Ys[tid * NOP + 1], Ys[tid * NOP + 2]);
+            if (q < a.n)
+                apply_displacement(a, q, pos_of(a, q), env[tid], Ys[tid * NOP + 0], Ys[tid * NOP + 1],
+                                   Ys[tid * NOP + 2]);
         }
         __syncthreads();
     }
@@ -660,25 +760,34 @@ __global__ void __launch_bounds__(256, 1) k_surr_fused(const FusedArgs a) {
 // tcgen05.mma (M = 128 particles; N = 128, 128, 16; K = 176, 128, 128 in steps
 // of 16) issued by one thread, with both operands in shared memory in the
 // K-major core-matrix layout without swizzle and the accumulator in tensor
-// memory.  The epilogues read the accumulators with tcgen05.ld (warp w reads
-// the 32 lanes 32 (w mod 4) + 0..31, half of the columns each), add the bias,
-// apply GELU and write the next layer's operand.  Every wait for the MMA
-// completion is bounded in time; when one gives up the kernel sets *status,
-// stops, frees its tensor memory and returns.
+// memory.  The block is split by role: warps 0-3 (consumers) run the layers --
+// the MMA chains, and the epilogues that read the accumulators with tcgen05.ld
+// (warp w reads the 32 lanes 32 w + 0..31, every column), add the bias, apply
+// GELU and write the next layer's operand in place of the tile's input, which
+// the first layer has consumed -- while warps 4-11 (producers) gather and
+// standardise the next tile into the other of two input buffers.  Full/empty
+// mbarriers hand the buffers over, so the stencil gather of one tile overlaps
+// the layers of the one before.  Every wait (for
+// a buffer or for the MMA completion) is bounded in time; when one gives up
+// the kernel raises an abort flag that every other wait also watches, sets
+// *status, stops, frees its tensor memory and returns.
 // ---------------------------------------------------------------------------
 constexpr int KG1 = KP / 8, KG2 = HID / 8;   // core-matrix columns of the K = 176 and K = 128 operands
 constexpr int NW3 = 16;                      // layer 3: the 3 outputs padded to N = 16
 constexpr uint32_t kTmemCols = 256;          // layer 1 in columns 0..127, layer 2 in 128..255, layer 3 in 0..15
 constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at the SM clock
 constexpr long long kTestWaitCycles = 20000000LL;  // ~10 ms: the wait test hook
+constexpr int kTcConsumers = 128, kTcProducers = 256, kTcThreads = kTcConsumers + kTcProducers;
+constexpr int kConsumerBar = 1;              // named barrier of the consumer warps (0 is __syncthreads)
 
 constexpr size_t kTcW1 = (size_t)HID * KP * 2, kTcW2 = (size_t)HID * HID * 2, kTcW3 = (size_t)NW3 * HID * 2,
                  kTcX = (size_t)FT * KP * 2, kTcH = (size_t)FT * HID * 2;
-constexpr size_t kTcSmem = kTcW1 + kTcW2 + kTcW3 + kTcX + kTcH + (size_t)(2 * HID + NOP) * 4 +
-                           (size_t)2 * KP * 4 + (size_t)FT * 4 + (size_t)kMaxNZ * 4 + 16;
+constexpr size_t kTcSmem = kTcW1 + kTcW2 + kTcW3 + 2 * kTcX + (size_t)(2 * HID + NOP) * 4 +
+                           (size_t)2 * KP * 4 + (size_t)2 * FT * 4 + (size_t)kMaxNZ * 4 + 64;
 static_assert(kTcW1 % 128 == 0 && kTcW2 % 128 == 0 && kTcW3 % 128 == 0 && kTcX % 128 == 0 && kTcH % 128 == 0,
               "operand blocks keep 128-byte alignment");
 static_assert(kTcSmem <= 227 * 1024, "shared memory of the tcgen05 inference kernel");
+static_assert(kTcH <= kTcX, "the hidden activations fit in place of the tile's input");
 
 // Byte offset of element (row r, column k) of a bf16 operand stored as 8 x 8
 // core matrices of 128 contiguous bytes (8 rows of 16 bytes), core matrix
@@ -749,6 +858,42 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, long lo
     }
 }
 
+// mbar_wait that also gives up as soon as another thread of the block has raised *abort.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t mbar, uint32_t phase, long long limit,
+                                                   const volatile int* abort) {
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (done) return true;
+        if (*abort || clock64() - t0 > limit) return false;
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// Named barrier over `n` threads that also ORs a predicate over them: every
+// participant gets the same answer, so a decision to stop stays uniform.
+__device__ __forceinline__ bool bar_red_or(int id, int n, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void bar_sync_n(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
 // 16 consecutive float32 accumulator columns of this thread's lane.  The wait
 // names the registers, so that no use of them is scheduled before it.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
@@ -769,6 +914,26 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// The same load without its wait, and the wait that names the 16 registers it
+// fills (so that no use is scheduled before it): a load can run while the
+// previous chunk is computed.
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait(uint32_t* r) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
     uint32_t r[4];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
@@ -779,44 +944,62 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
     for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Epilogue of layers 1 and 2: accumulator columns [c0, c0 + 64) of this
-// thread's row + bias, GELU, bf16, into the next layer's A operand.
-__device__ __forceinline__ void tc_epilogue_gelu(uint32_t taddr, int row, int c0, const float* bias,
-                                                 unsigned char* Hs) {
-#pragma unroll 1
-    for (int ch = 0; ch < 4; ++ch) {
-        const int c = c0 + 16 * ch;
-        float v[16];
-        tmem_ld16(taddr + (uint32_t)c, v);
-        uint32_t pk[8];
+// 16 accumulator values of columns [c, c + 16) + bias, GELU, bf16, into the next
+// layer's A operand at row `row`.
+__device__ __forceinline__ void gelu_chunk(const uint32_t* v, int row, int c, const float* bias, unsigned char* Hs) {
+    uint32_t pk[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const __nv_bfloat16 lo = __float2bfloat16_rn(gelu(v[2 * i] + bias[c + 2 * i]));
-            const __nv_bfloat16 hi = __float2bfloat16_rn(gelu(v[2 * i + 1] + bias[c + 2 * i + 1]));
-            pk[i] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-        }
-        *reinterpret_cast<uint4*>(Hs + cm_off(row, c, KG2)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        *reinterpret_cast<uint4*>(Hs + cm_off(row, c + 8, KG2)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    for (int i = 0; i < 8; ++i) {
+        const f2_t bb = *reinterpret_cast<const f2_t*>(bias + c + 2 * i);
+        float lo, hi;
+        f2_split(gelu2(f2_add(f2_pack(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])), bb)), lo, hi);
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(lo, hi);
+        pk[i] = *reinterpret_cast<const uint32_t*>(&h2);
+    }
+    *reinterpret_cast<uint4*>(Hs + cm_off(row, c, KG2)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    *reinterpret_cast<uint4*>(Hs + cm_off(row, c + 8, KG2)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+}
+
+// Epilogue of layers 1 and 2 for a whole row: the 128 accumulator columns of
+// this thread's lane, in chunks of 16; the load of each chunk runs while the
+// one before is computed (two register buffers, a loop of two chunks).
+__device__ __forceinline__ void tc_epilogue_gelu_row(uint32_t taddr, int row, const float* bias, unsigned char* Hs) {
+    uint32_t r0[16], r1[16];
+    tmem_ld16_issue(taddr, r0);
+    tmem_ld_wait(r0);
+#pragma unroll 1
+    for (int k = 0; k < HID / 32; ++k) {
+        const int c = 32 * k;
+        tmem_ld16_issue(taddr + (uint32_t)(c + 16), r1);
+        gelu_chunk(r0, row, c, bias, Hs);
+        tmem_ld_wait(r1);
+        if (k + 1 < HID / 32) tmem_ld16_issue(taddr + (uint32_t)(c + 32), r0);
+        gelu_chunk(r1, row, c + 16, bias, Hs);
+        if (k + 1 < HID / 32) tmem_ld_wait(r0);
     }
 }
 
 template <int ST>
-__global__ void __launch_bounds__(256, 1) k_surr_fused_tc(const FusedArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_surr_fused_tc(const FusedArgs a) {
     extern __shared__ __align__(128) unsigned char tc_smem[];
-    unsigned char* W1s = tc_smem;                       // B of layer 1: [HID][KP] core matrices
+    unsigned char* W1s = tc_smem;                    // B of layer 1: [HID][KP] core matrices
     unsigned char* W2s = W1s + kTcW1;                // B of layer 2: [HID][HID]
     unsigned char* W3s = W2s + kTcW2;                // B of layer 3: [16][HID] (rows 3..15 zero)
-    unsigned char* Xs = W3s + kTcW3;                 // A of layer 1: [FT][KP]
-    unsigned char* Hs = Xs + kTcX;                   // A of layers 2 and 3: [FT][HID]
-    float* bias = reinterpret_cast<float*>(Hs + kTcH);          // b1 | b2 | b3
+    unsigned char* Xs0 = W3s + kTcW3;                // A of layer 1 ([FT][KP]), then of layers 2 and 3
+                                                     // ([FT][HID]): two buffers
+    float* bias = reinterpret_cast<float*>(Xs0 + 2 * kTcX);     // b1 | b2 | b3
     float* mu = bias + 2 * HID + NOP;                            // [KP]
     float* isd = mu + KP;                                        // [KP]
-    int* env = reinterpret_cast<int*>(isd + KP);                 // [FT]
-    float* plevs = reinterpret_cast<float*>(env + FT);           // [kMaxNZ]
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(plevs + kMaxNZ);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+    int* env = reinterpret_cast<int*>(isd + KP);                 // [2][FT]
+    float* plevs = reinterpret_cast<float*>(env + 2 * FT);       // [kMaxNZ]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(plevs + kMaxNZ);   // full[2], empty[2], mma
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 5);
+    int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+    const volatile int* vabort = abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t mb = smem_u32(mbar);
+    const uint32_t full_b[2] = {smem_u32(&bars[0]), smem_u32(&bars[1])};
+    const uint32_t empty_b[2] = {smem_u32(&bars[2]), smem_u32(&bars[3])};
+    const uint32_t mma_b = smem_u32(&bars[4]);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -825,8 +1008,13 @@ __global__ void __launch_bounds__(256, 1) k_surr_fused_tc(const FusedArgs a) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full_b[b]), "r"(kTcProducers) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(empty_b[b]), "r"(kTcConsumers) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mma_b) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *abort_flag = 0;
     }
     for (int e = tid; e < a.g.nz; e += blockDim.x) plevs[e] = a.g.plev[e];
     // weights as B operands (N x K, K-major): W1 [k][n] -> (n, k)
@@ -857,59 +1045,99 @@ __global__ void __launch_bounds__(256, 1) k_surr_fused_tc(const FusedArgs a) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tmem_slot;
-    // this warp's lanes (rows) and column half in the epilogues
-    const int row = 32 * (warp & 3) + (tid & 31), chalf = warp >> 2;
-    const uint32_t tlane = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
-    const uint32_t xs_a = smem_u32(Xs), hs_a = smem_u32(Hs);
-    const uint32_t w1_a = smem_u32(W1s), w2_a = smem_u32(W2s), w3_a = smem_u32(W3s);
-    uint32_t phase = 0;
-    bool failed = false;
     const int64_t ntiles = (a.n + FT - 1) / FT;
-    for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-        gather_standardise<ST>(
-            a, plevs, mu, isd, tile, tid,
-            [&](int r, int c, __nv_bfloat16 v) { *reinterpret_cast<__nv_bfloat16*>(Xs + cm_off(r, c, KG1)) = v; },
-            env);
-        // three layers: MMA chain by thread 0, completion on the mbarrier, epilogue by all
-#pragma unroll 1
-        for (int layer = 0; layer < 3; ++layer) {
-            fence_async_smem();
-            tc_fence_before();
-            __syncthreads();
-            if (tid == 0 && !a.withhold_mma) {
-                tc_fence_after();
-                if (layer == 0)
-                    umma_layer(tbase, xs_a, w1_a, KP / 16, KG1, umma_idesc(FT, HID));
-                else if (layer == 1)
-                    umma_layer(tbase + 128u, hs_a, w2_a, HID / 16, KG2, umma_idesc(FT, HID));
-                else
-                    umma_layer(tbase, hs_a, w3_a, HID / 16, KG2, umma_idesc(FT, NW3));
-                umma_commit(mb);
+
+    if (warp >= kTcConsumers / 32) {
+        // ---- producers: gather and standardise tile i into buffer i mod 2 ----
+        const int pt = tid - kTcConsumers;   // (particle, snapshot) item pt of the tile
+        int i = 0;
+        // the positions of the next tile are loaded while this one is gathered (the consumers
+        // write positions only of tiles the producers are done with)
+        Pos next = blockIdx.x < ntiles ? load_pos(a, blockIdx.x, pt) : Pos{0.0, 0.0, 0.0};
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+            const int b = i & 1;
+            const Pos pos = next;
+            if (tile + gridDim.x < ntiles) next = load_pos(a, tile + gridDim.x, pt);
+            if (i >= 2) {   // the consumers are done with tile i - 2 in this buffer
+                const bool ok = mbar_wait_or_abort(empty_b[b], (uint32_t)(((i >> 1) - 1) & 1), a.wait_cycles, vabort);
+                if (__any_sync(0xffffffffu, !ok)) {
+                    *abort_flag = 1;
+                    break;
+                }
             }
-            const bool ok = mbar_wait(mb, phase, a.wait_cycles);
-            phase ^= 1u;
-            if (__syncthreads_or(!ok)) {
+            unsigned char* X = Xs0 + b * kTcX;
+            auto xs = [&](int r, int c, __nv_bfloat16 v) { *reinterpret_cast<__nv_bfloat16*>(X + cm_off(r, c, KG1)) = v; };
+            gather_standardise<ST>(a, plevs, mu, isd, tile, pt, pos, xs, env + b * FT);
+            fence_async_smem();   // the tensor cores read what the generic stores wrote
+            mbar_arrive(full_b[b]);
+        }
+    } else {
+        // ---- consumers: the three layers of tile i and the displacement ----
+        const int row = tid;
+        const uint32_t tlane = tbase + ((uint32_t)(32 * warp) << 16);
+        const uint32_t w1_a = smem_u32(W1s), w2_a = smem_u32(W2s), w3_a = smem_u32(W3s);
+        uint32_t phase = 0;
+        bool failed = false;
+        int i = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x, ++i) {
+            const int b = i & 1;
+            const bool ok_in = mbar_wait_or_abort(full_b[b], (uint32_t)((i >> 1) & 1), a.wait_cycles, vabort);
+            if (bar_red_or(kConsumerBar, kTcConsumers, !ok_in)) {
                 failed = true;
                 break;
             }
-            tc_fence_after();
-            if (layer == 0) {
-                tc_epilogue_gelu(tlane, row, 64 * chalf, bias, Hs);
-            } else if (layer == 1) {
-                tc_epilogue_gelu(tlane + 128u, row, 64 * chalf, bias + HID, Hs);
-            } else if (warp < 4) {
-                float y[4];
-                tmem_ld4(tlane, y);
-                const int64_t q = tile * FT + row;
-                if (q < a.n)
-                    apply_displacement(a, q, env[row], y[0] + bias[2 * HID], y[1] + bias[2 * HID + 1],
-                                       y[2] + bias[2 * HID + 2]);
+            unsigned char* Xb = Xs0 + b * kTcX;
+            const uint32_t xs_a = smem_u32(Xb);   // the input, then (after layer 1) the hidden activations
+            const Pos mine = pos_of(a, tile * FT + row);   // read now, used after the third layer
+#pragma unroll 1
+            for (int layer = 0; layer < 3; ++layer) {
+                if (layer > 0) {   // this layer's operand, written by every consumer, reaches the tensor cores
+                    fence_async_smem();
+                    tc_fence_before();
+                    bar_sync_n(kConsumerBar, kTcConsumers);
+                }
+                if (tid == 0 && !a.withhold_mma) {
+                    tc_fence_after();
+                    if (layer == 0)
+                        umma_layer(tbase, xs_a, w1_a, KP / 16, KG1, umma_idesc(FT, HID));
+                    else if (layer == 1)
+                        umma_layer(tbase + 128u, xs_a, w2_a, HID / 16, KG2, umma_idesc(FT, HID));
+                    else
+                        umma_layer(tbase, xs_a, w3_a, HID / 16, KG2, umma_idesc(FT, NW3));
+                    umma_commit(mma_b);
+                }
+                const bool ok = mbar_wait_or_abort(mma_b, phase, a.wait_cycles, vabort);
+                phase ^= 1u;
+                if (bar_red_or(kConsumerBar, kTcConsumers, !ok)) {
+                    failed = true;
+                    break;
+                }
+                tc_fence_after();
+                if (layer == 0) {
+                    tc_epilogue_gelu_row(tlane, row, bias, Xb);
+                } else if (layer == 1) {
+                    tc_epilogue_gelu_row(tlane + 128u, row, bias + HID, Xb);
+                } else {
+                    float y[4];
+                    tmem_ld4(tlane, y);
+                    const int64_t q = tile * FT + row;
+                    if (q < a.n)
+                        apply_displacement(a, q, mine, env[b * FT + row], y[0] + bias[2 * HID],
+                                           y[1] + bias[2 * HID + 1], y[2] + bias[2 * HID + 2]);
+                }
             }
+            if (failed) break;
+            // every accumulator read of this tile is done before the next tile's MMAs overwrite
+            // them; the input buffer and its envelope flags go back to the producers
+            tc_fence_before();
+            bar_sync_n(kConsumerBar, kTcConsumers);
+            mbar_arrive(empty_b[b]);
         }
+        if (failed) *abort_flag = 1;
     }
-    if (failed && tid == 0) atomicExch(a.status, 1);
     tc_fence_before();
     __syncthreads();
+    if (tid == 0 && *vabort) atomicExch(a.status, 1);
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols) : "memory");
@@ -1240,20 +1468,20 @@ cudaError_t launch_colstats(const float* D, int64_t n, int ncol, double* sum, do
 }
 
 template <class K>
-cudaError_t launch_dyn(K kern, int grid, size_t smem, const FusedArgs& a, cudaStream_t s) {
+cudaError_t launch_dyn(K kern, int grid, int threads, size_t smem, const FusedArgs& a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, 256, smem, s>>>(a);
+    kern<<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int ST>
 cudaError_t launch_surr_fused_st(int kernel, int grid, const FusedArgs& a, cudaStream_t s) {
-    if (kernel == MPTRAC_SURR_KERNEL_MMA_SYNC) return launch_dyn(k_surr_fused<ST>, grid, kFusedSmem, a, s);
+    if (kernel == MPTRAC_SURR_KERNEL_MMA_SYNC) return launch_dyn(k_surr_fused<ST>, grid, 256, kFusedSmem, a, s);
     FusedArgs t = a;
     t.withhold_mma = kernel == MPTRAC_SURR_KERNEL_WAIT_TEST ? 1 : 0;
     t.wait_cycles = t.withhold_mma ? kTestWaitCycles : kWaitCycles;
-    return launch_dyn(k_surr_fused_tc<ST>, grid, kTcSmem, t, s);
+    return launch_dyn(k_surr_fused_tc<ST>, grid, kTcThreads, kTcSmem, t, s);
 }
 
 cudaError_t launch_surr_fused(int storage, Surrogate& S, const Geo& g, MetView m0, MetView m1, int64_t n,
