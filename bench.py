@@ -491,7 +491,10 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         ms2 = max_over_ranks(s2.elapsed_time(e2))
         e2e = {"value": aggregate_rate(psteps_per_pass * k2, world, ms2), "unit": "particle-steps/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "copies": "particle state in and final lon/lat/p out: torch copies between pinned host buffers "
+                         "and the device on the timed stream; the 5 met snapshots: mptrac_load_met from pinned "
+                         "host memory (prefetched on a copy stream by the Simulation); compute through the C ABI"}
 
     # ---- the added forms on the same GPU: 16-bit storage, batched releases, surrogate ----
     forms, finals = None, {}
@@ -921,7 +924,7 @@ def surrogate_figures(dev, grid, snaps, n, n_train, epochs):
                       "speedup_vs_plain": ms_plain / ms, "km_median": float(np.median(km)),
                       "km_p99": float(np.quantile(km, 0.99)), "dp_rel_median": float(np.median(dp)),
                       "dp_rel_p99": float(np.quantile(dp, 0.99))}
-    runs["surrogate"]["fallback_fraction"] = float(fb)
+    runs["surrogate"]["fallback_fraction"] = fb[0].item() / fb[1]
     ctx.close()
     return {"runs": runs, "train_seconds": t_train, "dataset_seconds": t_data, "epochs": epochs,
             "train_samples": n_train, "particles": n, "train_loss": hist, "val_loss": val,

@@ -354,10 +354,14 @@ int mptrac_surr_features(mptrac_ctx* ctx, const mptrac_particles* parts, double 
 int mptrac_surr_targets(int64_t n, const double* lon0, const double* lat0, const double* p0,
                         const double* lon1, const double* lat1, const double* p1, float* y,
                         uintptr_t stream);
-/* Adds the column sums and sums of squares of DEVICE data [n][ncol] (float32)
- * to DEVICE sum[ncol], sumsq[ncol] (float64; the caller zeroes them). */
-int mptrac_surr_colstats(const float* data, int64_t n, int ncol, double* sum, double* sumsq,
-                         uintptr_t stream);
+/* Column means and standard deviations of DEVICE data [n][ncol] (float32,
+ * n >= 1, ncol <= 4096) into DEVICE mean[ncol], sd[ncol] (float64): sums in
+ * float32 per block of rows (compensated) and in float64 across blocks, then
+ * sd = sqrt(max(sum of squares / n - mean^2, 0)).  An sd not above sd_min is
+ * written as 1, so that a constant column (a padding feature) standardises to
+ * zero.  The statistics the surrogate's standardisation takes (training). */
+int mptrac_surr_colstats(const float* data, int64_t n, int ncol, double* mean, double* sd,
+                         double sd_min, uintptr_t stream);
 /* Normalised outputs y_hat of n <= max_batch DEVICE raw feature rows into
  * DEVICE y_hat [n][8] (columns 3..7 are zero padding). */
 int mptrac_surr_forward(mptrac_surr* s, const float* x, int64_t n, float* y_hat, uintptr_t stream);
@@ -374,9 +378,10 @@ int mptrac_surr_train_step(mptrac_surr* s, const float* x, const float* y, int64
  * feature within +-4, [t, t + dt_seg] inside the loaded snapshots) move by
  * the predicted displacement followed by the position rules; the others are
  * left in place with fallback[i] = 1 (DEVICE uint8 [n]) for the plain
- * integrator (mptrac_advect_masked).  Any n (processed in max_batch chunks). */
+ * integrator (mptrac_advect_masked).  If fallback_count (DEVICE uint64) is not
+ * NULL, the number of particles flagged is ADDED to it.  Any n. */
 int mptrac_surr_advance(mptrac_ctx* ctx, mptrac_surr* s, const mptrac_particles* parts, double t,
-                        double dt_seg, uint8_t* fallback, uintptr_t stream);
+                        double dt_seg, uint8_t* fallback, uint64_t* fallback_count, uintptr_t stream);
 /* Tensor-core kernels of the surrogate (training GEMMs and the fused
  * inference in mptrac_surr_advance):
  *   MPTRAC_SURR_KERNEL_TCGEN05 (default): tcgen05.mma chains issued by one

@@ -95,13 +95,14 @@ SIGNATURES = {
     "mptrac_surr_features": (C.c_int, [C.c_void_p, C.POINTER(ParticlesDesc), C.c_double, C.c_void_p, C.c_void_p]),
     "mptrac_surr_targets": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p]),
-    "mptrac_surr_colstats": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mptrac_surr_colstats": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_double,
+                                       C.c_void_p]),
     "mptrac_surr_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "mptrac_surr_grads": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "mptrac_surr_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_int,
                                          C.c_void_p, C.c_void_p]),
     "mptrac_surr_advance": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(ParticlesDesc), C.c_double, C.c_double,
-                                      C.c_void_p, C.c_void_p]),
+                                      C.c_void_p, C.c_void_p, C.c_void_p]),
     "mptrac_surr_set_kernel": (C.c_int, [C.c_void_p, C.c_int]),
     "mptrac_surr_status": (C.c_int, [C.c_void_p, C.c_void_p]),
 }
@@ -441,9 +442,11 @@ class Surrogate:
         check(load().mptrac_surr_train_step(self.h, _ptr(x), _ptr(y), x.shape[0], float(lr), int(step),
                                             _ptr(loss), _stream(stream)))
 
-    def advance(self, ctx: "Context", parts: "Particles", t, dt_seg, fallback: torch.Tensor, stream=None):
+    def advance(self, ctx: "Context", parts: "Particles", t, dt_seg, fallback: torch.Tensor,
+                count: torch.Tensor | None = None, stream=None):
+        """One surrogate segment; ``count`` (int64 device tensor, optional) accumulates the fallback particles."""
         check(load().mptrac_surr_advance(ctx.h, self.h, C.byref(parts.desc()), float(t), float(dt_seg),
-                                         _ptr(fallback), _stream(stream)), ctx.h)
+                                         _ptr(fallback), _ptr(count), _stream(stream)), ctx.h)
 
     def set_kernel(self, kernel: int):
         """SURR_KERNEL_TCGEN05 (default) or SURR_KERNEL_MMA_SYNC for the fused inference."""
@@ -470,15 +473,14 @@ def surr_targets(p0: "Particles", p1: "Particles", out: torch.Tensor | None = No
     return out
 
 
-def colstats(data: torch.Tensor, stream=None):
-    """Column mean and standard deviation of a [n][ncol] float32 device tensor (synchronises)."""
+def colstats(data: torch.Tensor, sd_min: float = 1e-12, stream=None):
+    """Column mean and standard deviation of a [n][ncol] float32 device tensor (synchronises);
+    a standard deviation not above sd_min comes back as 1 (``mptrac_surr_colstats``)."""
     n, ncol = data.shape
-    s = torch.zeros(ncol, dtype=torch.float64, device=data.device)
-    s2 = torch.zeros(ncol, dtype=torch.float64, device=data.device)
-    check(load().mptrac_surr_colstats(_ptr(data), n, ncol, _ptr(s), _ptr(s2), _stream(stream)))
-    mean = (s / n).cpu().numpy()
-    var = np.maximum((s2 / n).cpu().numpy() - mean * mean, 0.0)
-    return mean, np.sqrt(var)
+    mean = torch.empty(ncol, dtype=torch.float64, device=data.device)
+    sd = torch.empty(ncol, dtype=torch.float64, device=data.device)
+    check(load().mptrac_surr_colstats(_ptr(data), n, ncol, _ptr(mean), _ptr(sd), float(sd_min), _stream(stream)))
+    return mean.cpu().numpy(), sd.cpu().numpy()
 
 
 def advect_masked(ctx: "Context", parts: "Particles", mask: torch.Tensor, t, dt, nsteps, stream=None):

@@ -870,12 +870,12 @@ int mptrac_surr_targets(int64_t n, const double* lon0, const double* lat0, const
     return ok();
 }
 
-int mptrac_surr_colstats(const float* data, int64_t n, int ncol, double* sum, double* sumsq, uintptr_t stream) {
-    if (n < 0 || ncol <= 0 || ncol > 4096) return fail(MPTRAC_E_INVALID_ARG, "bad size");
-    if (n == 0) return ok();
-    if (!device_accessible(data) || !device_accessible(sum) || !device_accessible(sumsq))
+int mptrac_surr_colstats(const float* data, int64_t n, int ncol, double* mean, double* sd, double sd_min,
+                         uintptr_t stream) {
+    if (n < 1 || ncol <= 0 || ncol > 4096) return fail(MPTRAC_E_INVALID_ARG, "bad size (n >= 1, 1 <= ncol <= 4096)");
+    if (!device_accessible(data) || !device_accessible(mean) || !device_accessible(sd))
         return fail(MPTRAC_E_INVALID_ARG, "colstats arrays must be device memory");
-    MPTRAC_CUDA(launch_colstats(data, n, ncol, sum, sumsq, reinterpret_cast<cudaStream_t>(stream)));
+    MPTRAC_CUDA(launch_colstats(data, n, ncol, mean, sd, sd_min, reinterpret_cast<cudaStream_t>(stream)));
     return ok();
 }
 
@@ -916,7 +916,7 @@ int mptrac_surr_train_step(mptrac_surr* s, const float* x, const float* y, int64
 }
 
 int mptrac_surr_advance(mptrac_ctx* c, mptrac_surr* s, const mptrac_particles* P, double t, double dt_seg,
-                        uint8_t* fallback, uintptr_t stream) {
+                        uint8_t* fallback, uint64_t* fallback_count, uintptr_t stream) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
     DeviceGuard device_guard(c->device);
     if (!s) return fail(MPTRAC_E_NOT_INIT, "surrogate is NULL");
@@ -931,12 +931,14 @@ int mptrac_surr_advance(mptrac_ctx* c, mptrac_surr* s, const mptrac_particles* P
     if (!(dt_seg > 0)) return fail(MPTRAC_E_INVALID_ARG, "dt_seg must be > 0");
     if (P->n == 0) return ok();
     if (!device_accessible(fallback)) return fail(MPTRAC_E_INVALID_ARG, "fallback must be device memory");
+    if (fallback_count && !device_accessible(fallback_count))
+        return fail(MPTRAC_E_INVALID_ARG, "fallback_count must be device memory");
     const int window_ok = (t + dt_seg <= t1 + 1e-9 * (t1 - t0)) ? 1 : 0;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const float w = (float)((t - t0) / (t1 - t0));
     MPTRAC_CUDA(launch_surr_fused(c->storage, s->S, c->geo, MetView{c->d_met[s0], c->d_scales[s0]},
                                   MetView{c->d_met[s1], c->d_scales[s1]}, P->n, P->lon, P->lat, P->p, w,
-                                  window_ok, fallback, c->lon0, st));
+                                  window_ok, fallback, fallback_count, c->lon0, st));
     return ok();
 }
 

@@ -178,10 +178,11 @@ cudaError_t launch_surr_features(int storage, const Geo& g, MetView m0, MetView 
 cudaError_t launch_surr_targets(int64_t n, const double* lon0, const double* lat0, const double* p0,
                                 const double* lon1, const double* lat1, const double* p1, float* Y,
                                 cudaStream_t s);
-cudaError_t launch_colstats(const float* D, int64_t n, int ncol, double* sum, double* sumsq, cudaStream_t s);
+cudaError_t launch_colstats(const float* D, int64_t n, int ncol, double* mean, double* sd, double sd_min,
+                            cudaStream_t s);
 cudaError_t launch_surr_fused(int storage, Surrogate& S, const Geo& g, MetView m0, MetView m1, int64_t n,
                               double* lon, double* lat, double* p, float w, int window_ok, uint8_t* fallback,
-                              double lon0, cudaStream_t s);
+                              uint64_t* fallback_count, double lon0, cudaStream_t s);
 
 
 }  // namespace mptrac

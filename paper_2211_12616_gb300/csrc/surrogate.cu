@@ -148,6 +148,17 @@ __global__ void k_colstats(const float* __restrict__ D, int64_t n, int ncol, int
     }
 }
 
+// the sums (in mean, sd) -> mean and standard deviation; sd <= sd_min -> 1
+__global__ void k_colstats_final(int64_t n, int ncol, double sd_min, double* mean, double* sd) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncol) return;
+    const double m = mean[c] / (double)n;
+    const double v = fmax(sd[c] / (double)n - m * m, 0.0);
+    const double sdev = sqrt(v);
+    mean[c] = m;
+    sd[c] = sdev > sd_min ? sdev : 1.0;
+}
+
 // ---------------------------------------------------------------------------
 // BF16 tensor-core GEMM (mma.sync m16n8k16, f32 accumulate) with epilogues
 // C[M x N] = A[M x K] * B[K x N]; element (m, k) of A at A[m*sam + k*sak],
@@ -472,6 +483,7 @@ struct FusedArgs {
     int* status;            // set to 1 when a bounded wait of the tcgen05 kernel gives up
     long long wait_cycles;  // limit of each wait for the tensor cores (SM clock cycles)
     int withhold_mma;       // test hook: issue no MMA (nothing completes, the wait runs out)
+    unsigned long long* fb_count;   // if not null: the number of fallback particles is added here
 };
 
 constexpr size_t kFusedSmem = (size_t)HID * XS * 2 + (size_t)HID * HS * 2 + (size_t)NOP * HS * 2 +
@@ -539,6 +551,11 @@ __device__ __forceinline__ void apply_displacement(const FusedArgs& a, int64_t q
     const double la = pos.lat;
     const bool ok = a.window_ok && env_ok && fabs(la) <= 80.0;
     a.fallback[q] = ok ? 0 : 1;
+    if (a.fb_count) {   // the lanes of the warp that flag a fallback, counted with one atomic
+        const unsigned act = __activemask();
+        const unsigned fb = __ballot_sync(act, !ok);
+        if (fb && (int)(threadIdx.x & 31) == __ffs(act) - 1) atomicAdd(a.fb_count, (unsigned long long)__popc(fb));
+    }
     if (!ok) return;
     const float dx = y0 * a.sd_y[0] + a.mu_y[0];
     const float dy = y1 * a.sd_y[1] + a.mu_y[1];
@@ -1460,10 +1477,15 @@ cudaError_t launch_surr_targets(int64_t n, const double* lon0, const double* lat
     return cudaGetLastError();
 }
 
-cudaError_t launch_colstats(const float* D, int64_t n, int ncol, double* sum, double* sumsq, cudaStream_t s) {
+cudaError_t launch_colstats(const float* D, int64_t n, int ncol, double* mean, double* sd, double sd_min,
+                            cudaStream_t s) {
     const int rpb = 2048;
-    note_launches(1);
-    k_colstats<<<grid1(n, rpb), 256, 0, s>>>(D, n, ncol, rpb, sum, sumsq);
+    cudaError_t e = cudaMemsetAsync(mean, 0, (size_t)ncol * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sd, 0, (size_t)ncol * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    note_launches(2);
+    k_colstats<<<grid1(n, rpb), 256, 0, s>>>(D, n, ncol, rpb, mean, sd);
+    k_colstats_final<<<(ncol + 255) / 256, 256, 0, s>>>(n, ncol, sd_min, mean, sd);
     return cudaGetLastError();
 }
 
@@ -1486,10 +1508,11 @@ cudaError_t launch_surr_fused_st(int kernel, int grid, const FusedArgs& a, cudaS
 
 cudaError_t launch_surr_fused(int storage, Surrogate& S, const Geo& g, MetView m0, MetView m1, int64_t n,
                               double* lon, double* lat, double* p, float w, int window_ok, uint8_t* fallback,
-                              double lon0, cudaStream_t s) {
+                              uint64_t* fallback_count, double lon0, cudaStream_t s) {
     FusedArgs a{g, m0, m1, n, lon, lat, p, fallback, w, window_ok, S.W1b, S.W2b, S.W3b,
                 S.theta + OB1, S.theta + OB2, S.b3p, S.mu_x, S.isd_x, S.mu_y, S.sd_y,
                 lon0, g.pmin_d, g.pmax_d, S.status, kWaitCycles, 0};
+    a.fb_count = reinterpret_cast<unsigned long long*>(fallback_count);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -20,7 +20,6 @@ from __future__ import annotations
 
 import math
 
-import numpy as np
 import torch
 
 from ._native import (Context, Particles, Surrogate, advect_masked, colstats, surr_features,
@@ -75,9 +74,8 @@ def train(surr: Surrogate, X: torch.Tensor, Y: torch.Tensor, epochs: int = 4, ba
     X, Y = X[perm], Y[perm]
     n_val = int(n * val_frac)
     Xt, Yt, Xv, Yv = X[n_val:], Y[n_val:], X[:n_val], Y[:n_val]
-    mu_x, sd_x = colstats(Xt)
+    mu_x, sd_x = colstats(Xt)      # constant (padding) columns come back with sd 1
     mu_y, sd_y = colstats(Yt)
-    sd_x = np.where(sd_x > 1e-12, sd_x, 1.0)
     surr.set_norm(mu_x, sd_x, mu_y, sd_y)
     nt = Xt.shape[0]
     steps_per_epoch = nt // batch
@@ -110,7 +108,8 @@ def evaluate(surr: Surrogate, X: torch.Tensor, Y: torch.Tensor, batch: int = 819
 
 def run_surrogate(ctx: Context, surr: Surrogate, parts: Particles, snapshot_at, dt_met: float, t_start: float,
                   t_end: float, stream=None, workspace=None):
-    """Surrogate segments with the plain fallback; returns the fraction of fallback particle-segments.
+    """Surrogate segments with the plain fallback; returns (device count of fallback particle-segments,
+    particle-segments).
 
     Particles are sorted by met cell at the start of every met interval, which also groups the
     fallback particles (poles, rare wind patterns) into whole warps of the masked plain kernel.
@@ -120,17 +119,16 @@ def run_surrogate(ctx: Context, surr: Surrogate, parts: Particles, snapshot_at, 
         workspace = torch.empty(ctx.sort_workspace_bytes(parts.n), dtype=torch.uint8, device=parts.lon.device)
     segs_per_iv = int(round(dt_met / DT_SEG))
     n_iv = int(round((t_end - t_start) / dt_met))
-    fb = torch.zeros((), dtype=torch.float64, device=parts.lon.device)
+    count = torch.zeros(1, dtype=torch.int64, device=parts.lon.device)   # fallback particle-segments
     for iv in range(n_iv):
         ta = t_start + iv * dt_met
         _load_interval(ctx, snapshot_at, ta, ta + dt_met, stream)
         ctx.sort(parts, workspace, stream=stream)
         for sg in range(segs_per_iv):
             t = ta + sg * DT_SEG
-            surr.advance(ctx, parts, t, DT_SEG, fallback, stream=stream)
+            surr.advance(ctx, parts, t, DT_SEG, fallback, count, stream=stream)
             advect_masked(ctx, parts, fallback, t, DT, SEG_STEPS, stream=stream)
-            fb += fallback.sum()
-    return fb / (parts.n * segs_per_iv * n_iv)
+    return count, parts.n * segs_per_iv * n_iv
 
 
 def run_plain(ctx: Context, parts: Particles, snapshot_at, dt_met: float, t_start: float, t_end: float,

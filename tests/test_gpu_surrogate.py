@@ -240,7 +240,7 @@ def test_training_gains_over_untrained_and_first_order(M, field):
     raw.set_params(S.flatten(S.init_params(5)).astype(np.float32))
     mu_x, sd_x = M.colstats(X)
     mu_y, sd_y = M.colstats(Y)
-    raw.set_norm(mu_x, np.where(sd_x > 1e-12, sd_x, 1.0), mu_y, sd_y)
+    raw.set_norm(mu_x, sd_x, mu_y, sd_y)
     untrained = evaluate(raw, X[:20000], Y[:20000])
     assert val < 0.05 * untrained, (val, untrained)
     # first-order step u(x0, t0) * 1800 s from the stencil's centre node, in the same normalised units
@@ -301,7 +301,7 @@ def test_tcgen05_inference_equals_mma_sync(M, field, n):
     sur.set_params(S.flatten(S.init_params(5)).astype(np.float32))
     mu_x, sd_x = M.colstats(X)
     mu_y, sd_y = M.colstats(Y)
-    sur.set_norm(mu_x, np.where(sd_x > 1e-12, sd_x, 1.0), mu_y, sd_y)
+    sur.set_norm(mu_x, sd_x, mu_y, sd_y)
     a, fa = _advance_with(M, sur, ctx, st, M.SURR_KERNEL_MMA_SYNC, n)
     b, fb = _advance_with(M, sur, ctx, st, M.SURR_KERNEL_TCGEN05, n)
     np.testing.assert_array_equal(fb, fa)
@@ -321,7 +321,7 @@ def test_bounded_wait_reports_timeout_and_recovers(M, field):
     sur.set_params(S.flatten(S.init_params(7)).astype(np.float32))
     mu_x, sd_x = M.colstats(X)
     mu_y, sd_y = M.colstats(Y)
-    sur.set_norm(mu_x, np.where(sd_x > 1e-12, sd_x, 1.0), mu_y, sd_y)
+    sur.set_norm(mu_x, sd_x, mu_y, sd_y)
     sur.set_kernel(M.SURR_KERNEL_WAIT_TEST)
     parts = M.Particles.from_numpy(st, meso=False, release=False)
     fb = torch.zeros(2000, dtype=torch.uint8, device="cuda")
