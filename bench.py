@@ -187,6 +187,14 @@ def measure_l2_gbs(dev):
     return max(measure_copy_gbs(dev, mb, 100) for mb in (8, 16, 24))
 
 
+def _bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -912,6 +920,33 @@ def surrogate_figures(dev, grid, snaps, n, n_train, epochs):
         o = np.argsort(d["id"])
         return {k: v[o] for k, v in d.items()}
 
+    # the inference kernel alone: one segment over all particles, after the 48 h runs (sorted state)
+    fbuf = torch.zeros(n, dtype=torch.uint8, device=dev)
+    ctx.load_met(0, 0.0, *at(0.0))
+    ctx.load_met(1, DT_MET, *at(DT_MET))
+    probe = init.clone()
+    ctx.sort(probe, ws)
+    inf_ms = []
+    for _ in range(4):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sur.advance(ctx, probe, 3600.0, learn.DT_SEG, fbuf, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        inf_ms.append(a.elapsed_time(b))
+        probe.copy_(init)
+        ctx.sort(probe, ws)
+    sur.status()
+    t_inf = min(inf_ms[1:]) / 1000.0 / n                       # seconds per particle and segment
+    flop = 2 * (176 * 128 + 128 * 128 + 128 * 16)             # the three layers as computed (N of layer 3 padded to 16)
+    gather_b = 27 * 2 * 16                                      # 27 nodes x 2 snapshots x 16-byte records
+    peak_tf = _bf16_peak()
+    l2 = measure_l2_gbs(dev)
+    inference = {"ns_per_particle": t_inf * 1e9, "flop_per_particle": flop, "gather_bytes_per_particle": gather_b,
+                 "tensor_bound_ns": flop / (peak_tf * 1e12) * 1e9, "gather_bound_ns": gather_b / (l2 * 1e9) * 1e9,
+                 "frac_of_gather_bound": gather_b / (l2 * 1e9) / t_inf, "frac_of_tensor_bound": flop / (peak_tf * 1e12) / t_inf,
+                 "peaks": f"bf16 {peak_tf:.0f} TFLOP/s (MEASURED_PEAKS.json burst), L2 copy {l2:.0f} GB/s (measured here)"}
     ref = by_id(plain)
     substeps = n * int(round(SURR_T_END / DT))
     runs = {}
@@ -926,7 +961,7 @@ def surrogate_figures(dev, grid, snaps, n, n_train, epochs):
                       "dp_rel_p99": float(np.quantile(dp, 0.99))}
     runs["surrogate"]["fallback_fraction"] = fb[0].item() / fb[1]
     ctx.close()
-    return {"runs": runs, "train_seconds": t_train, "dataset_seconds": t_data, "epochs": epochs,
+    return {"runs": runs, "inference": inference, "train_seconds": t_train, "dataset_seconds": t_data, "epochs": epochs,
             "train_samples": n_train, "particles": n, "train_loss": hist, "val_loss": val,
             "workload": f"surrogate trained on {n_train} plain 30-min trajectories of the 1deg field, "
                         f"{n} particles, 48 h; errors against plain midpoint at 180 s"}
@@ -951,7 +986,7 @@ def run_surrogate_bench(args, rank, world):
             "config": {"workload": f["workload"] + "; value in 180-s substep equivalents per second",
                        "train_seconds": f["train_seconds"], "dataset_seconds": f["dataset_seconds"],
                        "epochs": f["epochs"], "train_loss": f["train_loss"], "val_loss": f["val_loss"]},
-            "surrogate": runs}
+            "surrogate": runs, "inference": f["inference"]}
     print(json.dumps(line), flush=True)
 
 
