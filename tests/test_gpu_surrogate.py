@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import met as omet
 from oracle import surrogate as S
 from oracle import transport as tr
 from workloads import fourier_modes, fourier_snapshot, grid_global, uniform_particles
@@ -21,6 +22,52 @@ def field(M):
     f1 = fourier_snapshot(grid, m, T6H)
     ctx = make_ctx(M, grid, [f0, f1], [0.0, T6H])
     return grid, f0, f1, ctx
+
+
+STORAGES = pytest.mark.parametrize("storage", [0, 1, 2], ids=["fp32", "bf16", "fp16"])
+
+
+@pytest.fixture(scope="module")
+def stored(M, field):
+    """Per storage: a context holding the two snapshots in that storage, and the values it holds
+    (the oracle's view of the same stored fields, decoded to float64)."""
+    grid, f0, f1, _ = field
+    cache = {}
+
+    def get(storage):
+        if storage not in cache:
+            ctx = make_ctx(M, grid, [f0, f1], [0.0, T6H], storage=storage)
+            cache[storage] = (ctx, omet.stored_fields(f0, storage), omet.stored_fields(f1, storage))
+        return cache[storage]
+    return get
+
+
+@STORAGES
+def test_features_match_oracle(M, field, stored, storage):
+    """Stencil features from the stored snapshots (16-bit codes decoded with their level scales),
+    offsets, time weight and sin/cos of latitude, against the oracle on the same stored values."""
+    grid = field[0]
+    ctx, f0, f1 = stored(storage)
+    st = uniform_particles(20_000, grid.plev, seed=3)
+    parts = M.Particles.from_numpy(st)
+    t = 5000.0
+    X = M.surr_features(ctx, parts, t).cpu().numpy()
+    ref = S.features(grid, f0, f1, t, 0.0, T6H, st["lon"], st["lat"], st["p"]).astype(np.float32)
+    # the nearest node is chosen in float64 on both sides: identical stencils
+    np.testing.assert_array_equal(X[:, :162], ref[:, :162])
+    np.testing.assert_allclose(X[:, 162:], ref[:, 162:], rtol=0, atol=2e-7)
+
+
+def test_targets_match_oracle(M):
+    rng = np.random.default_rng(1)
+    n = 5000
+    a = {"lon": rng.uniform(0, 360, n), "lat": rng.uniform(-80, 80, n), "p": rng.uniform(2e3, 9e4, n),
+         "id": np.arange(n, dtype=np.uint32)}
+    b = {"lon": np.mod(a["lon"] + rng.uniform(-1, 1, n), 360), "lat": a["lat"] + rng.uniform(-.5, .5, n),
+         "p": a["p"] * np.exp(rng.uniform(-.1, .1, n)), "id": a["id"]}
+    Y = M.surr_targets(M.Particles.from_numpy(a), M.Particles.from_numpy(b)).cpu().numpy()
+    ref = S.targets(a["lon"], a["lat"], a["p"], b["lon"], b["lat"], b["p"])
+    np.testing.assert_allclose(Y, ref, rtol=2e-7, atol=1e-6)
 
 
 KERNELS = pytest.mark.parametrize("kernel", [0, 1], ids=["tcgen05", "mma_sync"])
@@ -158,7 +205,8 @@ def _dataset(M, grid, ctx, f0, f1, n, seed):
 
 
 @KERNELS
-def test_fused_inference_matches_oracle_pipeline(M, field, kernel):
+@STORAGES
+def test_fused_inference_matches_oracle_pipeline(M, field, stored, kernel, storage):
     """The fused inference (stencil gather, standardisation, three bf16 layers, displacement,
     position rules, fallback flag) against the oracle's pipeline on the same positions:
     oracle features -> standardise -> BF16 network -> displacement -> position rules.
@@ -167,8 +215,10 @@ def test_fused_inference_matches_oracle_pipeline(M, field, kernel):
     a position within 1e-4 cells of a half-cell (another nearest node, another stencil), or a
     standardised feature within 1e-3 of the envelope limit 4.  Elsewhere the outputs agree to the
     float32 accumulation bound plus at most three bf16 flips (see above), converted to metres,
-    plus the float32 rounding of the conversion itself (2^-19 relative)."""
-    grid, f0, f1, ctx = field
+    plus the float32 rounding of the conversion itself (2^-19 relative).  In every storage the
+    oracle reads the values the context holds (16-bit codes decoded with their level scales)."""
+    grid = field[0]
+    ctx, f0, f1 = stored(storage)
     n, t = 20_000, 3600.0
     st = uniform_particles(n, grid.plev, seed=21)
     st["lat"][:5] = [85.0, -86.0, 81.0, 10.0, 20.0]
