@@ -71,32 +71,37 @@ def test_bench_workload_sampled_parity(M):
     ctx.close()
 
 
-@pytest.fixture(scope="module")
-def large_grid(M):
-    """The 0.3 degree x 137 level grid (98.8 M points) with the multiscale 256-mode wind."""
+@pytest.fixture(scope="module", params=[0, 1], ids=["fp32", "bf16"])
+def large_grid(M, request):
+    """The 0.3 degree x 137 level grid (98.8 M points) with the multiscale 256-mode wind, stored in
+    float32 or bf16 (with level scales); the oracle reads the values the context holds."""
+    from oracle import met as omet
     from workloads import grid_03deg_137lev
+    storage = request.param
     grid = grid_03deg_137lev()
     modes = fourier_modes(3, n_modes=256, multiscale=True)
     snaps = [fourier_snapshot(grid, modes, h * DT_MET, device="cuda", as_numpy=False) for h in range(2)]
-    ctx = M.Context(grid, M.MPTRAC_FP32)
+    ctx = M.Context(grid, storage)
     for slot, f in enumerate(snaps):
         ctx.load_met(slot, slot * DT_MET, f["u"], f["v"], f["w"])
     torch.cuda.synchronize()
-    met = tr.Met(grid, 0.0, {k: v.cpu().numpy() for k, v in snaps[0].items()},
-                 DT_MET, {k: v.cpu().numpy() for k, v in snaps[1].items()})
+    host = [{k: v.cpu().numpy() for k, v in sn.items()} for sn in snaps]
     del snaps
     torch.cuda.empty_cache()
+    met = tr.Met(grid, 0.0, omet.stored_fields(host[0], storage), DT_MET, omet.stored_fields(host[1], storage))
+    del host
     yield grid, ctx, met
     ctx.close()
+    torch.cuda.empty_cache()
 
 
 @pytest.mark.parametrize("diffuse", [False, True])
 def test_large_grid_parity(M, large_grid, diffuse):
     """The largest grid of the workloads: each pair-record buffer holds 98.8 M records of 32 B
-    (3.2 GB), so the records of the last rows lie beyond 2^31 bytes.  2e4 particles spread over the
-    grid, plus particles placed in the last latitude rows, the last longitude column and the top
-    levels (the largest record offsets), take 20 fused steps against the oracle at the transport
-    tolerances, with and without diffusion."""
+    (3.2 GB; 16 B in bf16), so the records of the last rows lie beyond 2^31 bytes.  2e4 particles
+    spread over the grid, plus particles placed in the last latitude rows, the last longitude
+    column and the top levels (the largest record offsets), take 20 fused steps against the
+    oracle at the transport tolerances, with and without diffusion."""
     from _gpu_common import assert_positions_close
     grid, ctx, met = large_grid
     st0 = uniform_particles(20_000, grid.plev, 61)

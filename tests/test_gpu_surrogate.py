@@ -269,6 +269,14 @@ def test_fused_inference_matches_oracle_pipeline(M, field, stored, kernel, stora
     assert exact.mean() >= 0.95, exact.mean()
     bad = (d > sd32 * (acc + FLIPS * _flip_bound(Pb, act)) + conv) & moved[:, None]
     assert not bad.any(), (np.argwhere(bad)[:5], d[bad][:5])
+    # the kernels' own count of fallback particles equals the flags they wrote
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    again = M.Particles.from_numpy(st, meso=False, release=False)
+    fb2 = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    sur.advance(ctx, again, t, 1800.0, fb2, count)
+    sur.advance(ctx, M.Particles.from_numpy(st, meso=False, release=False), t, 1800.0, fb2, count)
+    torch.cuda.synchronize()
+    assert count.item() == 2 * int(fb2.sum().item()) == 2 * int(fbn.sum())
     # the 30-minute window must fit inside the loaded interval, else everything falls back
     sur.advance(ctx, parts, T6H - 900.0, 1800.0, fb)
     torch.cuda.synchronize()
