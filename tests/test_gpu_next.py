@@ -127,3 +127,51 @@ def test_sampling_and_settling_at_degenerate_positions(M):
     assert np.all(np.isfinite(got["p"]))
     np.testing.assert_allclose(got["p"], refp, rtol=1e-4)
     assert np.all((got["p"] >= grid.plev[-1]) & (got["p"] <= grid.plev[0]))
+
+
+@pytest.mark.parametrize("storage", [omet.FP32, omet.BF16])
+def test_masked_advection_matches_oracle(M, storage):
+    """mptrac_advect_masked (the surrogate's plain fallback): the particles whose mask is set take
+    the plain midpoint steps of the oracle, and the others are left exactly as they were.  The mask
+    is random, then a block of whole warps, then empty and full."""
+    from _gpu_common import assert_positions_close
+    from oracle import transport as tr
+    grid = grid_global(90, 46, 25)
+    m = fourier_modes(7)
+    f0, f1 = fourier_snapshot(grid, m, 0.0), fourier_snapshot(grid, m, T6H)
+    ctx = make_ctx(M, grid, [f0, f1], [0.0, T6H], storage=storage)
+    met = tr.Met(grid, 0.0, omet.stored_fields(f0, storage), T6H, omet.stored_fields(f1, storage))
+    n = 20_003
+    st = uniform_particles(n, grid.plev, seed=13)
+    rng = np.random.default_rng(14)
+    masks = [rng.random(n) < 0.14, (np.arange(n) // 32) % 5 == 0, np.zeros(n, bool), np.ones(n, bool)]
+    for mask in masks:
+        parts = M.Particles.from_numpy(st, meso=False, release=False)
+        M.advect_masked(ctx, parts, torch.from_numpy(mask.astype(np.uint8)).cuda(), 3600.0, 180.0, 10)
+        torch.cuda.synchronize()
+        got = parts.to_numpy()
+        for k in ("lon", "lat", "p"):
+            np.testing.assert_array_equal(got[k][~mask], st[k][~mask], err_msg=k)
+        if mask.any():
+            sub = {k: v[mask] for k, v in st.items()}
+            ref = tr.advect(met, sub, 3600.0, 180.0, 10)
+            assert_positions_close({k: v[mask] for k, v in got.items()}, ref, what=f"masked advection, storage {storage}")
+
+
+def test_colstats_match_numpy(M):
+    """Column means and standard deviations of a float32 device matrix against numpy in float64,
+    with the floor that turns the standard deviation of a constant column into 1."""
+    rng = np.random.default_rng(15)
+    n, ncol = 300_001, 176
+    X = (rng.standard_normal((n, ncol)) * rng.uniform(0.01, 100, ncol) + rng.uniform(-50, 50, ncol)).astype(np.float32)
+    X[:, 170:] = 0.0
+    X[:, 100] = 3.25                       # constant, non-zero
+    mean, sd = M.colstats(torch.from_numpy(X).cuda())
+    ref_m = X.astype(np.float64).mean(axis=0)
+    ref_s = X.astype(np.float64).std(axis=0)
+    np.testing.assert_allclose(mean, ref_m, rtol=1e-6, atol=1e-6 * np.abs(X).max())
+    varying = ref_s > 0
+    np.testing.assert_allclose(sd[varying], ref_s[varying], rtol=1e-5)
+    assert np.all(sd[~varying] == 1.0) and not varying[100] and np.all(~varying[170:])
+    with pytest.raises(M.MptracError):
+        M.colstats(torch.zeros((0, 4), dtype=torch.float32, device="cuda"))
