@@ -229,7 +229,7 @@ def error_summary(got, ref):
 
 # launch schedule of the batched form in the default line (the autotuner's choice on this
 # workload: register corner cache with 128 registers, one sort per met interval)
-BATCH_SCHEDULE = {"variant": 1, "persistent": False, "sort_every": 120}
+BATCH_SCHEDULE = {"variant": 1, "persistent": False, "per_thread": 1, "sort_every": 120}
 
 
 def storage_figures(dev, grid, snaps, init, best, steps, warmup, n_sub, fp32_ms):
@@ -244,7 +244,7 @@ def storage_figures(dev, grid, snaps, init, best, steps, warmup, n_sub, fp32_ms)
     stream = torch.cuda.Stream(device=dev)
     for name, storage in (("bf16", M.MPTRAC_BF16), ("fp16", M.MPTRAC_FP16)):
         ctx = M.Context(grid, storage)
-        ctx.set_launch(best["variant"], best["persistent"])
+        ctx.set_launch(best["variant"], best["persistent"], best.get("per_thread", 1))
         work = init.clone()
         sim = Simulation(ctx, periodic_snapshots(snaps, DT_MET), DT_MET, work, DT, M.DiffParams(), SEED_RNG,
                          SORT_EVERY, groups=best["groups"])
@@ -405,20 +405,20 @@ def run_ours(args, rank, world):
         sim_c = sim_for(cfg["groups"])
 
         def go():
-            ctx.set_launch(cfg["variant"], cfg["persistent"])
+            ctx.set_launch(cfg["variant"], cfg["persistent"], cfg["per_thread"])
             with torch.cuda.stream(stream):
                 sim_c.run(0.0, 2 * DT_MET, stream=stream)   # two intervals: one overlapped met load
         return go
 
     groups_try = (args.groups,) if args.groups else (1, 2, 3)
     if args.variant >= 0:   # fixed schedule (profiling): no autotuner launches before the timed pass
-        best = {"variant": args.variant, "persistent": False, "sort_every": SORT_EVERY,
+        best = {"variant": args.variant, "persistent": False, "per_thread": 1, "sort_every": SORT_EVERY,
                 "groups": args.groups or 2}
         tune_ms = {}
     else:
         best, tune_ms = autotune(make, lambda: work.copy_(init),
                                  candidates(sort_every=(SORT_EVERY,), groups=groups_try), stream, repeats=3)
-    ctx.set_launch(best["variant"], best["persistent"])
+    ctx.set_launch(best["variant"], best["persistent"], best["per_thread"])
     sim = sim_for(best["groups"])
 
     def one_pass():
@@ -611,7 +611,7 @@ def batch_figures(dev, grid, snaps, steps, warmup, count_scale=1.0, schedule=Non
     """Batched releases on one GPU: rate of the 72 h pass replayed from CUDA graphs.
 
     ``schedule`` None: the autotuner picks the launch variant, persistence and sort interval
-    on one met interval; else that schedule (dict variant, persistent, sort_every)."""
+    on one met interval; else that schedule (dict variant, persistent, per_thread, sort_every)."""
     import torch
 
     import paper_2211_12616_gb300 as M
@@ -633,7 +633,7 @@ def batch_figures(dev, grid, snaps, steps, warmup, count_scale=1.0, schedule=Non
     psteps = float((rel.counts * steps_active).sum())
 
     def sched(cfg):   # the schedule keys BatchedRun takes (one particle group: graphs span all releases)
-        return {k: cfg[k] for k in ("variant", "persistent", "sort_every")}
+        return {k: cfg[k] for k in ("variant", "persistent", "per_thread", "sort_every")}
 
     if schedule is None:
         def make(cfg):

@@ -282,10 +282,16 @@ int mptrac_sort_at(mptrac_ctx* ctx, const mptrac_particles* parts, double t, voi
  *               3: 128 threads per block, >= 6 resident blocks per SM (80 registers),
  *                  the per-particle corner cache in shared memory (24.6 KB per block)
  *               4: as 3 with >= 7 resident blocks per SM (72 registers)
- *   persistent  non-zero: one wave of blocks (SMs x resident blocks per SM) strides
- *               over the particles; zero: one thread per particle.
- * Errors: E_INVALID_ARG for an unknown variant. */
-int mptrac_set_launch(mptrac_ctx* ctx, int variant, int persistent);
+ *   schedule    0: one thread per particle (the default);
+ *               1: one wave of blocks (SMs x resident blocks per SM) strides over
+ *                  the particles;
+ *               k in 2..64: k particles per thread (ceil(n / (threads per block x k))
+ *                  blocks stride over the particles).
+ * Both apply to the fused step with diffusion (mptrac_step and the forms that end in
+ * a sort hand-off); the other transport calls (advection only, diffusion only,
+ * masked advection) keep one fixed launch shape.
+ * Errors: E_INVALID_ARG for an unknown variant or a schedule outside 0..64. */
+int mptrac_set_launch(mptrac_ctx* ctx, int variant, int schedule);
 
 /* Sort without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory (a host

@@ -328,8 +328,13 @@ class Context:
         check(load().mptrac_grid_counts(self.h, C.byref(parts.desc()), _ptr(out), _stream(stream)), self.h)
         return out
 
-    def set_launch(self, variant: int = 0, persistent: bool = False):
-        check(load().mptrac_set_launch(self.h, int(variant), int(persistent)), self.h)
+    def set_launch(self, variant: int = 0, persistent: bool = False, per_thread: int = 1):
+        """Launch variant and schedule of the fused step (``mptrac_set_launch``): one wave of
+        persistent blocks, else ``per_thread`` particles per thread."""
+        if persistent and per_thread != 1:
+            raise ValueError("a persistent launch takes no particles-per-thread count")
+        schedule = 1 if persistent else (int(per_thread) if per_thread > 1 else 0)
+        check(load().mptrac_set_launch(self.h, int(variant), schedule), self.h)
 
     def cell_keys(self, parts: Particles, stream=None) -> torch.Tensor:
         keys = torch.empty(parts.n, dtype=torch.int32, device=parts.lon.device)

@@ -1,9 +1,10 @@
 """Autotuner for the launch schedule of the transport kernels.
 
 The knobs change only how the work is scheduled, never the result (tested
-bit-exact): the launch variant of the fused step kernel (threads per block and
-register cap), one wave of persistent blocks versus one thread per particle,
-and the number of fused steps between two sorts.  Each candidate is timed with
+bit-exact): the launch variant of the fused step kernel (threads per block,
+register cap, corner cache in registers or shared memory), the schedule of the
+blocks (one wave of persistent blocks, or 1, 2 or 4 particles per thread), and
+the number of fused steps between two sorts.  Each candidate is timed with
 CUDA events on a representative slice of the real workload (one met interval
 from the real initial state) and the fastest is kept; results can be cached in
 a JSON file keyed by the device and the workload.
@@ -18,14 +19,18 @@ import torch
 
 VARIANTS = (0, 1, 2, 3, 4)
 PERSISTENT = (False, True)
-SORT_EVERY = (10, 20, 40, 120)
+PER_THREAD = (1, 2, 4)
+SORT_EVERY = (5, 10, 20, 40, 120)
 
 
-def candidates(variants=VARIANTS, persistent=PERSISTENT, sort_every=SORT_EVERY, groups=(1,)):
+def candidates(variants=VARIANTS, persistent=PERSISTENT, sort_every=SORT_EVERY, groups=(1,),
+               per_thread=PER_THREAD):
     """Schedules to try; ``groups`` is the number of particle groups on streams of their own
-    (used by runs that support it)."""
-    return [{"variant": v, "persistent": p, "sort_every": s, "groups": g}
-            for v, p, s, g in itertools.product(variants, persistent, sort_every, groups)]
+    (used by runs that support it).  A persistent launch has no particles-per-thread count
+    (``per_thread`` 1)."""
+    blocks = [(p, k) for p in persistent for k in (per_thread if not p else (1,))]
+    return [{"variant": v, "persistent": p, "per_thread": k, "sort_every": s, "groups": g}
+            for v, (p, k), s, g in itertools.product(variants, blocks, sort_every, groups)]
 
 
 def _time(fn, reset, stream, repeats):

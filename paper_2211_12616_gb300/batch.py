@@ -11,7 +11,7 @@ of ``sort_every`` fused steps each preceded by a sort -- is captured once into a
 CUDA graph and replayed, so a 72 h run is a dozen graph launches instead of
 hundreds of kernel launches from Python.
 
-The launch configuration (``variant``, ``persistent``) and ``sort_every`` change
+The launch configuration (``variant``, ``persistent``, ``per_thread``) and ``sort_every`` change
 only the schedule, never the results; ``autotune`` picks them by timing.
 """
 from __future__ import annotations
@@ -24,10 +24,11 @@ from ._native import Context, DiffParams, Particles
 class BatchedRun:
     def __init__(self, ctx: Context, snapshot_at, dt_met: float, particles: Particles,
                  t_start_rel, t_end_rel, dt: float, prm: DiffParams, seed: int,
-                 sort_every: int = 20, variant: int = 0, persistent: bool = True):
+                 sort_every: int = 20, variant: int = 0, persistent: bool = True, per_thread: int = 1):
         self.ctx, self.snapshot_at, self.dt_met = ctx, snapshot_at, float(dt_met)
         self.parts, self.dt, self.prm, self.seed = particles, float(dt), prm, int(seed)
         self.sort_every, self.variant, self.persistent = int(sort_every), int(variant), bool(persistent)
+        self.per_thread = int(per_thread)
         ctx.set_releases(t_start_rel, t_end_rel)
         self.workspace = torch.empty(ctx.sort_workspace_bytes(particles.n), dtype=torch.uint8,
                                      device=particles.lon.device)
@@ -63,7 +64,7 @@ class BatchedRun:
 
     def _enqueue(self, loads, blocks, stream):
         ctx = self.ctx
-        ctx.set_launch(self.variant, self.persistent)
+        ctx.set_launch(self.variant, self.persistent, self.per_thread)
         for slot, t in loads:
             ctx.load_met(slot, t, *self.snapshot_at(t), stream=stream)
         for t, step0, cnt in blocks:

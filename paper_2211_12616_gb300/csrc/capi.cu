@@ -42,7 +42,7 @@ struct mptrac_ctx {
     int n_rel = 0;
     int key_bits = 0;
     int launch_variant = 0;
-    bool persistent = false;
+    int schedule = 0;   // see mptrac_set_launch
     Geo geo{};
 };
 
@@ -272,7 +272,7 @@ int run_transport(mptrac_ctx* c, const mptrac_particles* P, double t, double dt,
         if (use_win) MPTRAC_CUDA(launch_windows(c->d_rel_ts, c->d_rel_te, c->n_rel, t, dt, n0, cnt, c->d_win, st));
         // the last launch hands its results to the sort, if one follows
         a.emit = (emit && n0 + cnt >= nsteps) ? *emit : SortEmit{};
-        MPTRAC_CUDA(launch_transport(c->storage, mode, a, grid, c->launch_variant, c->persistent, st));
+        MPTRAC_CUDA(launch_transport(c->storage, mode, a, grid, c->launch_variant, c->schedule, st));
     }
     return ok();
 }
@@ -607,12 +607,14 @@ int mptrac_sort_at(mptrac_ctx* c, const mptrac_particles* P, double t, void* ws,
     return ok();
 }
 
-int mptrac_set_launch(mptrac_ctx* c, int variant, int persistent) {
+int mptrac_set_launch(mptrac_ctx* c, int variant, int schedule) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
     DeviceGuard device_guard(c->device);
     if (variant < 0 || variant > 4) return fail(MPTRAC_E_INVALID_ARG, "launch variant must be 0..4 (got %d)", variant);
+    if (schedule < 0 || schedule > 64)
+        return fail(MPTRAC_E_INVALID_ARG, "launch schedule must be 0..64 (got %d)", schedule);
     c->launch_variant = variant;
-    c->persistent = persistent != 0;
+    c->schedule = schedule;
     return ok();
 }
 

@@ -111,8 +111,9 @@ enum Mode { MODE_ADVECT = 0, MODE_DIFFUSE = 1, MODE_STEP = 2, MODE_STEP_FULL = 3
 void note_launches(int n);
 
 // ---- launchers (each returns a cudaError_t of the launch) -------------------
+// schedule: 0 one particle per thread, 1 one wave of resident blocks, k >= 2 k particles per thread
 cudaError_t launch_transport(int storage, int mode, const StepArgs& a, int grid, int variant,
-                             bool persistent, cudaStream_t s);
+                             int schedule, cudaStream_t s);
 cudaError_t launch_windows(const double* ts, const double* te, int nrel, double t, double dt,
                            int n_begin, int nsteps, int2* out, cudaStream_t s);
 cudaError_t launch_interp(int storage, const Geo& g, MetPair mp, float w_lane0, float w_lane1, int64_t n,

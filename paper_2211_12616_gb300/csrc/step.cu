@@ -1027,7 +1027,7 @@ int grid_for(int64_t n) {
 // registers, 28 warps per SM (24 with 16-bit storage, whose scale tables take
 // shared memory too).
 template <int ST, int MODE, int BLOCK, int MINB, int CACHE>
-cudaError_t launch_step_variant(const StepArgs& a, int grid, bool persistent, cudaStream_t s) {
+cudaError_t launch_step_variant(const StepArgs& a, int grid, int schedule, cudaStream_t s) {
     auto kern = k_transport<ST, MODE, BLOCK, MINB, CACHE>;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -1044,7 +1044,7 @@ cudaError_t launch_step_variant(const StepArgs& a, int grid, bool persistent, cu
             carveout_set[dev].store(1, std::memory_order_relaxed);
         }
     }
-    if (persistent) {
+    if (schedule == 1) {
         // resident blocks per SM of this instantiation, per device
         static std::atomic<int> per_sm_cache[kMaxDevices];
         int per_sm = per_sm_cache[dev].load(std::memory_order_relaxed);
@@ -1062,31 +1062,33 @@ cudaError_t launch_step_variant(const StepArgs& a, int grid, bool persistent, cu
         const int64_t need = (a.n + BLOCK - 1) / BLOCK;
         grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(per_sm, 1), need));
     } else {
-        grid = (int)std::max<int64_t>(1, std::min<int64_t>((a.n + BLOCK - 1) / BLOCK, (int64_t)1 << 20));
+        // schedule k >= 2: k particles per thread (the kernel's loop strides over the grid)
+        const int64_t per_block = (int64_t)BLOCK * (schedule >= 2 ? schedule : 1);
+        grid = (int)std::max<int64_t>(1, std::min<int64_t>((a.n + per_block - 1) / per_block, (int64_t)1 << 20));
     }
     kern<<<grid, BLOCK, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int ST>
-cudaError_t launch_transport_st(int mode, const StepArgs& a, int grid, int variant, bool persistent,
+cudaError_t launch_transport_st(int mode, const StepArgs& a, int grid, int variant, int schedule,
                                 cudaStream_t s) {
     if (mode == MODE_STEP && a.turb && a.meso) {
         switch (variant) {
-            case 1: return launch_step_variant<ST, MODE_STEP_FULL, 128, 4, 0>(a, grid, persistent, s);
-            case 2: return launch_step_variant<ST, MODE_STEP_FULL, 128, 5, 0>(a, grid, persistent, s);
-            case 3: return launch_step_variant<ST, MODE_STEP_FULL, 128, 6, 1>(a, grid, persistent, s);
-            case 4: return launch_step_variant<ST, MODE_STEP_FULL, 128, 7, 1>(a, grid, persistent, s);
-            default: return launch_step_variant<ST, MODE_STEP_FULL, kBlock, 2, 0>(a, grid, persistent, s);
+            case 1: return launch_step_variant<ST, MODE_STEP_FULL, 128, 4, 0>(a, grid, schedule, s);
+            case 2: return launch_step_variant<ST, MODE_STEP_FULL, 128, 5, 0>(a, grid, schedule, s);
+            case 3: return launch_step_variant<ST, MODE_STEP_FULL, 128, 6, 1>(a, grid, schedule, s);
+            case 4: return launch_step_variant<ST, MODE_STEP_FULL, 128, 7, 1>(a, grid, schedule, s);
+            default: return launch_step_variant<ST, MODE_STEP_FULL, kBlock, 2, 0>(a, grid, schedule, s);
         }
     }
     if (mode == MODE_STEP) {
         switch (variant) {
-            case 1: return launch_step_variant<ST, MODE_STEP, 128, 4, 0>(a, grid, persistent, s);
-            case 2: return launch_step_variant<ST, MODE_STEP, 128, 5, 0>(a, grid, persistent, s);
-            case 3: return launch_step_variant<ST, MODE_STEP, 128, 6, 1>(a, grid, persistent, s);
-            case 4: return launch_step_variant<ST, MODE_STEP, 128, 7, 1>(a, grid, persistent, s);
-            default: return launch_step_variant<ST, MODE_STEP, kBlock, 2, 0>(a, grid, persistent, s);
+            case 1: return launch_step_variant<ST, MODE_STEP, 128, 4, 0>(a, grid, schedule, s);
+            case 2: return launch_step_variant<ST, MODE_STEP, 128, 5, 0>(a, grid, schedule, s);
+            case 3: return launch_step_variant<ST, MODE_STEP, 128, 6, 1>(a, grid, schedule, s);
+            case 4: return launch_step_variant<ST, MODE_STEP, 128, 7, 1>(a, grid, schedule, s);
+            default: return launch_step_variant<ST, MODE_STEP, kBlock, 2, 0>(a, grid, schedule, s);
         }
     }
     switch (mode) {
@@ -1099,13 +1101,13 @@ cudaError_t launch_transport_st(int mode, const StepArgs& a, int grid, int varia
 }  // namespace
 
 cudaError_t launch_transport(int storage, int mode, const StepArgs& a, int grid, int variant,
-                             bool persistent, cudaStream_t s) {
+                             int schedule, cudaStream_t s) {
     if (grid <= 0) grid = grid_for(a.n);
     note_launches(1);
     switch (storage) {
-        case MPTRAC_FP32: return launch_transport_st<MPTRAC_FP32>(mode, a, grid, variant, persistent, s);
-        case MPTRAC_BF16: return launch_transport_st<MPTRAC_BF16>(mode, a, grid, variant, persistent, s);
-        default: return launch_transport_st<MPTRAC_FP16>(mode, a, grid, variant, persistent, s);
+        case MPTRAC_FP32: return launch_transport_st<MPTRAC_FP32>(mode, a, grid, variant, schedule, s);
+        case MPTRAC_BF16: return launch_transport_st<MPTRAC_BF16>(mode, a, grid, variant, schedule, s);
+        default: return launch_transport_st<MPTRAC_FP16>(mode, a, grid, variant, schedule, s);
     }
 }
 

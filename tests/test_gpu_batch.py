@@ -51,7 +51,8 @@ def _run(M, case, cfg, graphs):
     ctx = M.Context(grid)
     parts = M.Particles.from_numpy(rel.particles)
     run = BatchedRun(ctx, _at(snaps), DT_MET, parts, rel.t_start, rel.t_end, DT, M.DiffParams(), 4,
-                     sort_every=cfg["sort_every"], variant=cfg["variant"], persistent=cfg["persistent"])
+                     sort_every=cfg["sort_every"], variant=cfg["variant"], persistent=cfg["persistent"],
+                     per_thread=cfg.get("per_thread", 1))
     s = torch.cuda.Stream()
     if graphs:
         run.run_eager(0.0, 2 * DT_MET, stream=s)   # warm-up outside capture (occupancy queries)
@@ -81,7 +82,9 @@ def test_batched_run_parity_and_schedule_invariance(M, case):
                 {"variant": 2, "persistent": True, "sort_every": 40},
                 {"variant": 3, "persistent": False, "sort_every": 20},
                 {"variant": 4, "persistent": True, "sort_every": 20},
-                {"variant": 0, "persistent": True, "sort_every": 120}):
+                {"variant": 0, "persistent": True, "sort_every": 120},
+                {"variant": 2, "persistent": False, "per_thread": 2, "sort_every": 5},
+                {"variant": 3, "persistent": False, "per_thread": 4, "sort_every": 20}):
         got = _run(M, case, cfg, graphs=True)
         for k in ("lon", "lat", "p", "up", "vp", "wp"):
             np.testing.assert_array_equal(got[k], base[k], err_msg=f"{cfg} {k}")
@@ -98,7 +101,8 @@ def test_autotuner_picks_a_candidate(M, case):
 
     def make(cfg):
         run = BatchedRun(ctx, _at(snaps), DT_MET, parts, rel.t_start, rel.t_end, DT, M.DiffParams(), 4,
-                         sort_every=cfg["sort_every"], variant=cfg["variant"], persistent=cfg["persistent"])
+                         sort_every=cfg["sort_every"], variant=cfg["variant"], persistent=cfg["persistent"],
+                         per_thread=cfg["per_thread"])
         return lambda: run.run_eager(0.0, DT_MET, stream=s)
 
     cands = candidates(sort_every=(20, 120))

@@ -188,6 +188,13 @@ def test_host_validation_errors(M, cfg1):
     ctx.advect(parts, 0.0, 180.0, 0)             # no steps: no-op
     torch.cuda.synchronize()
     np.testing.assert_array_equal(parts.lon.cpu().numpy(), st0["lon"])
+    from paper_2211_12616_gb300 import _native
+    for variant, schedule in ((5, 0), (-1, 0), (2, 65), (2, -1)):
+        with pytest.raises(M.MptracError) as e:
+            _native.check(M.load().mptrac_set_launch(ctx.h, variant, schedule), ctx.h)
+        assert e.value.code == -1
+    with pytest.raises(ValueError):
+        ctx.set_launch(2, True, per_thread=2)
 
 
 def test_checkpoint_resume_bit_identical(M, fourier):
