@@ -37,15 +37,17 @@ SORT_EVERY = 20
 SEED_FIELD = 2
 SEED_PART = 2
 SEED_RNG = 2
-# DRAM bytes (read + write) of one fused-step launch of this workload by the
-# number of particle groups (a launch covers 1/groups of the particles), from ncu
-# captures of full-size launches of variant 2 with the hand-off to the sort (see
-# profiles/).  A schedule without a capture reports None, and so does any launch
-# after the kernel changes, until it is captured again.
-TRAFFIC_PER_LAUNCH = {2: 156479744}   # 142.16 MB read + 14.32 MB written, 5e5 particles (two groups)
+# DRAM bytes (read + write) of one fused-step launch of this workload by
+# (particle groups, particles per thread) -- a launch covers 1/groups of the
+# particles -- from ncu captures of full-size launches of variant 2 with the
+# hand-off to the sort (see profiles/).  A schedule without a capture reports
+# None, and so does any launch after the kernel changes, until it is captured again.
+TRAFFIC_PER_LAUNCH = {(2, 1): 156299008,   # 142.14 MB read + 14.16 MB written, 5e5 particles
+                      (2, 2): 156856320,   # 143.12 + 13.74 MB
+                      (2, 4): 157262080}   # 143.84 + 13.42 MB
 # sha256 (first 16 hex digits) of the fused step's sources when the counters
 # were taken; a different hash means the kernel changed and traffic is None
-TRAFFIC_KERNEL_SHA = "3c7aeb32e97a7f53"
+TRAFFIC_KERNEL_SHA = "b65625923e98a0df"
 TRAFFIC_SOURCES = ("paper_2211_12616_gb300/csrc/step.cu", "paper_2211_12616_gb300/csrc/internal.h",
                    "paper_2211_12616_gb300/csrc/cell_key.cuh", "paper_2211_12616_gb300/csrc/met_record.cuh")
 
@@ -412,7 +414,7 @@ def run_ours(args, rank, world):
 
     groups_try = (args.groups,) if args.groups else (1, 2, 3)
     if args.variant >= 0:   # fixed schedule (profiling): no autotuner launches before the timed pass
-        best = {"variant": args.variant, "persistent": False, "per_thread": 1, "sort_every": SORT_EVERY,
+        best = {"variant": args.variant, "persistent": False, "per_thread": args.per_thread, "sort_every": SORT_EVERY,
                 "groups": args.groups or 2}
         tune_ms = {}
     else:
@@ -537,8 +539,9 @@ def run_ours(args, rank, world):
     met_b = 32.0 * grid.nx * grid.ny * grid.nz / psteps_per_launch
     b_hbm = stream_b + met_b
     t_roof = max(b_hbm / (hbm_peak * 1e9), L2_BYTES_PER_PARTICLE_STEP / (l2_gbs * 1e9))
-    traffic = (TRAFFIC_PER_LAUNCH.get(n_groups)
-               if best["variant"] == 2 and kernel_sha() == TRAFFIC_KERNEL_SHA else None)
+    traffic = (TRAFFIC_PER_LAUNCH.get((n_groups, best["per_thread"]))
+               if best["variant"] == 2 and not best["persistent"] and kernel_sha() == TRAFFIC_KERNEL_SHA
+               else None)
     line = {
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -1057,6 +1060,8 @@ def main():
     ap.add_argument("--count-scale", type=float, default=1.0)
     ap.add_argument("--variant", type=int, default=-1,
                     help="fixed launch variant of the fused step (-1: autotuned)")
+    ap.add_argument("--per-thread", type=int, default=1, choices=[1, 2, 4],
+                    help="particles per thread of the fused step with a fixed --variant")
     ap.add_argument("--groups", type=int, default=0,
                     help="particle groups on streams of their own (0: the autotuner picks 1, 2 or 3; "
                          "2 with a fixed --variant)")

@@ -379,6 +379,20 @@ int mptrac_surr_grads(mptrac_surr* s, const float* x, const float* y, int64_t n,
  * eps 1e-8, bias correction with step >= 1) at learning rate lr. */
 int mptrac_surr_train_step(mptrac_surr* s, const float* x, const float* y, int64_t n, float lr,
                            int step, float* loss, uintptr_t stream);
+/* One epoch of training in a single call: floor(n / batch) Adam steps, as
+ * mptrac_surr_train_step, on the consecutive mini-batches x[b batch ...],
+ * y[b batch ...] (DEVICE, as for mptrac_surr_grads; the caller shuffles), with
+ * step numbers step0 + 1, step0 + 2, ... and the cosine learning-rate decay
+ *     lr(step) = lr_min + (lr_max - lr_min) (1 + cos(pi step / total_steps)) / 2
+ * evaluated in float64 (in this order, without fused multiply-adds) and
+ * rounded to float32 (lr_max at step 0, lr_min at step total_steps).  Each batch's loss is ADDED to DEVICE *loss.  The result
+ * equals the same steps made one call at a time.  Rows past the last whole
+ * batch are not used.  Errors: E_INVALID_ARG for batch outside [1, max_batch],
+ * n < batch, lr_min <= 0 or lr_max < lr_min, steps outside [1, total_steps], or
+ * host pointers; nothing is launched then. */
+int mptrac_surr_train_epoch(mptrac_surr* s, const float* x, const float* y, int64_t n, int64_t batch,
+                            double lr_max, double lr_min, int step0, int total_steps, float* loss,
+                            uintptr_t stream);
 /* One 30-minute surrogate segment from time t (segment length dt_seg [s]):
  * particles inside the training envelope (|lat| <= 80 deg, every standardised
  * feature within +-4, [t, t + dt_seg] inside the loaded snapshots) move by

@@ -101,6 +101,8 @@ SIGNATURES = {
     "mptrac_surr_grads": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "mptrac_surr_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_int,
                                          C.c_void_p, C.c_void_p]),
+    "mptrac_surr_train_epoch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_double,
+                                          C.c_double, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "mptrac_surr_advance": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(ParticlesDesc), C.c_double, C.c_double,
                                       C.c_void_p, C.c_void_p, C.c_void_p]),
     "mptrac_surr_set_kernel": (C.c_int, [C.c_void_p, C.c_int]),
@@ -446,6 +448,14 @@ class Surrogate:
         """One Adam step; the batch loss is added to the 1-element device tensor ``loss``."""
         check(load().mptrac_surr_train_step(self.h, _ptr(x), _ptr(y), x.shape[0], float(lr), int(step),
                                             _ptr(loss), _stream(stream)))
+
+    def train_epoch(self, x: torch.Tensor, y: torch.Tensor, batch: int, lr_max: float, lr_min: float,
+                    step0: int, total_steps: int, loss: torch.Tensor, stream=None):
+        """Adam steps step0 + 1 ... on the consecutive mini-batches of (x, y) under the cosine
+        learning-rate decay, in one library call (``mptrac_surr_train_epoch``)."""
+        check(load().mptrac_surr_train_epoch(self.h, _ptr(x), _ptr(y), x.shape[0], int(batch), float(lr_max),
+                                             float(lr_min), int(step0), int(total_steps), _ptr(loss),
+                                             _stream(stream)))
 
     def advance(self, ctx: "Context", parts: "Particles", t, dt_seg, fallback: torch.Tensor,
                 count: torch.Tensor | None = None, stream=None):

@@ -917,6 +917,34 @@ int mptrac_surr_train_step(mptrac_surr* s, const float* x, const float* y, int64
     return ok();
 }
 
+int mptrac_surr_train_epoch(mptrac_surr* s, const float* x, const float* y, int64_t n, int64_t batch,
+                            double lr_max, double lr_min, int step0, int total_steps, float* loss,
+                            uintptr_t stream) {
+    if (!s) return fail(MPTRAC_E_NOT_INIT, "surrogate is NULL");
+    DeviceGuard device_guard_s(s->device);
+    if (batch <= 0 || batch > s->S.max_batch) return fail(MPTRAC_E_INVALID_ARG, "batch must be in [1, max_batch]");
+    if (n < batch) return fail(MPTRAC_E_INVALID_ARG, "n (%lld) holds no whole batch", (long long)n);
+    if (!(lr_min > 0.0) || !(lr_max >= lr_min) || !((float)lr_min > 0.f))
+        return fail(MPTRAC_E_INVALID_ARG, "need lr_max >= lr_min > 0 (and lr_min > 0 in float32)");
+    const int64_t steps = n / batch;
+    if (step0 < 0 || total_steps < 1 || (int64_t)step0 + steps > (int64_t)total_steps)
+        return fail(MPTRAC_E_INVALID_ARG, "steps %d .. %lld lie outside the schedule of %d", step0 + 1,
+                    (long long)(step0 + steps), total_steps);
+    if (!device_accessible(x) || !device_accessible(y) || !device_accessible(loss))
+        return fail(MPTRAC_E_INVALID_ARG, "x, y and loss must be device memory");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const double pi = 3.14159265358979323846;
+    for (int64_t b = 0; b < steps; ++b) {
+        const int step = step0 + 1 + (int)b;
+        // cosine decay from lr_max (step 0) to lr_min (step total_steps)
+        const double lr = lr_min + 0.5 * (lr_max - lr_min) * (1.0 + std::cos(pi * (double)step / (double)total_steps));
+        MPTRAC_CUDA(surr_forward(s->S, x + b * batch * MPTRAC_SURR_KPAD, batch, st));
+        MPTRAC_CUDA(surr_backward(s->S, y + b * batch * MPTRAC_SURR_NOUT, batch, loss, st));
+        MPTRAC_CUDA(surr_adam(s->S, (float)lr, step, st));
+    }
+    return ok();
+}
+
 int mptrac_surr_advance(mptrac_ctx* c, mptrac_surr* s, const mptrac_particles* P, double t, double dt_seg,
                         uint8_t* fallback, uint64_t* fallback_count, uintptr_t stream) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");

@@ -10,7 +10,8 @@ and moves tensors around.
   start, then the plain integrator (advection only) runs 10 substeps of 180 s
   and the displacement becomes the target.
 * ``train``: standardises features and targets with their column statistics,
-  then runs Adam on shuffled mini-batches with a cosine learning-rate decay.
+  then runs Adam on shuffled mini-batches with a cosine learning-rate decay
+  (``mptrac_surr_train_epoch``: one library call per epoch).
 * ``run_surrogate`` / ``run_plain``: 30-minute segments by the network (with
   the plain fallback), or by the plain integrator -- 10 substeps of 180 s (the
   reference trajectory), or one midpoint step of 30 minutes (``dt=DT_SEG``, the cheapest plain
@@ -82,15 +83,12 @@ def train(surr: Surrogate, X: torch.Tensor, Y: torch.Tensor, epochs: int = 4, ba
     total = steps_per_epoch * epochs
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     history = []
-    step = 0
     for ep in range(epochs):
         loss.zero_()
         order = torch.randperm(nt, generator=g, device="cuda")
         Xe, Ye = Xt[order], Yt[order]
-        for b in range(steps_per_epoch):
-            step += 1
-            lr_t = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * step / total))
-            surr.train_step(Xe[b * batch:(b + 1) * batch], Ye[b * batch:(b + 1) * batch], lr_t, step, loss)
+        if steps_per_epoch:   # the epoch's Adam steps and their learning rates: one library call
+            surr.train_epoch(Xe, Ye, batch, lr, lr_min, ep * steps_per_epoch, total, loss)
         history.append(loss.item() / max(steps_per_epoch, 1))
         if log:
             log(f"epoch {ep}: train loss {history[-1]:.5f}")

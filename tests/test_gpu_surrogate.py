@@ -425,3 +425,42 @@ def test_training_gemms_tcgen05_match_mma_sync(M, batch):
     np.testing.assert_allclose(b[0], a[0], rtol=1e-6, atol=1e-6 * np.abs(a[0]).max())
     assert abs(b[1] - a[1]) <= 1e-5 * abs(a[1])
     np.testing.assert_allclose(b[2], a[2], rtol=1e-5, atol=1e-5 * np.abs(a[2]).max())
+
+
+def test_train_epoch_equals_step_by_step(M):
+    """mptrac_surr_train_epoch makes exactly the Adam steps of single mptrac_surr_train_step calls
+    with the cosine learning rates evaluated on the host, bit for bit (rows past the last whole
+    batch unused); invalid arguments are rejected before anything runs.  Batches of 512 keep the
+    gradients deterministic: every reduction then adds at most two partial sums to a zeroed
+    value (larger batches split K across blocks that add their parts with atomics, in any order)."""
+    import math
+    batch, lr, lr_min, total = 512, 2e-3, 2e-5, 12
+    P, mu_x, sd_x, mu_y, sd_y, X, Y = _random_model(10, 5 * batch + 300)
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    a = _gpu_model(M, M.SURR_KERNEL_TCGEN05, P, mu_x, sd_x, mu_y, sd_y, max_batch=batch)
+    b = _gpu_model(M, M.SURR_KERNEL_TCGEN05, P, mu_x, sd_x, mu_y, sd_y, max_batch=batch)
+    la = torch.zeros(1, device="cuda")
+    lb = torch.zeros(1, device="cuda")
+    a.train_epoch(Xd, Yd, batch, lr, lr_min, 2, total, la)          # steps 3 .. 7 of a 12-step decay
+    for k in range(5):
+        step = 3 + k
+        lr_t = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * step / total))
+        b.train_step(Xd[k * batch:(k + 1) * batch], Yd[k * batch:(k + 1) * batch], lr_t, step, lb)
+    torch.cuda.synchronize()
+    theta = a.get_params()
+    np.testing.assert_array_equal(theta, b.get_params())
+    assert la.item() == lb.item() and la.item() > 0
+    assert not np.array_equal(theta, S.flatten(P).astype(np.float32))
+    bad = ((Xd, Yd, 0, lr, lr_min, 0, total),              # empty batch
+           (Xd, Yd, batch + 1, lr, lr_min, 0, total),      # above max_batch
+           (Xd[:batch - 1], Yd[:batch - 1], batch, lr, lr_min, 0, total),   # no whole batch
+           (Xd, Yd, batch, lr, 0.0, 0, total),             # lr_min not > 0
+           (Xd, Yd, batch, 1e-5, 2e-5, 0, total),          # lr_max < lr_min
+           (Xd, Yd, batch, lr, lr_min, 10, total),         # steps 11 .. 15 past the schedule
+           (Xd, Yd, batch, lr, lr_min, -1, total))
+    for args in bad:
+        with pytest.raises(M.MptracError) as e:
+            a.train_epoch(*args, la)
+        assert e.value.code == -1
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(a.get_params(), theta)   # nothing ran
