@@ -294,6 +294,62 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs& g, int64_t m, int6
     }
 }
 
+// The 16 consecutive columns [n, n + 16) of row m (one tensor-memory load of
+// the tcgen05 GEMM) through the epilogue: 16-byte loads, stores and atomics
+// where the row segment is whole and aligned, else element by element.  The
+// arithmetic is that of gemm_epilogue, element for element.
+template <int EPI>
+__device__ __forceinline__ void gemm_epilogue16(const GemmArgs& g, int64_t m, int64_t n, const float (&v)[16]) {
+    if (m >= g.M) return;
+    const int64_t o = m * g.ldc + n;
+    bool vec = n + 16 <= g.N && n + 16 <= g.n_valid && (g.ldc & 7) == 0 && (n & 7) == 0;
+    if (EPI != EPI_GELU_BWD) vec = vec && (reinterpret_cast<uintptr_t>(g.Cf + o) & 15) == 0;
+    if (EPI == EPI_BIAS_GELU || EPI == EPI_GELU_BWD) vec = vec && (reinterpret_cast<uintptr_t>(g.Cb + o) & 15) == 0;
+    if (EPI == EPI_GELU_BWD) vec = vec && (reinterpret_cast<uintptr_t>(g.Zin + o) & 15) == 0;
+    if (!vec) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) gemm_epilogue<EPI>(g, m, n + j, v[j]);
+        return;
+    }
+    if (EPI == EPI_ATOMIC_F32) {
+        float4* dst = reinterpret_cast<float4*>(g.Cf + o);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) atomicAdd(dst + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+        return;
+    }
+    float r[16];   // f32 result (BIAS_*) or pre-activation (GELU_BWD)
+    if (EPI == EPI_GELU_BWD) {
+        const float4* zin = reinterpret_cast<const float4*>(g.Zin + o);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 z = zin[q];
+            r[4 * q] = z.x;
+            r[4 * q + 1] = z.y;
+            r[4 * q + 2] = z.z;
+            r[4 * q + 3] = z.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) r[j] = v[j] + g.bias[n + j];
+        float4* dst = reinterpret_cast<float4*>(g.Cf + o);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+    }
+    if (EPI == EPI_BIAS_GELU || EPI == EPI_GELU_BWD) {
+        uint32_t w[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float a = EPI == EPI_BIAS_GELU ? gelu(r[2 * j]) : v[2 * j] * gelu_grad(r[2 * j]);
+            const float b = EPI == EPI_BIAS_GELU ? gelu(r[2 * j + 1]) : v[2 * j + 1] * gelu_grad(r[2 * j + 1]);
+            const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+            w[j] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(g.Cb + o);
+        dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+}
+
 constexpr int TM = 64, TN = 64, TK = 32, TKP = TK + 8;
 
 template <int EPI>
@@ -1170,10 +1226,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_surr_fused_tc(const FusedArgs
 // lanes x 128 columns of tensor memory) goes through the same epilogues as
 // k_gemm.  Waits are bounded as in k_surr_fused_tc.
 // ---------------------------------------------------------------------------
-constexpr int GT_M = 128, GT_N = 128, GT_K = 64;
-constexpr size_t kGStage = (size_t)(GT_M + GT_N) * GT_K * 2;   // 32 KB per stage
-constexpr size_t kGemmTcSmem = 2 * kGStage + 32;
-constexpr uint32_t kGemmTmemCols = 128;
+constexpr int GT_M = 128, GT_K = 64;   // the tile's N (BN) is 128, or 64 where M alone gives few tiles
+template <int BN>
+__host__ __device__ constexpr size_t gemm_stage_bytes() { return (size_t)(GT_M + BN) * GT_K * 2; }   // 32 KB (BN 128), 24 KB (64)
+template <int BN>
+__host__ __device__ constexpr size_t gemm_tc_smem() { return 2 * gemm_stage_bytes<BN>() + 32; }
 
 // Rows [r0, r0 + ROWS) x columns [kb, kb + GT_K) of an operand whose element
 // (row, k) is P[row * s_row + k * s_k], into the core-matrix layout at dst;
@@ -1212,13 +1269,16 @@ __device__ __forceinline__ void load_operand(unsigned char* dst, const __nv_bflo
     }
 }
 
-template <int EPI>
+template <int EPI, int BN>
 __global__ void __launch_bounds__(256, 1) k_gemm_tc(const GemmArgs g) {
+    static_assert(BN == 64 || BN == 128, "tile N of 64 or 128");
+    constexpr size_t kGStage = gemm_stage_bytes<BN>();
+    constexpr uint32_t kGemmTmemCols = BN;   // a power of two >= 32
     extern __shared__ __align__(128) unsigned char g_smem[];
     uint64_t* mbar = reinterpret_cast<uint64_t*>(g_smem + 2 * kGStage);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int64_t m0 = (int64_t)blockIdx.x * GT_M, n0 = (int64_t)blockIdx.y * GT_N;
+    const int64_t m0 = (int64_t)blockIdx.x * GT_M, n0 = (int64_t)blockIdx.y * BN;
     const int64_t kb0 = (int64_t)blockIdx.z * g.kchunk;
     const int64_t kend = min(g.K, kb0 + g.kchunk);
     if (warp == 0) {
@@ -1253,7 +1313,7 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc(const GemmArgs g) {
         unsigned char* Bs = As + (size_t)GT_M * GT_K * 2;
         const int64_t kb = kb0 + (int64_t)i * GT_K;
         load_operand<GT_M>(As, g.A, g.sam, g.sak, m0, g.M, kb, kend, tid);
-        load_operand<GT_N>(Bs, g.B, g.sbn, g.sbk, n0, g.N, kb, kend, tid);
+        load_operand<BN>(Bs, g.B, g.sbn, g.sbk, n0, g.N, kb, kend, tid);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -1263,7 +1323,7 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc(const GemmArgs g) {
 #pragma unroll
             for (int ks = 0; ks < GT_K / 16; ++ks)
                 umma_f16(tbase, umma_desc(a_addr + 256u * ks, 128u, 128u * (GT_K / 8)),
-                         umma_desc(b_addr + 256u * ks, 128u, 128u * (GT_K / 8)), umma_idesc(GT_M, GT_N),
+                         umma_desc(b_addr + 256u * ks, 128u, 128u * (GT_K / 8)), umma_idesc(GT_M, BN),
                          (i > 0 || ks > 0) ? 1u : 0u);
             umma_commit(smem_u32(&mbar[st]));
         }
@@ -1284,13 +1344,12 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc(const GemmArgs g) {
         const int row = 32 * (warp & 3) + (tid & 31);
         const uint32_t tlane = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
 #pragma unroll 1
-        for (int ch = 0; ch < 4; ++ch) {
-            const int c = 64 * (warp >> 2) + 16 * ch;
+        for (int ch = 0; ch < BN / 32; ++ch) {   // warps 0-3: columns [0, BN/2), warps 4-7: the rest
+            const int c = (BN / 2) * (warp >> 2) + 16 * ch;
             if (n0 + c >= g.N) break;   // warp-uniform
             float v[16];
             tmem_ld16(tlane + (uint32_t)c, v);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) gemm_epilogue<EPI>(g, m0 + row, n0 + c + j, v[j]);
+            gemm_epilogue16<EPI>(g, m0 + row, n0 + c, v);
         }
     }
     if (failed && tid == 0) atomicExch(g.status, 1);
@@ -1308,6 +1367,19 @@ int grid1(int64_t n, int block) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, 1 << 20));
 }
 
+template <int EPI, int BN>
+cudaError_t gemm_tc_bn(const GemmArgs& a, int gz, cudaStream_t s) {
+    dim3 grid((unsigned)((a.M + GT_M - 1) / GT_M), (unsigned)((a.N + BN - 1) / BN), (unsigned)std::max(gz, 1));
+    note_launches(1);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<EPI, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gemm_tc_smem<BN>());
+    if (e != cudaSuccess) return e;
+    k_gemm_tc<EPI, BN><<<grid, 256, gemm_tc_smem<BN>(), s>>>(a);
+    return cudaGetLastError();
+}
+
+// Tiles of 128 x 128, or 128 x 64 where N is at most 64 or where the 128-wide
+// tiles would leave more than half the SMs idle (the forward GEMMs of a batch).
 template <int EPI>
 cudaError_t gemm_tc(const GemmArgs& g, int splits, int* status, cudaStream_t s) {
     GemmArgs a = g;
@@ -1317,12 +1389,14 @@ cudaError_t gemm_tc(const GemmArgs& g, int splits, int* status, cudaStream_t s) 
     a.kchunk = ((g.K + splits - 1) / splits + GT_K - 1) / GT_K * GT_K;
     if (a.kchunk <= 0) a.kchunk = GT_K;
     const int gz = (int)((g.K + a.kchunk - 1) / a.kchunk);
-    dim3 grid((unsigned)((g.M + GT_M - 1) / GT_M), (unsigned)((g.N + GT_N - 1) / GT_N), (unsigned)std::max(gz, 1));
-    note_launches(1);
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmTcSmem);
-    if (e != cudaSuccess) return e;
-    k_gemm_tc<EPI><<<grid, 256, kGemmTcSmem, s>>>(a);
-    return cudaGetLastError();
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        sms = 1;
+    }
+    const int64_t tiles = ((g.M + GT_M - 1) / GT_M) * ((g.N + 127) / 128) * (int64_t)std::max(gz, 1);
+    if (g.N <= 64 || 2 * tiles <= sms) return gemm_tc_bn<EPI, 64>(a, gz, s);
+    return gemm_tc_bn<EPI, 128>(a, gz, s);
 }
 
 template <int EPI>
@@ -1404,6 +1478,19 @@ cudaError_t surr_forward(Surrogate& S, const float* X, int64_t B, cudaStream_t s
     return run_gemm<EPI_BIAS_F32>(S, g, 1, s);
 }
 
+// Split of K (the batch) of a weight-gradient GEMM [M x N]: about one CTA of
+// 128 x 128 per SM, each split at least one 64-wide chunk of K.
+int wgrad_splits(int64_t M, int64_t N, int64_t B) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        sms = 1;
+    }
+    const int64_t tiles = ((M + 127) / 128) * ((N + 127) / 128);
+    const int64_t want = std::max<int64_t>(1, (int64_t)sms / tiles);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (B + 63) / 64));
+}
+
 // Gradients of the loss for B samples into S.grad (zeroed first); loss added to *loss.
 cudaError_t surr_backward(Surrogate& S, const float* Yt, int64_t B, float* loss, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(S.grad, 0, NPAR * 4, s);
@@ -1411,12 +1498,11 @@ cudaError_t surr_backward(Surrogate& S, const float* Yt, int64_t B, float* loss,
     note_launches(1);
     k_loss<<<grid1(B, 256), 256, 0, s>>>(S.Yh, Yt, B, S.mu_y, S.isd_y, S.dY, loss, S.grad + OB3);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, B / 512));
     GemmArgs g{};
     // dW3 = H2^T dY  [HID x NO]
     g.A = S.H2; g.sam = 1; g.sak = HID; g.B = S.dY; g.sbk = NOP; g.sbn = 1;
     g.M = HID; g.N = NOP; g.K = B; g.Cf = S.grad + OW3; g.ldc = NO; g.n_valid = NO;
-    if ((e = run_gemm<EPI_ATOMIC_F32>(S, g, splits, s)) != cudaSuccess) return e;
+    if ((e = run_gemm<EPI_ATOMIC_F32>(S, g, wgrad_splits(g.M, g.N, B), s)) != cudaSuccess) return e;
     // dZ2 = (dY W3^T) * gelu'(Z2)
     g = GemmArgs{};
     g.A = S.dY; g.sam = NOP; g.sak = 1; g.B = S.W3b; g.sbk = 1; g.sbn = NOP;
@@ -1426,8 +1512,8 @@ cudaError_t surr_backward(Surrogate& S, const float* Yt, int64_t B, float* loss,
     g = GemmArgs{};
     g.A = S.H1; g.sam = 1; g.sak = HID; g.B = S.dZ2; g.sbk = HID; g.sbn = 1;
     g.M = HID; g.N = HID; g.K = B; g.Cf = S.grad + OW2; g.ldc = HID; g.n_valid = HID;
-    if ((e = run_gemm<EPI_ATOMIC_F32>(S, g, splits, s)) != cudaSuccess) return e;
-    const int rpb = 512;
+    if ((e = run_gemm<EPI_ATOMIC_F32>(S, g, wgrad_splits(g.M, g.N, B), s)) != cudaSuccess) return e;
+    const int rpb = 64;   // 128 blocks for a batch of 8192
     note_launches(1);
     k_colsum_bf16<<<grid1(B, rpb), HID, 0, s>>>(S.dZ2, B, rpb, S.grad + OB2);
     // dZ1 = (dZ2 W2^T) * gelu'(Z1)
@@ -1439,7 +1525,7 @@ cudaError_t surr_backward(Surrogate& S, const float* Yt, int64_t B, float* loss,
     g = GemmArgs{};
     g.A = S.Xh; g.sam = 1; g.sak = KP; g.B = S.dZ1; g.sbk = HID; g.sbn = 1;
     g.M = KP; g.N = HID; g.K = B; g.Cf = S.grad + OW1; g.ldc = HID; g.n_valid = HID;
-    if ((e = run_gemm<EPI_ATOMIC_F32>(S, g, splits, s)) != cudaSuccess) return e;
+    if ((e = run_gemm<EPI_ATOMIC_F32>(S, g, wgrad_splits(g.M, g.N, B), s)) != cudaSuccess) return e;
     note_launches(1);
     k_colsum_bf16<<<grid1(B, rpb), HID, 0, s>>>(S.dZ1, B, rpb, S.grad + OB1);
     return cudaGetLastError();
