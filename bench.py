@@ -372,7 +372,7 @@ def run_ours(args, rank, world):
     st0 = uniform_particles(n, grid.plev, SEED_PART + 1000 * rank, id0=id_offset(rank, n))
     init = M.Particles.from_numpy(st0, device=dev)
     work = init.clone()
-    ctx = M.Context(grid, M.MPTRAC_FP32)
+    ctx = M.Context(grid, {"fp32": M.MPTRAC_FP32, "bf16": M.MPTRAC_BF16, "fp16": M.MPTRAC_FP16}[args.storage])
     prm = M.DiffParams()
     stream = torch.cuda.Stream(device=dev)
     sims = {}
@@ -509,7 +509,7 @@ def run_ours(args, rank, world):
     # ---- the added forms on the same GPU: 16-bit storage, batched releases, surrogate ----
     forms, finals = None, {}
     n_sub = int(os.environ.get("BENCH_ORACLE_SAMPLE", "8000"))
-    if world == 1 and not args.no_forms:
+    if world == 1 and not args.no_forms and args.storage == "fp32":   # the forms compare against fp32 storage
         finals["fp32"] = final_subset(work, n_sub)
         t_forms = time.perf_counter()
         storage, f16 = storage_figures(dev, grid, snaps, init, best, max(1, args.steps // 2), 1, n_sub,
@@ -536,17 +536,20 @@ def run_ours(args, rank, world):
     # bytes (every pair record of the interval read once per launch: an upper bound)
     l2_gbs = measure_l2_gbs(dev)
     stream_b = PARTICLE_STREAM_BYTES * (n / n_groups) / psteps_per_launch
-    met_b = 32.0 * grid.nx * grid.ny * grid.nz / psteps_per_launch
+    rec_b = 32.0 if args.storage == "fp32" else 16.0        # bytes of a pair record
+    met_b = rec_b * grid.nx * grid.ny * grid.nz / psteps_per_launch
     b_hbm = stream_b + met_b
-    t_roof = max(b_hbm / (hbm_peak * 1e9), L2_BYTES_PER_PARTICLE_STEP / (l2_gbs * 1e9))
+    b_l2 = L2_BYTES_PER_PARTICLE_STEP * rec_b / 32.0
+    t_roof = max(b_hbm / (hbm_peak * 1e9), b_l2 / (l2_gbs * 1e9))
     traffic = (TRAFFIC_PER_LAUNCH.get((n_groups, best["per_thread"]))
                if best["variant"] == 2 and not best["persistent"] and kernel_sha() == TRAFFIC_KERNEL_SHA
-               else None)
+               and args.storage == "fp32" else None)
     line = {
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": _config(n, {"autotuned": best, "autotune_ms": tune_ms}),
+        "data": "synthetic", "config": _config(n, {"autotuned": best, "autotune_ms": tune_ms,
+                                                   "met_storage": args.storage}),
         "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TOP/s",
                      "frac": alu_achieved / alu_peak,
                      "traffic": traffic,
@@ -562,7 +565,7 @@ def run_ours(args, rank, world):
                               "unit": "TOP/s", "frac": mufu_achieved / mufu_peak,
                               "peak_kind": f"derived: {n_sm} SMs x {MUFU_PER_SM_PER_CLK} per clock x "
                                            f"{sm_mhz:.0f} MHz"}},
-        "gather_roofline": {"b_l2_per_particle_step": L2_BYTES_PER_PARTICLE_STEP, "l2_gbs": l2_gbs,
+        "gather_roofline": {"b_l2_per_particle_step": b_l2, "l2_gbs": l2_gbs,
                             "l2_kind": "measured here: device copy resident in L2 (read + write bytes)",
                             "b_hbm_per_particle_step": b_hbm, "hbm_gbs": hbm_peak,
                             "hbm_kind": f"{peak_kind} hbm_gbs",
@@ -1060,6 +1063,9 @@ def main():
     ap.add_argument("--count-scale", type=float, default=1.0)
     ap.add_argument("--variant", type=int, default=-1,
                     help="fixed launch variant of the fused step (-1: autotuned)")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"],
+                    help="met storage of the transport workload (fp32: the headline; bf16/fp16 for profiling, "
+                         "also reported under forms.storage of the default line)")
     ap.add_argument("--per-thread", type=int, default=1, choices=[1, 2, 4],
                     help="particles per thread of the fused step with a fixed --variant")
     ap.add_argument("--groups", type=int, default=0,

@@ -11,7 +11,8 @@
 // levels: reads are 128-byte rows of one level, writes are runs of 32
 // consecutive records.  The same values go to this slot's lane of the
 // interleaved pair records that the particle kernels read (two slots per grid
-// point), in both pair buffers the slot belongs to.
+// point), in both pair buffers the slot belongs to; for bf16 the pair records
+// hold the stored values with their level scale applied.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -114,6 +115,14 @@ __global__ void __launch_bounds__(256) k_pack(const float* __restrict__ u, const
 #pragma unroll
             for (int var = 0; var < 4; ++var) c[var] = code16(tile[var][kl][il], ST);
             static_cast<uint2*>(recv)[r] = make_uint2(c[0] | (c[1] << 16), c[2] | (c[3] << 16));
+            if (ST == MPTRAC_BF16) {
+                // the pair records hold the stored value itself (code times its power-of-two
+                // level scale): bf16 has float32's exponent range, so the product is again a
+                // bf16 number (for |value| >= 2^-126) and the step kernel needs no scale
+#pragma unroll
+                for (int var = 0; var < 4; ++var)
+                    c[var] = code16(__uint_as_float(c[var] << 16) * scales[var * nz + k], ST);
+            }
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 uint4* pr = static_cast<uint4*>(q ? pairs1 : pairs0) + r;   // words (u, v, omega, T), lane 0 low

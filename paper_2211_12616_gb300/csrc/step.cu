@@ -256,7 +256,8 @@ struct SmemT {
     float2 sc[3][NSC];     // scales of u, v, omega per level as pairs (slot 0, slot 1)
 };
 using Smem = SmemT<kMaxNZ>;
-template <int ST> using SmemFor = SmemT<ST == MPTRAC_FP32 ? 1 : kMaxNZ>;
+// level scales in shared memory only for fp16 pair records (bf16 pair records hold scaled values)
+template <int ST> using SmemFor = SmemT<ST == MPTRAC_FP16 ? kMaxNZ : 1>;
 
 // Cell of a point: indices (lon i, lat j, lower level k) and the
 // interpolation weights as (f, g = 1 - f) pairs.  All indices are clamped into
@@ -479,10 +480,16 @@ __device__ __forceinline__ void fetch_corners(const MetPair& mp, const S& s, con
             }
 #pragma unroll
             for (int qq = 0; qq < QG; ++qq) {
-                const int k = c.k + ((gi * QG + qq) >> 2);
-                U[qq] = f2_mul(decode_pair16<ST>(r[qq].x), *reinterpret_cast<const f2_t*>(&s.sc[0][k]));
-                V[qq] = f2_mul(decode_pair16<ST>(r[qq].y), *reinterpret_cast<const f2_t*>(&s.sc[1][k]));
-                W[qq] = f2_mul(decode_pair16<ST>(r[qq].z), *reinterpret_cast<const f2_t*>(&s.sc[2][k]));
+                if constexpr (ST == MPTRAC_BF16) {   // bf16 pair records hold the scaled values
+                    U[qq] = decode_pair16<ST>(r[qq].x);
+                    V[qq] = decode_pair16<ST>(r[qq].y);
+                    W[qq] = decode_pair16<ST>(r[qq].z);
+                } else {
+                    const int k = c.k + ((gi * QG + qq) >> 2);
+                    U[qq] = f2_mul(decode_pair16<ST>(r[qq].x), *reinterpret_cast<const f2_t*>(&s.sc[0][k]));
+                    V[qq] = f2_mul(decode_pair16<ST>(r[qq].y), *reinterpret_cast<const f2_t*>(&s.sc[1][k]));
+                    W[qq] = f2_mul(decode_pair16<ST>(r[qq].z), *reinterpret_cast<const f2_t*>(&s.sc[2][k]));
+                }
             }
         }
         cc.store(gi, U, V, W);
@@ -689,7 +696,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_transport(const __grid_constant
     __shared__ SmemFor<ST> s;
     __shared__ ulonglong2 s_cc[CACHE ? 12 * BLOCK : 1];
     using Cache = typename std::conditional<CACHE != 0, SmemCache<BLOCK>, RegCache>::type;
-    load_tables(s, a.geo, a.mp.scales[0], a.mp.scales[1], ST != MPTRAC_FP32);
+    load_tables(s, a.geo, a.mp.scales[0], a.mp.scales[1], ST == MPTRAC_FP16);
     const Geo& g = a.geo;
     constexpr bool FULL = (MODE == MODE_STEP_FULL);
     constexpr bool ADVECT = (MODE != MODE_DIFFUSE);
@@ -850,7 +857,7 @@ __global__ void __launch_bounds__(kBlock) k_interp(Geo g, MetPair mp, float wl, 
                                                    float* ou, float* ov, float* ow,
                                                    float* ovar) {
     __shared__ Smem s;
-    load_tables(s, g, mp.scales[0], mp.scales[1], ST != MPTRAC_FP32);
+    load_tables(s, g, mp.scales[0], mp.scales[1], ST == MPTRAC_FP16);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
         const Cell c = locate(ff_make(lon[idx] - g.lon0_d), ff_make(lat[idx] - g.lat0_d), ff_make(p[idx]).hi, g, s, -1);
