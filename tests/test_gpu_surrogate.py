@@ -204,6 +204,42 @@ def _dataset(M, grid, ctx, f0, f1, n, seed):
     return st, X, Y, p1
 
 
+def _compare_with_oracle_pipeline(grid, st, X, got, fbn, P, mu_x, sd_x, mu_y, sd_y):
+    """The fused inference's output (positions ``got``, fallback flags ``fbn``) for the particles
+    ``st`` with oracle features ``X``, against the oracle's pipeline: standardise -> BF16
+    network -> displacement -> position rules (bounds: see the test below)."""
+    xh = S.normalise(X, mu_x.astype(np.float32), sd_x.astype(np.float32))
+    xh[:, S.NFEAT:] = 0
+    env = S.in_envelope(xh, st["lat"])
+    Pb = _oracle_bf16(P)
+    yh, act = S.forward(Pb, S.bf16_round(xh), rnd=S.bf16_round)
+    mu32, sd32 = mu_y.astype(np.float32).astype(np.float64), sd_y.astype(np.float32).astype(np.float64)
+    y = yh * sd32 + mu32
+    pmin, pmax = grid.plev[-1], grid.plev[0]
+    lon1, lat1, p1 = S.apply_displacement(st["lon"], st["lat"], st["p"], y)
+    lon1, lat1, p1 = tr.position_bc(lon1, lat1, p1, 0.0, pmin, pmax)
+
+    near = np.any(np.abs(np.abs(X[:, 162:165]) - 0.5) < 1e-4, axis=1)
+    near |= np.any(np.abs(np.abs(xh[:, :S.NFEAT]) - 4.0) < 1e-3, axis=1)
+    assert near.mean() < 0.01, near.mean()
+    np.testing.assert_array_equal(fbn[~near] == 0, env[~near])
+    for k in ("lon", "lat", "p"):                      # fallback particles are not moved
+        np.testing.assert_array_equal(got[k][fbn == 1], st[k][fbn == 1])
+
+    moved = (fbn == 0) & ~near
+    clamped = (p1 <= pmin) | (p1 >= pmax)
+    np.testing.assert_array_equal(got["p"][moved & clamped], p1[moved & clamped])
+    ygot = S.targets(st["lon"], st["lat"], st["p"], got["lon"], got["lat"], got["p"])
+    acc = (S.HIDDEN + 1) * ACC * (S.bf16_round(np.abs(act[4])) @ np.abs(Pb["W3"]) + np.abs(Pb["b3"]))
+    conv = 2.0 ** -19 * (np.abs(y) + np.abs(mu32)) + np.array([1e-6, 1e-6, 2.0 ** -20])
+    d = np.abs(ygot - y)
+    d[:, 2] = np.where(clamped, 0.0, d[:, 2])
+    exact = np.all(d <= sd32 * acc + conv, axis=1)[moved]
+    assert exact.mean() >= 0.95, exact.mean()
+    bad = (d > sd32 * (acc + FLIPS * _flip_bound(Pb, act)) + conv) & moved[:, None]
+    assert not bad.any(), (np.argwhere(bad)[:5], d[bad][:5])
+
+
 @KERNELS
 @STORAGES
 def test_fused_inference_matches_oracle_pipeline(M, field, stored, kernel, storage):
@@ -237,38 +273,9 @@ def test_fused_inference_matches_oracle_pipeline(M, field, stored, kernel, stora
     sur.status()
     got, fbn = parts.to_numpy(), fb.cpu().numpy()
 
-    xh = S.normalise(X, mu_x.astype(np.float32), sd_x.astype(np.float32))
-    xh[:, S.NFEAT:] = 0
-    env = S.in_envelope(xh, st["lat"])
-    Pb = _oracle_bf16(P)
-    yh, act = S.forward(Pb, S.bf16_round(xh), rnd=S.bf16_round)
-    mu32, sd32 = mu_y.astype(np.float32).astype(np.float64), sd_y.astype(np.float32).astype(np.float64)
-    y = yh * sd32 + mu32
-    pmin, pmax = grid.plev[-1], grid.plev[0]
-    lon1, lat1, p1 = S.apply_displacement(st["lon"], st["lat"], st["p"], y)
-    lon1, lat1, p1 = tr.position_bc(lon1, lat1, p1, 0.0, pmin, pmax)
-
-    near = np.any(np.abs(np.abs(X[:, 162:165]) - 0.5) < 1e-4, axis=1)
-    near |= np.any(np.abs(np.abs(xh[:, :S.NFEAT]) - 4.0) < 1e-3, axis=1)
-    assert near.mean() < 0.01, near.mean()
-    np.testing.assert_array_equal(fbn[~near] == 0, env[~near])
+    _compare_with_oracle_pipeline(grid, st, X, got, fbn, P, mu_x, sd_x, mu_y, sd_y)
     assert fbn[0] == 1 and fbn[1] == 1 and fbn[2] == 1
     assert 0.05 < fbn.mean() < 0.5
-    for k in ("lon", "lat", "p"):                      # fallback particles are not moved
-        np.testing.assert_array_equal(got[k][fbn == 1], st[k][fbn == 1])
-
-    moved = (fbn == 0) & ~near
-    clamped = (p1 <= pmin) | (p1 >= pmax)
-    np.testing.assert_array_equal(got["p"][moved & clamped], p1[moved & clamped])
-    ygot = S.targets(st["lon"], st["lat"], st["p"], got["lon"], got["lat"], got["p"])
-    acc = (S.HIDDEN + 1) * ACC * (S.bf16_round(np.abs(act[4])) @ np.abs(Pb["W3"]) + np.abs(Pb["b3"]))
-    conv = 2.0 ** -19 * (np.abs(y) + np.abs(mu32)) + np.array([1e-6, 1e-6, 2.0 ** -20])
-    d = np.abs(ygot - y)
-    d[:, 2] = np.where(clamped, 0.0, d[:, 2])
-    exact = np.all(d <= sd32 * acc + conv, axis=1)[moved]
-    assert exact.mean() >= 0.95, exact.mean()
-    bad = (d > sd32 * (acc + FLIPS * _flip_bound(Pb, act)) + conv) & moved[:, None]
-    assert not bad.any(), (np.argwhere(bad)[:5], d[bad][:5])
     # the kernels' own count of fallback particles equals the flags they wrote
     count = torch.zeros(1, dtype=torch.int64, device="cuda")
     again = M.Particles.from_numpy(st, meso=False, release=False)
@@ -464,3 +471,45 @@ def test_train_epoch_equals_step_by_step(M):
         assert e.value.code == -1
     torch.cuda.synchronize()
     np.testing.assert_array_equal(a.get_params(), theta)   # nothing ran
+
+
+@pytest.fixture(scope="module")
+def field_1deg(M):
+    from workloads import grid_1deg_60lev
+    grid = grid_1deg_60lev()
+    m = fourier_modes(2)
+    f0, f1 = fourier_snapshot(grid, m, 0.0), fourier_snapshot(grid, m, T6H)
+    return grid, f0, f1, make_ctx(M, grid, [f0, f1], [0.0, T6H])
+
+
+def test_fused_inference_full_size_sampled(M, field_1deg):
+    """At the size of the surrogate run: 1e7 + 77 particles (a ragged last tile) on the 1-degree,
+    60-level grid, one 30-minute segment of the tcgen05 inference as the run launches it; 3000
+    sampled particles (the first and the last 1000, and 1000 drawn between) against the oracle
+    pipeline, and the kernel's count of fallback particles against the flags it wrote."""
+    grid, f0, f1, ctx = field_1deg
+    n, t = 10_000_077, 3600.0
+    st = uniform_particles(n, grid.plev, seed=23)
+    rng = np.random.default_rng(24)
+    idx = np.unique(np.concatenate([np.arange(1000), np.arange(n - 1000, n),
+                                    rng.choice(np.arange(1000, n - 1000), 1000, replace=False)]))
+    sub = {k: v[idx] for k, v in st.items()}
+    X = S.features(grid, f0, f1, t, 0.0, T6H, sub["lon"], sub["lat"], sub["p"])
+    P = S.init_params(4)
+    for b in ("b1", "b2", "b3"):
+        P[b] = rng.standard_normal(P[b].shape) * 0.1
+    mu_x, sd_x = X.mean(axis=0), X.std(axis=0)
+    sd_x[sd_x < 1e-12] = 1.0
+    mu_y, sd_y = np.array([500.0, -300.0, 0.001]), np.array([2.0e4, 1.5e4, 0.05])
+    sur = _gpu_model(M, M.SURR_KERNEL_TCGEN05, P, mu_x, sd_x, mu_y, sd_y, max_batch=1024)
+    parts = M.Particles.from_numpy(st, meso=False, release=False)
+    fb = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    sur.advance(ctx, parts, t, 1800.0, fb, count)
+    sur.status()
+    it = torch.from_numpy(idx).cuda()
+    got = {k: getattr(parts, k)[it].cpu().numpy() for k in ("lon", "lat", "p")}
+    fbn = fb[it].cpu().numpy()
+    assert count.item() == int(fb.sum().item()) > 0
+    _compare_with_oracle_pipeline(grid, sub, X, got, fbn, P, mu_x, sd_x, mu_y, sd_y)
+    assert 0.05 < fbn.mean() < 0.5
