@@ -98,7 +98,8 @@ typedef struct {
 } mptrac_grid_desc;
 
 /* Particle state (the paper's atm_t, Section 4.4), structure of arrays of
- * length n, all DEVICE pointers owned by the caller.
+ * length n (0 <= n <= 2^31 - 1; every call rejects other counts with
+ * E_INVALID_ARG), all DEVICE pointers owned by the caller.
  *   lon, lat, p     float64 positions [deg, deg, Pa]; lon in [lon0, lon0+360)
  *   id              uint32 particle identity (the random-number counter uses
  *                   it, so results do not depend on the array order)

@@ -175,3 +175,29 @@ def test_colstats_match_numpy(M):
     assert np.all(sd[~varying] == 1.0) and not varying[100] and np.all(~varying[170:])
     with pytest.raises(M.MptracError):
         M.colstats(torch.zeros((0, 4), dtype=torch.float32, device="cuda"))
+
+
+def test_every_particle_call_accepts_zero_particles(M):
+    """n = 0 through every entry point that takes particles: nothing is launched on the
+    particle arrays and nothing faults; fixed-size outputs are still written (grid counts zero)."""
+    grid = grid_global(36, 19, 8)
+    z = {k: np.full((grid.nz, grid.ny, grid.nx), 250.0 if k == "T" else 1.0, np.float32) for k in ("u", "v", "w", "T")}
+    ctx = make_ctx(M, grid, [z, z], [0.0, T6H], nvars=4)
+    empty = {"lon": np.zeros(0), "lat": np.zeros(0), "p": np.zeros(0), "id": np.zeros(0, np.uint32)}
+    parts = M.Particles.from_numpy(empty)
+    ctx.advect(parts, 0.0, 180.0, 3)
+    ctx.step(parts, 0.0, 180.0, M.DiffParams(), 1, 0, 3)
+    ctx.sort(parts)
+    assert ctx.sample_met(parts, 0.0).numel() == 0
+    counts = ctx.grid_counts(parts)
+    assert counts.numel() == grid.nx * grid.ny * grid.nz and int(counts.sum().item()) == 0
+    zf = torch.zeros(0, dtype=torch.float32, device="cuda")
+    ctx.sediment(parts, zf, zf, 0.0, 60.0, 2)
+    assert ctx.cell_keys(parts).numel() == 0
+    M.advect_masked(ctx, parts, torch.zeros(0, dtype=torch.uint8, device="cuda"), 0.0, 180.0, 2)
+    assert M.surr_features(ctx, parts, 0.0).shape[0] == 0
+    sur = M.Surrogate(64)
+    sur.advance(ctx, parts, 0.0, 1800.0, torch.zeros(0, dtype=torch.uint8, device="cuda"))
+    sur.status()
+    torch.cuda.synchronize()
+    assert parts.n == 0

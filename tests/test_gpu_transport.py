@@ -195,6 +195,18 @@ def test_host_validation_errors(M, cfg1):
         assert e.value.code == -1
     with pytest.raises(ValueError):
         ctx.set_launch(2, True, per_thread=2)
+    # particle counts outside [0, 2^31 - 1] are rejected before any launch
+    import ctypes
+    lib = M.load()
+    for bad_n in (-1, 2 ** 31):
+        d = parts.desc()
+        d.n = bad_n
+        assert lib.mptrac_advect(ctx.h, ctypes.byref(d), 0.0, 180.0, 1, torch.cuda.current_stream().cuda_stream) == -1
+        assert lib.mptrac_step(ctx.h, ctypes.byref(d), 0.0, 180.0, ctypes.byref(M.DiffParams().desc()), 1, 0, 1,
+                               torch.cuda.current_stream().cuda_stream) == -1
+        assert b"out of range" in lib.mptrac_last_error(ctx.h)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(parts.lon.cpu().numpy(), st0["lon"])
 
 
 def test_checkpoint_resume_bit_identical(M, fourier):
