@@ -1597,8 +1597,8 @@ cudaError_t launch_surr_fused(int storage, Surrogate& S, const Geo& g, MetView m
                               uint64_t* fallback_count, double lon0, cudaStream_t s) {
     FusedArgs a{g, m0, m1, n, lon, lat, p, fallback, w, window_ok, S.W1b, S.W2b, S.W3b,
                 S.theta + OB1, S.theta + OB2, S.b3p, S.mu_x, S.isd_x, S.mu_y, S.sd_y,
-                lon0, g.pmin_d, g.pmax_d, S.status, kWaitCycles, 0};
-    a.fb_count = reinterpret_cast<unsigned long long*>(fallback_count);
+                lon0, g.pmin_d, g.pmax_d, S.status, kWaitCycles, 0,
+                reinterpret_cast<unsigned long long*>(fallback_count)};
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
