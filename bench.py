@@ -1037,12 +1037,36 @@ def run_next(args, rank, world):
     ms_sample = timeit(lambda: ctx.sample_met(parts, 3600.0))
     ms_count = timeit(lambda: ctx.grid_counts(parts))
     ms_sedi = timeit(lambda: (parts.p.copy_(p_save), ctx.sediment(parts, radius, density, 0.0, 180.0, 20)))
+    # rooflines from algorithmic bytes: HBM = particle arrays read and written + every slot record
+    # of both snapshots read once (an upper bound); L2 = the per-particle corner gather with no reuse
+    hbm_peak, hbm_kind = _peaks()
+    l2_gbs = measure_l2_gbs(dev)
+    cells = grid.nx * grid.ny * grid.nz
+    met_b = 2 * cells * 16
+
+    def roof(ms, hbm_b, l2_b=None):
+        r = {"hbm_bytes": hbm_b, "hbm_gbs": hbm_b / (ms / 1e3) / 1e9,
+             "hbm_frac": hbm_b / (ms / 1e3) / 1e9 / hbm_peak, "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": hbm_kind}
+        if l2_b is not None:
+            r.update({"l2_bytes": l2_b, "l2_gbs": l2_b / (ms / 1e3) / 1e9, "l2_frac": l2_b / (ms / 1e3) / 1e9 / l2_gbs,
+                      "l2_peak_gbs": l2_gbs, "l2_peak_kind": "measured here (copy probe resident in L2)"})
+        return r
+
     line = {"workload": f"next rows on the 1deg x 60-level grid (u, v, omega, T), {n} sorted particles",
             "sample_met": {"ms": ms_sample, "particles_per_s": n / (ms_sample / 1e3),
-                           "bytes_per_particle": 24 + 16 + 2 * 8 * 16},
+                           "bytes_per_particle": "HBM 24 (lon, lat, p) + 16 (u, v, omega, T out); "
+                                                 "L2 2 snapshots x 8 corners x 16 B",
+                           "roofline": roof(ms_sample, 40 * n + met_b, 2 * 8 * 16 * n)},
             "grid_counts": {"ms": ms_count, "particles_per_s": n / (ms_count / 1e3),
-                            "bytes_per_particle": 24, "cells": grid.npoints},
-            "sediment_20_steps": {"ms": ms_sedi, "particle_steps_per_s": 20 * n / (ms_sedi / 1e3)}}
+                            "bytes_per_particle": "HBM 24 (lon, lat, p) + 4 per cell (zeroed counts)",
+                            "cells": grid.npoints, "roofline": roof(ms_count, 24 * n + 4 * cells)},
+            "sediment_20_steps": {"ms": ms_sedi, "particle_steps_per_s": 20 * n / (ms_sedi / 1e3),
+                                  "bytes_per_particle": "HBM 16 (lon, lat) + 16 (p read, written) + 8 (radius, "
+                                                        "density) per launch",
+                                  "roofline": roof(ms_sedi, 40 * n + met_b),
+                                  "note": "the T corners stay in registers while a particle stays in its cell, so "
+                                          "there is no per-step gather; the launch is bound by its arithmetic "
+                                          "(T interpolation, viscosity, slip correction per step)"}}
     print(json.dumps(line), flush=True)
 
 
