@@ -283,6 +283,8 @@ int mptrac_sort_at(mptrac_ctx* ctx, const mptrac_particles* parts, double t, voi
  *               3: 128 threads per block, >= 6 resident blocks per SM (80 registers),
  *                  the per-particle corner cache in shared memory (24.6 KB per block)
  *               4: as 3 with >= 7 resident blocks per SM (72 registers)
+ *               5: 64 threads per block, >= 10 resident blocks per SM (96 registers)
+ *               6: 512 threads per block, >= 1 resident block per SM (128 registers)
  *   schedule    0: one thread per particle (the default);
  *               1: one wave of blocks (SMs x resident blocks per SM) strides over
  *                  the particles;

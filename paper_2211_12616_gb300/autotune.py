@@ -17,7 +17,7 @@ import os
 
 import torch
 
-VARIANTS = (0, 1, 2, 3, 4)
+VARIANTS = (0, 1, 2, 3, 4, 5, 6)   # 64 to 512 threads per block, register or shared-memory corner cache
 PERSISTENT = (False, True)
 PER_THREAD = (1, 2, 4)
 SORT_EVERY = (5, 10, 20, 40, 120)

@@ -610,7 +610,7 @@ int mptrac_sort_at(mptrac_ctx* c, const mptrac_particles* P, double t, void* ws,
 int mptrac_set_launch(mptrac_ctx* c, int variant, int schedule) {
     if (!c) return fail(MPTRAC_E_NOT_INIT, "context is NULL");
     DeviceGuard device_guard(c->device);
-    if (variant < 0 || variant > 4) return fail(MPTRAC_E_INVALID_ARG, "launch variant must be 0..4 (got %d)", variant);
+    if (variant < 0 || variant > 6) return fail(MPTRAC_E_INVALID_ARG, "launch variant must be 0..6 (got %d)", variant);
     if (schedule < 0 || schedule > 64)
         return fail(MPTRAC_E_INVALID_ARG, "launch schedule must be 0..64 (got %d)", schedule);
     c->launch_variant = variant;

@@ -1032,7 +1032,8 @@ int grid_for(int64_t n) {
 // 2 = (128, 5) 96 registers, 20 warps per SM; 3 = (128, 6) corner cache in
 // shared memory, 80 registers, 24 warps per SM; 4 = (128, 7) the same with 72
 // registers, 28 warps per SM (24 with 16-bit storage, whose scale tables take
-// shared memory too).
+// shared memory too); 5 = (64, 10) 96 registers in the smallest blocks; 6 =
+// (512, 1) 128 registers in the largest.
 template <int ST, int MODE, int BLOCK, int MINB, int CACHE>
 cudaError_t launch_step_variant(const StepArgs& a, int grid, int schedule, cudaStream_t s) {
     auto kern = k_transport<ST, MODE, BLOCK, MINB, CACHE>;
@@ -1086,6 +1087,8 @@ cudaError_t launch_transport_st(int mode, const StepArgs& a, int grid, int varia
             case 2: return launch_step_variant<ST, MODE_STEP_FULL, 128, 5, 0>(a, grid, schedule, s);
             case 3: return launch_step_variant<ST, MODE_STEP_FULL, 128, 6, 1>(a, grid, schedule, s);
             case 4: return launch_step_variant<ST, MODE_STEP_FULL, 128, 7, 1>(a, grid, schedule, s);
+            case 5: return launch_step_variant<ST, MODE_STEP_FULL, 64, 10, 0>(a, grid, schedule, s);
+            case 6: return launch_step_variant<ST, MODE_STEP_FULL, 512, 1, 0>(a, grid, schedule, s);
             default: return launch_step_variant<ST, MODE_STEP_FULL, kBlock, 2, 0>(a, grid, schedule, s);
         }
     }
@@ -1095,6 +1098,8 @@ cudaError_t launch_transport_st(int mode, const StepArgs& a, int grid, int varia
             case 2: return launch_step_variant<ST, MODE_STEP, 128, 5, 0>(a, grid, schedule, s);
             case 3: return launch_step_variant<ST, MODE_STEP, 128, 6, 1>(a, grid, schedule, s);
             case 4: return launch_step_variant<ST, MODE_STEP, 128, 7, 1>(a, grid, schedule, s);
+            case 5: return launch_step_variant<ST, MODE_STEP, 64, 10, 0>(a, grid, schedule, s);
+            case 6: return launch_step_variant<ST, MODE_STEP, 512, 1, 0>(a, grid, schedule, s);
             default: return launch_step_variant<ST, MODE_STEP, kBlock, 2, 0>(a, grid, schedule, s);
         }
     }

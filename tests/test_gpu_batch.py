@@ -84,7 +84,9 @@ def test_batched_run_parity_and_schedule_invariance(M, case):
                 {"variant": 4, "persistent": True, "sort_every": 20},
                 {"variant": 0, "persistent": True, "sort_every": 120},
                 {"variant": 2, "persistent": False, "per_thread": 2, "sort_every": 5},
-                {"variant": 3, "persistent": False, "per_thread": 4, "sort_every": 20}):
+                {"variant": 3, "persistent": False, "per_thread": 4, "sort_every": 20},
+                {"variant": 5, "persistent": False, "per_thread": 1, "sort_every": 40},
+                {"variant": 6, "persistent": True, "sort_every": 10}):
         got = _run(M, case, cfg, graphs=True)
         for k in ("lon", "lat", "p", "up", "vp", "wp"):
             np.testing.assert_array_equal(got[k], base[k], err_msg=f"{cfg} {k}")

@@ -189,7 +189,7 @@ def test_host_validation_errors(M, cfg1):
     torch.cuda.synchronize()
     np.testing.assert_array_equal(parts.lon.cpu().numpy(), st0["lon"])
     from paper_2211_12616_gb300 import _native
-    for variant, schedule in ((5, 0), (-1, 0), (2, 65), (2, -1)):
+    for variant, schedule in ((7, 0), (-1, 0), (2, 65), (2, -1)):
         with pytest.raises(M.MptracError) as e:
             _native.check(M.load().mptrac_set_launch(ctx.h, variant, schedule), ctx.h)
         assert e.value.code == -1

@@ -57,9 +57,9 @@ def test_batch_plan_rejects_a_fractional_interval():
 def test_candidates_are_the_full_product():
     c = candidates()
     # block schedules: 1, 2 or 4 particles per thread, or one persistent wave
-    assert len(c) == 5 * 4 * 5
+    assert len(c) == 7 * 4 * 5
     assert {(x["variant"], x["persistent"], x["per_thread"], x["sort_every"]) for x in c} == {
-        (v, p, k, s) for v in range(5) for (p, k) in ((False, 1), (False, 2), (False, 4), (True, 1))
+        (v, p, k, s) for v in range(7) for (p, k) in ((False, 1), (False, 2), (False, 4), (True, 1))
         for s in (5, 10, 20, 40, 120)}
     g = candidates(variants=(2,), persistent=(False,), sort_every=(20,), groups=(1, 2, 3), per_thread=(1,))
     assert [x["groups"] for x in g] == [1, 2, 3]
