@@ -26,7 +26,9 @@ first sorts need no met and overlap the loads of the first two snapshots.
 Snapshots that ``snapshot_at`` returns in host memory (pinned, for the copies
 to overlap) are prefetched: right after an interval's loads, the snapshot the
 next interval needs is copied into one of two device buffers on a copy stream
-while the interval computes, and its load then reads the device copy.
+while the interval computes, and its load then reads the device copy.  The
+first two snapshots go the same way, so that the first one's repack overlaps
+the second one's copy.
 
 This module only sequences ABI calls.
 """
@@ -138,7 +140,11 @@ class Simulation:
         # the particles are ready here: the first sorts need no met and overlap the loads
         parts_ready = torch.cuda.Event()
         parts_ready.record(main)
-        # snapshots 0 and 1 in stream order; snapshot 2 (a free slot) on the load stream
+        # snapshots 0 and 1 in stream order; snapshot 2 (a free slot) on the load stream.  Host
+        # snapshots 0 and 1 are first both copied on the copy stream, so that the repack of the
+        # first overlaps the copy of the second (and the caller's own uploads)
+        for k in (0, 1):
+            self._prefetch(T(k))
         for k in (0, 1):
             self._load(ctx, k % 3, T(k), main)
         ls.wait_stream(main)
