@@ -111,6 +111,21 @@ enum Mode { MODE_ADVECT = 0, MODE_DIFFUSE = 1, MODE_STEP = 2, MODE_STEP_FULL = 3
 void note_launches(int n);
 
 // ---- launchers (each returns a cudaError_t of the launch) -------------------
+// Blocks of `block` threads for a grid-stride launch over n items: one thread per
+// item, but at most per_sm blocks per SM, so that each block fills its shared
+// tables (levels, key tables) once for many items.
+inline int strided_grid(int64_t n, int block, int per_sm) {
+    int64_t b = (n + block - 1) / block;
+    if (b < 1) b = 1;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        sms > 0 && b > (int64_t)sms * per_sm)
+        b = (int64_t)sms * per_sm;
+    else
+        (void)cudaGetLastError();
+    return (int)(b > (1 << 20) ? (1 << 20) : b);
+}
+
 // schedule: 0 one particle per thread, 1 one wave of resident blocks, k >= 2 k particles per thread
 cudaError_t launch_transport(int storage, int mode, const StepArgs& a, int grid, int variant,
                              int schedule, cudaStream_t s);

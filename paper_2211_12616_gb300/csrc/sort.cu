@@ -355,13 +355,6 @@ WsLayout ws_layout(int64_t n) {
     return L;
 }
 
-int grid_for(int64_t n) {
-    int64_t b = (n + 255) / 256;
-    if (b < 1) b = 1;
-    if (b > (1 << 20)) b = 1 << 20;
-    return (int)b;
-}
-
 }  // namespace
 
 size_t sort_workspace_bytes(int64_t n) { return ws_layout(n).total; }
@@ -369,7 +362,7 @@ size_t sort_workspace_bytes(int64_t n) { return ws_layout(n).total; }
 cudaError_t launch_cell_keys(const Geo& g, int64_t n, const double* lon, const double* lat,
                              const double* p, uint32_t* keys, cudaStream_t s) {
     note_launches(1);
-    k_keys<<<grid_for(n), 256, 0, s>>>(g, n, lon, lat, p, keys, nullptr);
+    k_keys<<<strided_grid(n, 256, 8), 256, 0, s>>>(g, n, lon, lat, p, keys, nullptr);
     return cudaGetLastError();
 }
 
@@ -456,7 +449,7 @@ cudaError_t sort_from_keys(const mptrac_particles& P, void* ws, int key_bits, cu
 cudaError_t launch_grid_counts(const Geo& g, int64_t n, const double* lon, const double* lat,
                                const double* p, uint32_t* counts, cudaStream_t s) {
     note_launches(1);
-    k_grid_counts<<<grid_for(n), 256, 0, s>>>(g, n, lon, lat, p, counts);
+    k_grid_counts<<<strided_grid(n, 256, 8), 256, 0, s>>>(g, n, lon, lat, p, counts);
     return cudaGetLastError();
 }
 

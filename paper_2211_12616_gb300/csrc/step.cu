@@ -890,6 +890,7 @@ __global__ void __launch_bounds__(kBlock) k_sample(Geo g, MetView m0, MetView m1
         const int i1 = (c.i + 1 == g.nx) ? 0 : c.i + 1;
         const int col[4] = {c.j * g.nx + c.i, c.j * g.nx + i1, (c.j + 1) * g.nx + c.i, (c.j + 1) * g.nx + i1};
         float res[2][4];
+#pragma unroll   // the 16 record loads of both snapshots in flight together
         for (int t = 0; t < 2; ++t) {
             const R* rec = static_cast<const R*>(t ? m1.rec : m0.rec);
             const float* sc = t ? m1.scales : m0.scales;
@@ -1133,7 +1134,7 @@ cudaError_t launch_windows(const double* ts, const double* te, int nrel, double 
 cudaError_t launch_interp(int storage, const Geo& g, MetPair mp, float w_lane0, float w_lane1, int64_t n,
                           const double* lon, const double* lat, const double* p, float* ou,
                           float* ov, float* ow, float* ovar, cudaStream_t s) {
-    const int grid = grid_for(n);
+    const int grid = strided_grid(n, kBlock, 8);
     note_launches(1);
     switch (storage) {
         case MPTRAC_FP32:
@@ -1151,7 +1152,7 @@ cudaError_t launch_interp(int storage, const Geo& g, MetPair mp, float w_lane0, 
 
 cudaError_t launch_sample(int storage, const Geo& g, MetView m0, MetView m1, float w, int64_t n,
                           const double* lon, const double* lat, const double* p, float* out, cudaStream_t s) {
-    const int grid = grid_for(n);
+    const int grid = strided_grid(n, kBlock, 8);
     note_launches(1);
     switch (storage) {
         case MPTRAC_FP32: k_sample<MPTRAC_FP32><<<grid, kBlock, 0, s>>>(g, m0, m1, w, n, lon, lat, p, out); break;
@@ -1165,7 +1166,7 @@ cudaError_t launch_sedi(int storage, const Geo& g, MetView m0, MetView m1, int64
                         const double* lat, double* p, const float* radius, const float* rho_p, int nsteps,
                         float dt, float w0, float dw, cudaStream_t s) {
     SediArgs a{g, m0, m1, n, lon, lat, p, radius, rho_p, nsteps, dt, w0, dw};
-    const int grid = grid_for(n);
+    const int grid = grid_for(n);   // 20 steps a thread: one particle per thread balances best
     note_launches(1);
     switch (storage) {
         case MPTRAC_FP32: k_sedi<MPTRAC_FP32><<<grid, kBlock, 0, s>>>(a); break;
