@@ -388,9 +388,9 @@ int mptrac_surr_train_step(mptrac_surr* s, const float* x, const float* y, int64
  * step numbers step0 + 1, step0 + 2, ... and the cosine learning-rate decay
  *     lr(step) = lr_min + (lr_max - lr_min) (1 + cos(pi step / total_steps)) / 2
  * evaluated in float64 (in this order, without fused multiply-adds) and
- * rounded to float32 (lr_max at step 0, lr_min at step total_steps).  Each batch's loss is ADDED to DEVICE *loss.  The result
- * equals the same steps made one call at a time.  Rows past the last whole
- * batch are not used.  Errors: E_INVALID_ARG for batch outside [1, max_batch],
+ * rounded to float32 (lr_max at step 0, lr_min at step total_steps).  Each
+ * batch's loss is ADDED to DEVICE *loss.  The result equals the same steps
+ * made one call at a time.  Rows past the last whole batch are not used.  Errors: E_INVALID_ARG for batch outside [1, max_batch],
  * n < batch, lr_min <= 0 or lr_max < lr_min, steps outside [1, total_steps], or
  * host pointers; nothing is launched then. */
 int mptrac_surr_train_epoch(mptrac_surr* s, const float* x, const float* y, int64_t n, int64_t batch,
